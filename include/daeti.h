@@ -1,0 +1,210 @@
+/*
+ * daeti.h — C ABI of libdaeti, a GB300 (sm_103a) solver for the cardiac
+ * monodomain equation by dual adaptive explicit time integration.
+ *
+ * Method (Mountris & Pueyo, arXiv:2011.04747):
+ *   Eq. 1    dV/dt = -I_ion(V)/C + div(D grad V),  n . D grad V = 0 on the boundary.
+ *   Eq. 2    Strang operator splitting: step I  (diffusion, dt/2),
+ *            step II (reaction, dt), step III (diffusion, dt/2); steps III and I of
+ *            consecutive steps merge into one "step B" (Section 2).
+ *   Step A   (Section 2) forward Euler (Rush-Larsen gates for TP06) with
+ *            dt_ar = dt/k per node, k = k0 + floor(|dV/dt|), k0 = 5 if dV/dt > 0
+ *            else 1, clamped to [1, k_max], k_max = floor(dt/dt0).
+ *   Step B   (Section 2) forward Euler with dt_ad = dt/(2l) on M_L dV/dt = -K V,
+ *            l = floor(dt/(2 dt_s)) if dt/2 > dt_s else 1.
+ *   Eq. 3    dt_s = 0.9 min_i m_ii / (k_ii + sum_{j!=i} |k_ij|)  (Gershgorin).
+ *
+ * Conventions common to every entry point
+ *   - Every function returns an int status: DAETI_OK (0) or one of the
+ *     DAETI_E* codes below; daeti_last_error() gives a message for the last
+ *     failure on that context.  No function aborts the process.
+ *   - Input arrays are host memory owned by the caller and are copied during
+ *     the call; the caller may free them on return.
+ *   - The library owns every device allocation it makes (cudaMalloc in
+ *     daeti_prepare); daeti_destroy frees them.
+ *   - Work is enqueued on the stream given by daeti_set_stream (default: a
+ *     stream created by the library).  daeti_advance is asynchronous;
+ *     daeti_synchronize and the host-side read functions wait for it.
+ *   - Node numbering of structured grids: x + nx*(y + ny*z); element
+ *     numbering: ex + (nx-1)*(ey + (ny-1)*ez).  Units: ms, cm, cm^2/ms and
+ *     the cell model's own voltage unit (mV for TP06, dimensionless for
+ *     Mitchell-Schaeffer).
+ *   - Call order: create -> set_mesh_* -> set_conductivity -> set_cell_model
+ *     -> add_stimulus* -> prepare -> [init_state] -> advance / read_* ... ->
+ *     destroy.  Out-of-order calls return DAETI_ESTATE.
+ */
+#ifndef DAETI_H
+#define DAETI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DAETI_OK 0
+#define DAETI_EINVAL 1        /* bad argument (NULL, size, negative D, t_end not a multiple of dt, ...) */
+#define DAETI_ENOMEM 2        /* device or host allocation failed */
+#define DAETI_ECUDA 3         /* a CUDA runtime call failed (message names it) */
+#define DAETI_ESTATE 4        /* call made in the wrong order */
+#define DAETI_EUNSTABLE 5     /* dt_ad * lambda_max >= 2 (explicit diffusion would diverge) */
+#define DAETI_ENONFINITE 6    /* V became NaN/Inf during advance */
+#define DAETI_ETIMEOUT 7      /* a bounded device wait gave up */
+#define DAETI_EUNSUPPORTED 8  /* valid request this build does not implement */
+
+/* arithmetic of the time stepping */
+#define DAETI_FP64 0          /* every state, operator and update in double */
+#define DAETI_FP32_KAHAN 1    /* float state/operators, compensated (Kahan) V updates */
+#define DAETI_FP32 2          /* float, plain V updates */
+
+/* splitting variants of Section 3 */
+#define DAETI_SCHEME_DAETI 0  /* adaptive k (step A) and adaptive l (step B) */
+#define DAETI_SCHEME_OSTAR 1  /* adaptive k, l = 1, dt reduced to dt/ceil(dt/dt_s) if dt_s < dt */
+#define DAETI_SCHEME_OST 2    /* k = l = 1 at the given dt */
+
+#define DAETI_L_FLOOR 0       /* l = floor(dt / (2 dt_s)), as printed in Section 2 */
+#define DAETI_L_CEIL 1        /* l = ceil(dt / (2 dt_s)) */
+
+/* cell models */
+#define DAETI_MODEL_MS 1      /* Mitchell-Schaeffer, params {tau_in, tau_out, tau_open, tau_close, v_gate} */
+#define DAETI_MODEL_TP06 2    /* ten Tusscher-Panfilov 2006, params {celltype: 0 endo, 1 epi, 2 mid} */
+
+/* dtype codes for the read functions */
+#define DAETI_DTYPE_F64 0
+#define DAETI_DTYPE_F32 1
+
+typedef struct daeti_options {
+    int32_t struct_size;       /* sizeof(daeti_options); checked by daeti_create */
+    int32_t precision;         /* DAETI_FP64 | DAETI_FP32_KAHAN | DAETI_FP32 */
+    int32_t scheme;            /* DAETI_SCHEME_* */
+    int32_t l_rounding;        /* DAETI_L_FLOOR | DAETI_L_CEIL */
+    double dt;                 /* splitting step (ms), > 0 */
+    double dt0;                /* smallest reaction sub-step (ms): k_max = floor(dt/dt0) */
+    double v_threshold;        /* activation threshold; NaN = model default (MS 0.5, TP06 -40 mV) */
+    int32_t gate_rush_larsen;  /* TP06 gates: 1 Rush-Larsen, 0 forward Euler */
+    int32_t bucket_k;          /* 1: group nodes by k before step A (warp-uniform sub-step counts) */
+    int32_t graph_steps;       /* steps per captured CUDA graph (even, 0 = plain launches) */
+    int32_t react_block;       /* threads per block of the reaction kernel (0 = default) */
+    int32_t diff_block;        /* threads per block of the diffusion kernel (0 = default) */
+    int32_t fuse_diffusion;    /* 1: one launch per step B when l == 1 (both halves + sync) */
+} daeti_options;
+
+typedef struct daeti_ctx daeti_ctx;
+
+/* Fill *opt with defaults: FP32_KAHAN, DAETI, FLOOR, dt = 0.1, dt0 = 0.01,
+ * v_threshold = NaN, Rush-Larsen gates, bucketing on, 20 steps per graph,
+ * default block sizes, fused diffusion on. */
+void daeti_default_options(daeti_options* opt);
+
+/* Create a context.  opt may be NULL (defaults).  *out receives the handle.
+ * Errors: EINVAL (bad struct_size or option values), ECUDA (no device). */
+int daeti_create(daeti_ctx** out, const daeti_options* opt);
+
+/* Free every host and device resource of ctx (NULL is accepted). */
+int daeti_destroy(daeti_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+const char* daeti_last_error(const daeti_ctx* ctx);
+
+/* Use cuda_stream (a cudaStream_t, may be NULL for the legacy default stream)
+ * for all later work.  The stream stays owned by the caller. */
+int daeti_set_stream(daeti_ctx* ctx, void* cuda_stream);
+
+/* Structured grid (Section 3.1/3.2 "4-node regular elements"; 8-node hexes in
+ * 3D): dim = 2 or 3, n[0..dim-1] >= 2 nodes per axis (n[2] ignored in 2D),
+ * spacing h > 0 (cm). */
+int daeti_set_mesh_grid(daeti_ctx* ctx, int dim, const int64_t n[3], double h);
+
+/* Tetrahedral mesh (Section 3.3): xyz = 3*n_nodes doubles (cm), tets =
+ * 4*n_tets node indices in [0, n_nodes).  Degenerate tets -> EINVAL. */
+int daeti_set_mesh_tet(daeti_ctx* ctx, int64_t n_nodes, const double* xyz,
+                       int64_t n_tets, const int64_t* tets);
+
+/* Per-element conductivity D_e = d_trans I + (d_long - d_trans) f f^T
+ * (Section 3.1: longitudinal d0, transverse rho*d0, fibre direction f).
+ * n_elem must equal the mesh's element count; d_long, d_trans >= 0 (0 makes
+ * a non-conducting element); fibre = 3*n_elem doubles (normalised here), or
+ * NULL for isotropic d_long. */
+int daeti_set_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
+                           const double* d_trans, const double* fibre);
+
+/* Cell model for every node (DAETI_MODEL_*) with n_params parameters
+ * (params may be NULL for the published defaults). */
+int daeti_set_cell_model(daeti_ctx* ctx, int model, const double* params, int n_params);
+
+/* Stimulus (Section 3: current injected at a node set): amplitude is added to
+ * dV/dt (model units per ms) at every reaction sub-step whose start time t
+ * satisfies t0 + p*period <= t < t0 + p*period + duration, p < count
+ * (1e-9 ms guard on both edges).  At most 32 stimuli. */
+int daeti_add_stimulus(daeti_ctx* ctx, const int64_t* nodes, int64_t n_nodes,
+                       double t_start, double duration, double amplitude,
+                       double period, int count);
+
+/* Assemble K and the lumped mass M_L, allocate device memory, compute dt_s
+ * (Eq. 3, FP64 on the GPU), lambda_max(M_L^-1 K) by FP64 power iteration,
+ * l, k_max and the effective dt of the scheme; set the published initial
+ * state.  Errors: ESTATE (missing mesh/conductivity/model), EUNSTABLE,
+ * ENOMEM, ECUDA. */
+int daeti_prepare(daeti_ctx* ctx);
+
+/* Stability data computed by prepare (any pointer may be NULL). */
+int daeti_get_stability(daeti_ctx* ctx, double* dt_s, double* lambda_max, int* l,
+                        int* k_max, double* dt_eff);
+
+/* Node and state counts after prepare. */
+int daeti_get_sizes(daeti_ctx* ctx, int64_t* n_nodes, int* n_states);
+
+/* Set the state (host, double, state-major: state[s*n_nodes + i]; row 0 = V)
+ * or the model's published initial state when state == NULL; resets t = 0,
+ * activation times to -1 and k to 1. */
+int daeti_init_state(daeti_ctx* ctx, const double* state);
+
+/* Advance from the current time to t_end (ms; must be a whole number of
+ * steps ahead).  Enqueues work and returns without waiting. */
+int daeti_advance(daeti_ctx* ctx, double t_end);
+
+/* Wait for enqueued work; returns ENONFINITE if V became NaN/Inf. */
+int daeti_synchronize(daeti_ctx* ctx);
+
+/* Current simulated time (ms) and number of completed steps. */
+int daeti_get_time(daeti_ctx* ctx, double* t, int64_t* n_steps);
+
+/* Copy V (n_nodes values) into out as dtype (DAETI_DTYPE_*); on_device = 1
+ * means out is device memory (enqueued on the stream), 0 host (waits). */
+int daeti_read_v(daeti_ctx* ctx, void* out, int dtype, int on_device);
+
+/* Activation times (ms, first upward crossing of v_threshold, -1 if none). */
+int daeti_read_activation(daeti_ctx* ctx, void* out, int dtype, int on_device);
+
+/* Full state into host memory (double, state-major, n_states*n_nodes). */
+int daeti_read_state(daeti_ctx* ctx, double* out);
+
+/* Checkpoint: byte size of a saved state (*bytes), and save/restore of the
+ * complete time-stepping state (state, Kahan terms, V at the last sync, k,
+ * activation times, step counter) to/from caller host memory. */
+int daeti_state_bytes(daeti_ctx* ctx, int64_t* bytes);
+int daeti_save_state(daeti_ctx* ctx, void* buf, int64_t buf_bytes);
+int daeti_load_state(daeti_ctx* ctx, const void* buf, int64_t buf_bytes);
+
+/* Total node reaction sub-steps (sum of k over nodes and steps) since the
+ * last init_state/load_state, counted while nodes are grouped by k
+ * (bucket_k = 1); waits for enqueued work. */
+int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
+
+/* Per-kernel timing (CUDA events around every launch of the plain-launch
+ * path; graphs are not used while it is on).  which: 0 reaction,
+ * 1 diffusion, 2 bucketing.  Returns total milliseconds and launch count
+ * since profiling was enabled. */
+int daeti_set_profiling(daeti_ctx* ctx, int enable);
+int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* launches);
+
+/* Algorithmic bytes and FP32/FP64 operations of one launch of kernel `which`
+ * at the current problem (the counts the roofline figures use). */
+int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAETI_H */

@@ -1,0 +1,332 @@
+"""Thin ctypes binding of libdaeti (argument marshalling only).
+
+Every ``daeti_*`` function here has the name and meaning of the C entry point
+declared in ``include/daeti.h`` and only converts Python arguments (numpy
+arrays, torch tensors, streams) into pointers and sizes.  All computation runs
+in the library's CUDA kernels; there is no Python or CPU fallback, and
+importing the binding without a built ``libdaeti.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdaeti.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(9)
+FP64, FP32_KAHAN, FP32 = 0, 1, 2
+SCHEME_DAETI, SCHEME_OSTAR, SCHEME_OST = 0, 1, 2
+L_FLOOR, L_CEIL = 0, 1
+MODEL_MS, MODEL_TP06 = 1, 2
+DTYPE_F64, DTYPE_F32 = 0, 1
+KERNEL_REACTION, KERNEL_DIFFUSION, KERNEL_BUCKET = 0, 1, 2
+
+_PREC = {"fp64": FP64, "fp32_kahan": FP32_KAHAN, "fp32": FP32}
+_SCHEME = {"daeti": SCHEME_DAETI, "ostar": SCHEME_OSTAR, "ost": SCHEME_OST}
+_MODEL = {"ms": MODEL_MS, "tp06": MODEL_TP06}
+
+
+class DaetiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdaeti error {code}: {msg}")
+        self.code = code
+
+
+class daeti_options(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
+        ("l_rounding", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("dt0", ctypes.c_double),
+        ("v_threshold", ctypes.c_double),
+        ("gate_rush_larsen", ctypes.c_int32),
+        ("bucket_k", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+        ("react_block", ctypes.c_int32),
+        ("diff_block", ctypes.c_int32),
+        ("fuse_diffusion", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+_SIGNATURES = {
+    "daeti_default_options": (None, [ctypes.POINTER(daeti_options)]),
+    "daeti_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(daeti_options)]),
+    "daeti_destroy": (ctypes.c_int, [_VP]),
+    "daeti_last_error": (ctypes.c_char_p, [_VP]),
+    "daeti_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "daeti_set_mesh_grid": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_double]),
+    "daeti_set_mesh_tet": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, ctypes.c_int64, _I64P]),
+    "daeti_set_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
+    "daeti_set_cell_model": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
+    "daeti_add_stimulus": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    "daeti_prepare": (ctypes.c_int, [_VP]),
+    "daeti_get_stability": (ctypes.c_int, [_VP, _DP, _DP, _IP, _IP, _DP]),
+    "daeti_get_sizes": (ctypes.c_int, [_VP, _I64P, _IP]),
+    "daeti_init_state": (ctypes.c_int, [_VP, _DP]),
+    "daeti_advance": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "daeti_synchronize": (ctypes.c_int, [_VP]),
+    "daeti_get_time": (ctypes.c_int, [_VP, _DP, _I64P]),
+    "daeti_read_v": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int]),
+    "daeti_read_activation": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int]),
+    "daeti_read_state": (ctypes.c_int, [_VP, _DP]),
+    "daeti_state_bytes": (ctypes.c_int, [_VP, _I64P]),
+    "daeti_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "daeti_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "daeti_get_substeps": (ctypes.c_int, [_VP, _I64P]),
+    "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
+    "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdaeti.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdaeti.so not built at {path}; run paper_2011_04747_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    return sorted(_SIGNATURES)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+class Solver:
+    """One tissue on the GPU: owns a ``daeti_ctx``.
+
+    Methods map one to one onto the C entry points of the same name.
+    """
+
+    def __init__(self, precision="fp32_kahan", scheme="daeti", dt=0.1, dt0=0.01, l_rounding="floor",
+                 v_threshold: Optional[float] = None, gate_rush_larsen=True, bucket_k=True, graph_steps=20,
+                 react_block=0, diff_block=0, fuse_diffusion=True, stream=None):
+        self.lib = load_library()
+        o = daeti_options()
+        self.lib.daeti_default_options(ctypes.byref(o))
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.scheme = _SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+        o.l_rounding = L_FLOOR if l_rounding == "floor" else L_CEIL
+        o.dt = float(dt)
+        o.dt0 = float(dt0)
+        o.v_threshold = float("nan") if v_threshold is None else float(v_threshold)
+        o.gate_rush_larsen = int(bool(gate_rush_larsen))
+        o.bucket_k = int(bool(bucket_k))
+        o.graph_steps = int(graph_steps)
+        o.react_block = int(react_block)
+        o.diff_block = int(diff_block)
+        o.fuse_diffusion = int(bool(fuse_diffusion))
+        self.options = o
+        self.precision = o.precision
+        h = _VP()
+        rc = self.lib.daeti_create(ctypes.byref(h), ctypes.byref(o))
+        if rc != OK:
+            raise DaetiError(rc, "daeti_create failed")
+        self.ctx = h
+        self.n_nodes = 0
+        self.n_states = 0
+        if stream is not None:
+            self.daeti_set_stream(stream)
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.daeti_last_error(self.ctx)
+            raise DaetiError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.daeti_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -----------------------------------------------------------
+    def daeti_set_stream(self, stream):
+        """stream: torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.daeti_set_stream(self.ctx, _VP(int(handle) if handle else 0)))
+
+    def daeti_set_mesh_grid(self, dim, n, h):
+        nn = _i64(list(n) + [1] * (3 - len(n)))
+        self._check(self.lib.daeti_set_mesh_grid(self.ctx, int(dim), _ptr(nn, ctypes.c_int64), float(h)))
+        self._sizes()
+
+    def daeti_set_mesh_tet(self, xyz, tets):
+        x = _f64(xyz)
+        t = _i64(tets)
+        self._check(self.lib.daeti_set_mesh_tet(self.ctx, x.shape[0], _ptr(x, ctypes.c_double), t.shape[0],
+                                                _ptr(t, ctypes.c_int64)))
+        self._sizes()
+
+    def daeti_set_conductivity(self, d_long, d_trans=None, fibre=None):
+        dl = _f64(d_long)
+        dtr = _f64(d_trans) if d_trans is not None else None
+        fb = _f64(fibre) if fibre is not None else None
+        self._check(self.lib.daeti_set_conductivity(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
+                                                    _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
+
+    def daeti_set_cell_model(self, model, params=()):
+        m = _MODEL[model] if isinstance(model, str) else int(model)
+        p = _f64(params) if len(params) else None
+        self._check(self.lib.daeti_set_cell_model(self.ctx, m, _ptr(p, ctypes.c_double), 0 if p is None else len(p)))
+        self._sizes()
+
+    def daeti_add_stimulus(self, nodes, t_start, duration, amplitude, period=0.0, count=1):
+        nd = _i64(nodes)
+        self._check(self.lib.daeti_add_stimulus(self.ctx, _ptr(nd, ctypes.c_int64), nd.shape[0], float(t_start),
+                                                float(duration), float(amplitude), float(period), int(count)))
+
+    def daeti_prepare(self):
+        self._check(self.lib.daeti_prepare(self.ctx))
+        self._sizes()
+
+    def daeti_get_stability(self):
+        dts, lam, dte = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        l, km = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.daeti_get_stability(self.ctx, ctypes.byref(dts), ctypes.byref(lam), ctypes.byref(l),
+                                                 ctypes.byref(km), ctypes.byref(dte)))
+        return {"dt_s": dts.value, "lambda_max": lam.value, "l": l.value, "k_max": km.value, "dt": dte.value}
+
+    def _sizes(self):
+        n = ctypes.c_int64()
+        s = ctypes.c_int()
+        if self.lib.daeti_get_sizes(self.ctx, ctypes.byref(n), ctypes.byref(s)) == OK:
+            self.n_nodes, self.n_states = n.value, s.value
+
+    def daeti_init_state(self, state=None):
+        st = None if state is None else _f64(state).reshape(-1)
+        self._check(self.lib.daeti_init_state(self.ctx, _ptr(st, ctypes.c_double)))
+
+    def daeti_advance(self, t_end):
+        self._check(self.lib.daeti_advance(self.ctx, float(t_end)))
+
+    def daeti_synchronize(self):
+        self._check(self.lib.daeti_synchronize(self.ctx))
+
+    def daeti_get_time(self):
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.daeti_get_time(self.ctx, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def _read(self, fn, out, dtype):
+        if out is not None and hasattr(out, "data_ptr"):           # torch tensor
+            if out.is_cuda:
+                dt = DTYPE_F32 if str(out.dtype) == "torch.float32" else DTYPE_F64
+                self._check(fn(self.ctx, _VP(out.data_ptr()), dt, 1))
+                return out
+            arr = out.numpy()
+            self._check(fn(self.ctx, arr.ctypes.data_as(_VP), DTYPE_F32 if arr.dtype == np.float32 else DTYPE_F64, 0))
+            return out
+        if out is None:
+            out = np.empty(self.n_nodes, dtype=np.dtype(dtype))
+        dt = DTYPE_F32 if out.dtype == np.float32 else DTYPE_F64
+        self._check(fn(self.ctx, out.ctypes.data_as(_VP), dt, 0))
+        return out
+
+    def daeti_read_v(self, out=None, dtype=np.float64):
+        return self._read(self.lib.daeti_read_v, out, dtype)
+
+    def daeti_read_activation(self, out=None, dtype=np.float64):
+        return self._read(self.lib.daeti_read_activation, out, dtype)
+
+    def daeti_read_state(self):
+        out = np.empty(self.n_states * self.n_nodes, dtype=np.float64)
+        self._check(self.lib.daeti_read_state(self.ctx, _ptr(out, ctypes.c_double)))
+        return out.reshape(self.n_states, self.n_nodes)
+
+    def daeti_save_state(self):
+        nb = ctypes.c_int64()
+        self._check(self.lib.daeti_state_bytes(self.ctx, ctypes.byref(nb)))
+        buf = np.empty(nb.value, dtype=np.uint8)
+        self._check(self.lib.daeti_save_state(self.ctx, buf.ctypes.data_as(_VP), nb.value))
+        return buf
+
+    def daeti_load_state(self, buf):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.daeti_load_state(self.ctx, b.ctypes.data_as(_VP), b.shape[0]))
+
+    def daeti_get_substeps(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.daeti_get_substeps(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def daeti_set_profiling(self, enable=True):
+        self._check(self.lib.daeti_set_profiling(self.ctx, int(bool(enable))))
+
+    def daeti_get_kernel_time(self, which):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.daeti_get_kernel_time(self.ctx, int(which), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def daeti_kernel_work(self, which):
+        b, f = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.daeti_kernel_work(self.ctx, int(which), ctypes.byref(b), ctypes.byref(f)))
+        return b.value, f.value
+
+    # -- convenience --------------------------------------------------------------
+    @property
+    def time(self):
+        return self.daeti_get_time()[0]
+
+
+def solver_from_workload(wl, **options) -> Solver:
+    """Build and prepare a Solver from a workload description.
+
+    ``wl`` needs the attributes of ``inputs.Workload`` (dim, n, h or xyz/tets,
+    d_long, d_trans, fibre, model, model_params, stimuli, dt, dt0,
+    v_threshold); the description is only copied into the library.
+    """
+    opts = dict(dt=wl.dt, dt0=wl.dt0, v_threshold=wl.v_threshold)
+    opts.update(options)
+    s = Solver(**opts)
+    if getattr(wl, "tets", None) is not None:
+        s.daeti_set_mesh_tet(wl.xyz, wl.tets)
+    else:
+        s.daeti_set_mesh_grid(wl.dim, wl.n, wl.h)
+    s.daeti_set_conductivity(wl.d_long, wl.d_trans, wl.fibre)
+    s.daeti_set_cell_model(wl.model, tuple(wl.model_params))
+    for st in wl.stimuli:
+        s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
+    s.daeti_prepare()
+    return s
+

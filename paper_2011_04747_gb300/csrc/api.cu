@@ -1,0 +1,975 @@
+// libdaeti C ABI: context, setup, the Strang-splitting scheduler of Eq. 2
+// (Section 2) and the read/checkpoint functions.  Host code only; all time
+// stepping runs in the kernels of reaction.cu / diffusion.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "../../include/daeti.h"
+#include "assembly.h"
+#include "kernels.h"
+
+using namespace daeti;
+
+struct StimHost {
+    std::vector<int64_t> nodes;
+    double t0, dur, amp, period;
+    int count;
+};
+
+struct daeti_ctx {
+    daeti_options opt;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool own_stream = false;
+    // inputs
+    int mesh_kind = 0;   // 1 grid, 2 tets
+    int dim = 0;
+    int64_t n[3] = {1, 1, 1};
+    double h = 0.0;
+    int64_t n_nodes = 0, n_elem = 0;
+    std::vector<double> xyz;
+    std::vector<int64_t> tets;
+    bool have_cond = false;
+    std::vector<double> dl, dtr, fib;
+    bool fib_null = true;
+    int model = 0;
+    std::vector<double> params;
+    std::vector<StimHost> stims;
+    // prepared
+    bool prepared = false;
+    DevState s;
+    DiffOp op;
+    ModelArgs margs;
+    SyncArgs sargs;
+    double dt_eff = 0.1, dt_s = 0.0, lam = 0.0, dt_ad = 0.0;
+    int l = 1, kmax = 1;
+    int64_t nstep = 0;
+    int cur = 0;
+    int par = 0;
+    void* scratch = nullptr;   // n doubles for conversions
+    std::vector<void*> allocs;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int g_steps = 0;
+    int g_par = 0;
+    // profiling
+    bool prof = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double ktime[3] = {0, 0, 0};
+    int64_t klaunch[3] = {0, 0, 0};
+};
+
+namespace {
+
+int fail(daeti_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? DAETI_ENOMEM : DAETI_ECUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+// Copies and fills on the context's stream, completed before returning (the
+// legacy default stream does not order against the library's streams).
+cudaError_t cpy_(daeti_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+cudaError_t set_(daeti_ctx* c, void* dst, int v, size_t bytes) {
+    cudaError_t e = cudaMemsetAsync(dst, v, bytes, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+int dalloc(daeti_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, DAETI_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return DAETI_OK;
+}
+
+void free_device(daeti_ctx* c) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->s = DevState();
+    c->op = DiffOp();
+    c->scratch = nullptr;
+    c->prepared = false;
+}
+
+size_t rsize(const daeti_ctx* c) { return c->s.prec == P_F64 ? 8 : 4; }
+
+int n_states_of(int model) { return model == DAETI_MODEL_MS ? 2 : 19; }
+
+// published initial states
+const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
+                              0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
+
+// host double -> device in state precision
+int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
+    if (c->s.prec == P_F64) {
+        CK(cpy_(c, dst, src, sizeof(double) * count, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> tmp(count);
+        for (int64_t i = 0; i < count; ++i) tmp[i] = (float)src[i];
+        CK(cpy_(c, dst, tmp.data(), sizeof(float) * count, cudaMemcpyHostToDevice));
+    }
+    return DAETI_OK;
+}
+
+StepRef plain_ref(int64_t n) { return StepRef{nullptr, (long long)n}; }
+
+// Launches of one Strang step (state at a synchronisation on entry and exit).
+void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed) {
+    const bool bucket = c->opt.bucket_k != 0 && c->sargs.adaptive;
+    int buf = c->cur;
+    auto tstart = [&](int) {
+        if (timed) cudaEventRecord(c->ev[0], st);
+    };
+    auto tstop = [&](int which) {
+        if (timed) {
+            cudaEventRecord(c->ev[1], st);
+            cudaEventSynchronize(c->ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+            c->ktime[which] += ms;
+            c->klaunch[which] += 1;
+        }
+    };
+    // step I (first diffusion half)
+    for (int i = 0; i < c->l; ++i) {
+        tstart(1);
+        launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, c->opt.diff_block, st);
+        tstop(1);
+        buf ^= 1;
+    }
+    // step II (reaction), nodes grouped by k
+    if (bucket) {
+        tstart(2);
+        launch_bucket_scatter(c->s, c->par, c->kmax, 256, st);
+        tstop(2);
+    }
+    tstart(0);
+    launch_reaction(c->s, c->margs, c->dt_eff, ref, bucket, buf, c->opt.react_block, st);
+    tstop(0);
+    // step III (second half), synchronisation at its end
+    for (int i = 0; i < c->l; ++i) {
+        const bool last = i == c->l - 1;
+        tstart(1);
+        launch_diffusion(c->s, c->op, buf, last, c->par ^ 1, c->sargs, ref, bucket, c->opt.diff_block, st);
+        tstop(1);
+        buf ^= 1;
+    }
+    if (bucket) c->par ^= 1;
+}
+
+int capture_graph(daeti_ctx* c) {
+    const int G = c->opt.graph_steps;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    const int par0 = c->par;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < G; ++j) enqueue_step(c, StepRef{c->s.step_ctr, (long long)j}, c->cap_stream, false);
+    launch_tick(c->s.step_ctr, G, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->par = par0;   // capture only recorded the launches
+    if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail(c, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    c->g_steps = G;
+    c->g_par = par0;
+    return DAETI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void daeti_default_options(daeti_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = (int32_t)sizeof(daeti_options);
+    o->precision = DAETI_FP32_KAHAN;
+    o->scheme = DAETI_SCHEME_DAETI;
+    o->l_rounding = DAETI_L_FLOOR;
+    o->dt = 0.1;
+    o->dt0 = 0.01;
+    o->v_threshold = std::numeric_limits<double>::quiet_NaN();
+    o->gate_rush_larsen = 1;
+    o->bucket_k = 1;
+    o->graph_steps = 20;
+    o->react_block = 0;
+    o->diff_block = 0;
+    o->fuse_diffusion = 1;
+}
+
+int daeti_create(daeti_ctx** out, const daeti_options* opt) {
+    daeti_ctx* c = nullptr;
+    if (!out) return DAETI_EINVAL;
+    *out = nullptr;
+    daeti_options o;
+    daeti_default_options(&o);
+    if (opt) {
+        if (opt->struct_size != (int32_t)sizeof(daeti_options)) return DAETI_EINVAL;
+        o = *opt;
+    }
+    if (!(o.dt > 0) || !(o.dt0 > 0) || o.precision < 0 || o.precision > 2 || o.scheme < 0 || o.scheme > 2 ||
+        o.l_rounding < 0 || o.l_rounding > 1 || o.graph_steps < 0)
+        return DAETI_EINVAL;
+    if (o.graph_steps % 2) o.graph_steps += 1;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DAETI_ECUDA;
+    c = new daeti_ctx();
+    c->opt = o;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return DAETI_ECUDA;
+    }
+    c->own_stream = true;
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&c->ev[i]);
+    *out = c;
+    return DAETI_OK;
+}
+
+int daeti_destroy(daeti_ctx* c) {
+    if (!c) return DAETI_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_device(c);
+    for (int i = 0; i < 4; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return DAETI_OK;
+}
+
+const char* daeti_last_error(const daeti_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int daeti_set_stream(daeti_ctx* c, void* stream) {
+    if (!c) return DAETI_EINVAL;
+    if (c->own_stream && c->stream) {
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+    }
+    c->own_stream = false;
+    c->stream = (cudaStream_t)stream;
+    return DAETI_OK;
+}
+
+int daeti_set_mesh_grid(daeti_ctx* c, int dim, const int64_t n[3], double h) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "mesh cannot change after prepare");
+    if ((dim != 2 && dim != 3) || !n || !(h > 0)) return fail(c, DAETI_EINVAL, "bad grid arguments");
+    for (int d = 0; d < dim; ++d)
+        if (n[d] < 2) return fail(c, DAETI_EINVAL, "grid needs >= 2 nodes per axis");
+    c->mesh_kind = 1;
+    c->dim = dim;
+    c->n[0] = n[0];
+    c->n[1] = n[1];
+    c->n[2] = dim == 3 ? n[2] : 1;
+    c->h = h;
+    c->n_nodes = c->n[0] * c->n[1] * c->n[2];
+    c->n_elem = (c->n[0] - 1) * (c->n[1] - 1) * (dim == 3 ? c->n[2] - 1 : 1);
+    if (c->n_nodes >= (int64_t)1 << 31) return fail(c, DAETI_EINVAL, "more than 2^31 - 1 nodes");
+    c->have_cond = false;
+    return DAETI_OK;
+}
+
+int daeti_set_mesh_tet(daeti_ctx* c, int64_t n_nodes, const double* xyz, int64_t n_tets, const int64_t* tets) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "mesh cannot change after prepare");
+    if (n_nodes < 4 || n_tets < 1 || !xyz || !tets) return fail(c, DAETI_EINVAL, "bad tet mesh arguments");
+    if (n_nodes >= (int64_t)1 << 31) return fail(c, DAETI_EINVAL, "more than 2^31 - 1 nodes");
+    for (int64_t e = 0; e < 4 * n_tets; ++e)
+        if (tets[e] < 0 || tets[e] >= n_nodes) return fail(c, DAETI_EINVAL, "tet node index out of range");
+    c->mesh_kind = 2;
+    c->dim = 3;
+    c->n_nodes = n_nodes;
+    c->n_elem = n_tets;
+    c->xyz.assign(xyz, xyz + 3 * n_nodes);
+    c->tets.assign(tets, tets + 4 * n_tets);
+    c->have_cond = false;
+    return DAETI_OK;
+}
+
+int daeti_set_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long, const double* d_trans,
+                           const double* fibre) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "conductivity cannot change after prepare");
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "set the mesh first");
+    if (n_elem != c->n_elem || !d_long) return fail(c, DAETI_EINVAL, "n_elem does not match the mesh");
+    for (int64_t e = 0; e < n_elem; ++e) {
+        const double a = d_long[e], b = d_trans ? d_trans[e] : d_long[e];
+        if (!(a >= 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b))
+            return fail(c, DAETI_EINVAL, "conductivities must be finite and >= 0");
+    }
+    c->dl.assign(d_long, d_long + n_elem);
+    c->dtr.assign(d_trans ? d_trans : d_long, (d_trans ? d_trans : d_long) + n_elem);
+    c->fib_null = fibre == nullptr;
+    if (fibre) c->fib.assign(fibre, fibre + 3 * n_elem);
+    else c->fib.clear();
+    c->have_cond = true;
+    return DAETI_OK;
+}
+
+int daeti_set_cell_model(daeti_ctx* c, int model, const double* params, int n_params) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "cell model cannot change after prepare");
+    if (model != DAETI_MODEL_MS && model != DAETI_MODEL_TP06) return fail(c, DAETI_EINVAL, "unknown cell model");
+    if (n_params < 0 || (n_params > 0 && !params)) return fail(c, DAETI_EINVAL, "bad parameters");
+    c->model = model;
+    c->params.assign(params, params + n_params);
+    if (model == DAETI_MODEL_MS && n_params != 0 && n_params != 5)
+        return fail(c, DAETI_EINVAL, "Mitchell-Schaeffer takes 5 parameters");
+    if (model == DAETI_MODEL_TP06 && n_params > 1) return fail(c, DAETI_EINVAL, "TP06 takes 1 parameter");
+    if (model == DAETI_MODEL_TP06 && n_params == 1 && (params[0] < 0 || params[0] > 2))
+        return fail(c, DAETI_EINVAL, "TP06 celltype must be 0, 1 or 2");
+    if (model == DAETI_MODEL_MS && n_params == 5)
+        for (int i = 0; i < 4; ++i)
+            if (!(params[i] > 0)) return fail(c, DAETI_EINVAL, "time constants must be > 0");
+    return DAETI_OK;
+}
+
+int daeti_add_stimulus(daeti_ctx* c, const int64_t* nodes, int64_t n_nodes, double t_start, double duration,
+                       double amplitude, double period, int count) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "stimuli cannot change after prepare");
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "set the mesh first");
+    if ((int)c->stims.size() >= DAETI_MAX_STIM) return fail(c, DAETI_EINVAL, "at most 32 stimuli");
+    if (n_nodes < 0 || (n_nodes > 0 && !nodes) || !(duration >= 0) || count < 1 || !std::isfinite(amplitude) ||
+        !std::isfinite(t_start) || (count > 1 && !(period > 0)))
+        return fail(c, DAETI_EINVAL, "bad stimulus arguments");
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (nodes[i] < 0 || nodes[i] >= c->n_nodes) return fail(c, DAETI_EINVAL, "stimulus node out of range");
+    StimHost sh;
+    sh.nodes.assign(nodes, nodes + n_nodes);
+    sh.t0 = t_start;
+    sh.dur = duration;
+    sh.amp = amplitude;
+    sh.period = count > 1 ? period : 0.0;
+    sh.count = count;
+    c->stims.push_back(sh);
+    return DAETI_OK;
+}
+
+// Power iteration for lambda_max of M_L^-1 K (self-adjoint in the M inner product).
+static int power_iteration(daeti_ctx* c, const EstOp& est, const double* d_m, double* lam_out) {
+    const int64_t n = est.n;
+    double *x = nullptr, *y = nullptr, *dots = nullptr;
+    CK(cudaMalloc(&x, sizeof(double) * n));
+    CK(cudaMalloc(&y, sizeof(double) * n));
+    CK(cudaMalloc(&dots, sizeof(double) * 2));
+    std::vector<double> hx(n);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (int64_t i = 0; i < n; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        const double u = (double)(st >> 11) * (1.0 / 9007199254740992.0);
+        double sgn = 1.0;
+        if (est.kind == 0) {
+            const int64_t xx = i % est.nx, yy = (i / est.nx) % est.ny, zz = i / ((int64_t)est.nx * est.ny);
+            sgn = ((xx + yy + zz) & 1) ? -1.0 : 1.0;
+            hx[i] = sgn * (1.0 + 0.1 * u);
+        } else {
+            hx[i] = u - 0.5;
+        }
+    }
+    cudaStream_t s = c->stream;
+    CK(cpy_(c, x, hx.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    double hd[2];
+    CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, s));
+    launch_mdots(n, d_m, x, x, dots, s);
+    CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launch_scale(n, x, 1.0 / std::sqrt(hd[1]), x, s);
+    double lam = 0.0, prev = 0.0;
+    for (int it = 0; it < 500; ++it) {
+        launch_apply_minvk(est, x, y, s);
+        CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, s));
+        launch_mdots(n, d_m, x, y, dots, s);
+        CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        lam = hd[0];
+        if (!(hd[1] > 0)) break;
+        launch_scale(n, y, 1.0 / std::sqrt(hd[1]), x, s);
+        if (it > 5 && std::fabs(lam - prev) <= 1e-8 * std::fabs(lam)) break;
+        prev = lam;
+    }
+    CK(cudaStreamSynchronize(s));
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(dots);
+    *lam_out = lam;
+    return DAETI_OK;
+}
+
+int daeti_prepare(daeti_ctx* c) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "already prepared");
+    if (!c->mesh_kind || !c->have_cond || !c->model)
+        return fail(c, DAETI_ESTATE, "prepare needs mesh, conductivity and cell model");
+    const int64_t N = c->n_nodes;
+    c->s = DevState();
+    c->s.prec = c->opt.precision == DAETI_FP64 ? P_F64 : P_F32;
+    c->s.kahan = c->opt.precision == DAETI_FP32_KAHAN;
+    c->s.n = N;
+    c->s.n_states = n_states_of(c->model);
+    const double* fib = c->fib_null ? nullptr : c->fib.data();
+
+    // ---- assembly and FP64 stable-step estimate
+    GridTable tab;
+    bool table = false;
+    CsrK K;
+    std::string err;
+    if (c->mesh_kind == 1) table = build_grid_table(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, tab);
+    if (!table) {
+        bool ok = c->mesh_kind == 1
+                      ? assemble_grid_csr(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, K, err)
+                      : assemble_tet_csr(N, c->xyz.data(), c->n_elem, c->tets.data(), c->dl.data(), c->dtr.data(),
+                                         fib, K, err);
+        if (!ok) return fail(c, DAETI_EINVAL, err);
+    }
+    EstOp est;
+    est.n = N;
+    std::vector<void*> tmp;
+    auto tmalloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    auto free_tmp = [&]() {
+        for (void* p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    Sell32 sell;
+    double* d_m = nullptr;
+    if (table) {
+        est.kind = 0;
+        est.dim = c->dim;
+        est.nx = tab.nx;
+        est.ny = tab.ny;
+        est.nz = tab.nz;
+        double* kt = (double*)tmalloc(tab.K.size() * 8);
+        double* mt = (double*)tmalloc(tab.m.size() * 8);
+        d_m = (double*)tmalloc(N * 8);
+        if (!kt || !mt || !d_m) {
+            free_tmp();
+            return fail(c, DAETI_ENOMEM, "estimator buffers");
+        }
+        cpy_(c, kt, tab.K.data(), tab.K.size() * 8, cudaMemcpyHostToDevice);
+        cpy_(c, mt, tab.m.data(), tab.m.size() * 8, cudaMemcpyHostToDevice);
+        est.ktab = kt;
+        est.mtab = mt;
+        launch_node_mass(est, d_m, c->stream);
+        est.m = d_m;
+    } else {
+        csr_to_sell32(K, nullptr, sell);
+        est.kind = 1;
+        est.n_chunks = sell.n_chunks;
+        int64_t* cp = (int64_t*)tmalloc(sell.chunk_ptr.size() * 8);
+        int* cw = (int*)tmalloc(sell.chunk_w.size() * 4);
+        int* col = (int*)tmalloc(sell.col.size() * 4);
+        double* kv = (double*)tmalloc(sell.val.size() * 8);
+        double* kd = (double*)tmalloc(N * 8);
+        d_m = (double*)tmalloc(N * 8);
+        if (!cp || !cw || !col || !kv || !kd || !d_m) {
+            free_tmp();
+            return fail(c, DAETI_ENOMEM, "estimator buffers");
+        }
+        cpy_(c, cp, sell.chunk_ptr.data(), sell.chunk_ptr.size() * 8, cudaMemcpyHostToDevice);
+        cpy_(c, cw, sell.chunk_w.data(), sell.chunk_w.size() * 4, cudaMemcpyHostToDevice);
+        cpy_(c, col, sell.col.data(), sell.col.size() * 4, cudaMemcpyHostToDevice);
+        cpy_(c, kv, sell.val.data(), sell.val.size() * 8, cudaMemcpyHostToDevice);
+        cpy_(c, kd, sell.diag.data(), N * 8, cudaMemcpyHostToDevice);
+        cpy_(c, d_m, K.m.data(), N * 8, cudaMemcpyHostToDevice);
+        est.chunk_ptr = cp;
+        est.chunk_w = cw;
+        est.col = col;
+        est.kval = kv;
+        est.kdiag = kd;
+        est.m = d_m;
+    }
+    {
+        unsigned long long* bits = (unsigned long long*)tmalloc(8);
+        if (!bits) {
+            free_tmp();
+            return fail(c, DAETI_ENOMEM, "estimator buffers");
+        }
+        const double big = 1e300;
+        unsigned long long hb;
+        std::memcpy(&hb, &big, 8);
+        cpy_(c, bits, &hb, 8, cudaMemcpyHostToDevice);
+        launch_gershgorin(est, bits, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            free_tmp();
+            return fail(c, DAETI_ECUDA, std::string("gershgorin: ") + cudaGetErrorString(e));
+        }
+        cpy_(c, &hb, bits, 8, cudaMemcpyDeviceToHost);
+        double mn;
+        std::memcpy(&mn, &hb, 8);
+        c->dt_s = 0.9 * mn;
+    }
+    {
+        int rc = power_iteration(c, est, d_m, &c->lam);
+        if (rc) {
+            free_tmp();
+            return rc;
+        }
+    }
+    free_tmp();
+
+    // ---- scheme: effective dt, l, k_max (Section 2, Section 3)
+    double dt = c->opt.dt;
+    const bool no_diff = !(c->dt_s < 1e299);   // all-zero conductivity
+    if (c->opt.scheme == DAETI_SCHEME_DAETI) {
+        c->l = 1;
+        if (!no_diff && dt / 2.0 > c->dt_s) {
+            const double x = dt / (2.0 * c->dt_s);
+            c->l = c->opt.l_rounding == DAETI_L_FLOOR ? (int)std::floor(x) : (int)std::ceil(x);
+        }
+        c->kmax = std::max(1, (int)std::floor(dt / c->opt.dt0 + 1e-9));
+        c->sargs.adaptive = 1;
+    } else if (c->opt.scheme == DAETI_SCHEME_OSTAR) {
+        if (!no_diff && c->dt_s < dt) dt = dt / std::ceil(dt / c->dt_s - 1e-12);
+        c->l = 1;
+        c->kmax = std::max(1, (int)std::floor(dt / c->opt.dt0 + 1e-9));
+        c->sargs.adaptive = 1;
+    } else {
+        c->l = 1;
+        c->kmax = 1;
+        c->sargs.adaptive = 0;
+    }
+    if (c->kmax >= DAETI_MAX_K) return fail(c, DAETI_EINVAL, "k_max = floor(dt/dt0) must be < 16");
+    c->dt_eff = dt;
+    c->dt_ad = dt / (2.0 * c->l);
+    if (c->dt_ad * c->lam >= 2.0)
+        return fail(c, DAETI_EUNSTABLE, "dt_ad * lambda_max >= 2: explicit diffusion would diverge");
+
+    // ---- device state
+    const size_t R = rsize(c);
+    int rc = 0;
+    void* p = nullptr;
+    if ((rc = dalloc(c, &c->s.V[0], R * N)) || (rc = dalloc(c, &c->s.V[1], R * N))) return rc;
+    if (c->s.kahan) {
+        if ((rc = dalloc(c, &p, 4 * N))) return rc;
+        c->s.C[0] = (float*)p;
+        if ((rc = dalloc(c, &p, 4 * N))) return rc;
+        c->s.C[1] = (float*)p;
+    }
+    if ((rc = dalloc(c, &c->s.S, R * N * (c->s.n_states - 1)))) return rc;
+    if ((rc = dalloc(c, &c->s.vsync, R * N)) || (rc = dalloc(c, &c->s.act, R * N))) return rc;
+    if ((rc = dalloc(c, &p, N))) return rc;
+    c->s.kk = (uint8_t*)p;
+    if ((rc = dalloc(c, &p, 4 * N))) return rc;
+    c->s.perm = (int*)p;
+    if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
+    c->s.counts = (int*)p;
+    if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
+    c->s.cursor = (int*)p;
+    if ((rc = dalloc(c, &p, 8))) return rc;
+    c->s.step_ctr = (long long*)p;
+    if ((rc = dalloc(c, &p, 16))) return rc;
+    c->s.flags = (int*)p;
+    if ((rc = dalloc(c, &p, 8))) return rc;
+    c->s.substeps = (unsigned long long*)p;
+    if ((rc = dalloc(c, &c->scratch, 8 * N))) return rc;
+    if (!c->stims.empty()) {
+        std::vector<unsigned> mask(N, 0u);
+        std::vector<StimDev> sd(c->stims.size());
+        for (size_t k = 0; k < c->stims.size(); ++k) {
+            for (int64_t v : c->stims[k].nodes) mask[v] |= 1u << k;
+            sd[k].t0 = c->stims[k].t0;
+            sd[k].dur = c->stims[k].dur;
+            sd[k].amp = c->stims[k].amp;
+            sd[k].period = c->stims[k].period;
+            sd[k].reps = c->stims[k].count;
+            sd[k].pad = 0;
+        }
+        if ((rc = dalloc(c, &p, 4 * N))) return rc;
+        c->s.stim_mask = (unsigned*)p;
+        CK(cpy_(c, p, mask.data(), 4 * N, cudaMemcpyHostToDevice));
+        if ((rc = dalloc(c, &p, sizeof(StimDev) * sd.size()))) return rc;
+        c->s.stims = (StimDev*)p;
+        CK(cpy_(c, p, sd.data(), sizeof(StimDev) * sd.size(), cudaMemcpyHostToDevice));
+        c->s.n_stims = (int)sd.size();
+    }
+
+    // ---- time-stepping operator a_ij = dt_ad k_ij / m_i in state precision
+    c->op = DiffOp();
+    if (table) {
+        c->op.kind = 0;
+        c->op.dim = c->dim;
+        c->op.nx = tab.nx;
+        c->op.ny = tab.ny;
+        c->op.nz = tab.nz;
+        std::vector<double> A(tab.K.size(), 0.0);
+        const int self = c->dim == 3 ? 13 : 4;
+        for (size_t cls = 0; cls < tab.m.size(); ++cls)
+            for (int j = 0; j < 27; ++j)
+                if (j != self) A[cls * 27 + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
+        if ((rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
+        if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
+    } else {
+        std::vector<double> scale(N);
+        for (int64_t i = 0; i < N; ++i) scale[i] = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
+        Sell32 sa;
+        csr_to_sell32(K, scale.data(), sa);
+        c->op.kind = 1;
+        c->op.n_chunks = sa.n_chunks;
+        c->op.nnz_padded = (int64_t)sa.col.size();
+        if ((rc = dalloc(c, &p, sa.chunk_ptr.size() * 8))) return rc;
+        c->op.chunk_ptr = (int64_t*)p;
+        CK(cpy_(c, p, sa.chunk_ptr.data(), sa.chunk_ptr.size() * 8, cudaMemcpyHostToDevice));
+        if ((rc = dalloc(c, &p, sa.chunk_w.size() * 4))) return rc;
+        c->op.chunk_w = (int*)p;
+        CK(cpy_(c, p, sa.chunk_w.data(), sa.chunk_w.size() * 4, cudaMemcpyHostToDevice));
+        if ((rc = dalloc(c, &p, sa.col.size() * 4))) return rc;
+        c->op.col = (int*)p;
+        CK(cpy_(c, p, sa.col.data(), sa.col.size() * 4, cudaMemcpyHostToDevice));
+        if ((rc = dalloc(c, &c->op.val, R * sa.val.size()))) return rc;
+        if ((rc = upload_real(c, c->op.val, sa.val.data(), (int64_t)sa.val.size()))) return rc;
+    }
+
+    // ---- model and synchronisation arguments
+    c->margs = ModelArgs();
+    c->margs.model = c->model == DAETI_MODEL_MS ? M_MS : M_TP06;
+    if (c->model == DAETI_MODEL_MS && c->params.size() == 5)
+        for (int i = 0; i < 5; ++i) c->margs.ms[i] = c->params[i];
+    if (c->model == DAETI_MODEL_TP06 && c->params.size() == 1) c->margs.celltype = (int)c->params[0];
+    c->margs.gate_rl = c->opt.gate_rush_larsen ? 1 : 0;
+    c->sargs.dt = c->dt_eff;
+    c->sargs.vscale = c->model == DAETI_MODEL_MS ? 100.0 : 1.0;
+    c->sargs.vth = std::isnan(c->opt.v_threshold) ? (c->model == DAETI_MODEL_MS ? 0.5 : -40.0) : c->opt.v_threshold;
+    c->sargs.kmax = c->kmax;
+    c->prepared = true;
+    return daeti_init_state(c, nullptr);
+}
+
+int daeti_get_stability(daeti_ctx* c, double* dt_s, double* lambda_max, int* l, int* k_max, double* dt_eff) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (dt_s) *dt_s = c->dt_s;
+    if (lambda_max) *lambda_max = c->lam;
+    if (l) *l = c->l;
+    if (k_max) *k_max = c->kmax;
+    if (dt_eff) *dt_eff = c->dt_eff;
+    return DAETI_OK;
+}
+
+int daeti_get_sizes(daeti_ctx* c, int64_t* n_nodes, int* n_states) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "no mesh");
+    if (n_nodes) *n_nodes = c->n_nodes;
+    if (n_states) *n_states = c->model ? n_states_of(c->model) : 0;
+    return DAETI_OK;
+}
+
+int daeti_init_state(daeti_ctx* c, const double* state) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    const int64_t N = c->n_nodes;
+    const int ns = c->s.n_states;
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> host;
+    if (!state) {
+        host.resize((size_t)ns * N);
+        for (int k = 0; k < ns; ++k) {
+            double v = c->model == DAETI_MODEL_MS ? (k == 0 ? 0.0 : 1.0) : TP06_INIT[k];
+            std::fill(host.begin() + (size_t)k * N, host.begin() + (size_t)(k + 1) * N, v);
+        }
+        state = host.data();
+    }
+    for (int64_t i = 0; i < (int64_t)ns * N; ++i)
+        if (!std::isfinite(state[i])) return fail(c, DAETI_EINVAL, "state must be finite");
+    const size_t R = rsize(c);
+    int rc;
+    if ((rc = upload_real(c, c->s.V[0], state, N))) return rc;
+    if ((rc = upload_real(c, c->s.vsync, state, N))) return rc;
+    if ((rc = upload_real(c, c->s.S, state + N, (int64_t)(ns - 1) * N))) return rc;
+    if (c->s.kahan) {
+        CK(set_(c, c->s.C[0], 0, 4 * N));
+        CK(set_(c, c->s.C[1], 0, 4 * N));
+    }
+    std::vector<double> neg(N, -1.0);
+    if ((rc = upload_real(c, c->s.act, neg.data(), N))) return rc;
+    CK(set_(c, c->s.kk, 1, N));
+    std::vector<int> cnt(2 * DAETI_MAX_K, 0);
+    cnt[1] = (int)N;
+    CK(cpy_(c, c->s.counts, cnt.data(), 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
+    CK(set_(c, c->s.cursor, 0, 4 * 2 * DAETI_MAX_K));
+    CK(set_(c, c->s.flags, 0, 16));
+    CK(set_(c, c->s.step_ctr, 0, 8));
+    CK(set_(c, c->s.substeps, 0, 8));
+    (void)R;
+    c->nstep = 0;
+    c->cur = 0;
+    c->par = 0;
+    return DAETI_OK;
+}
+
+int daeti_advance(daeti_ctx* c, double t_end) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (!std::isfinite(t_end)) return fail(c, DAETI_EINVAL, "t_end must be finite");
+    const double steps_f = t_end / c->dt_eff;
+    const int64_t target = (int64_t)std::llround(steps_f);
+    if (std::fabs((double)target * c->dt_eff - t_end) > 1e-9 * std::max(1.0, std::fabs(t_end)))
+        return fail(c, DAETI_EINVAL, "t_end is not a whole number of steps");
+    if (target < c->nstep) return fail(c, DAETI_EINVAL, "t_end is before the current time");
+    int64_t remaining = target - c->nstep;
+    cudaStream_t st = c->stream;
+    const int G = c->opt.graph_steps;
+    if (!c->prof && G > 0 && remaining >= G) {
+        if (!c->gexec || c->g_steps != G) {
+            int rc = capture_graph(c);
+            if (rc) return rc;
+        }
+        if (c->par != c->g_par) {
+            enqueue_step(c, plain_ref(c->nstep), st, false);
+            c->nstep++;
+            remaining--;
+        }
+        if (remaining >= G) {
+            launch_set_counter(c->s.step_ctr, c->nstep, st);
+            while (remaining >= G) {
+                CK(cudaGraphLaunch(c->gexec, st));
+                c->nstep += G;
+                remaining -= G;
+            }
+        }
+    }
+    while (remaining > 0) {
+        enqueue_step(c, plain_ref(c->nstep), st, c->prof);
+        c->nstep++;
+        remaining--;
+    }
+    CK(cudaGetLastError());
+    return DAETI_OK;
+}
+
+int daeti_synchronize(daeti_ctx* c) {
+    if (!c) return DAETI_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->prepared) {
+        int f[4];
+        CK(cpy_(c, f, c->s.flags, 16, cudaMemcpyDeviceToHost));
+        if (f[0]) return fail(c, DAETI_ENONFINITE, "V became non-finite");
+        if (f[1]) return fail(c, DAETI_ETIMEOUT, "a bounded device wait gave up");
+    }
+    return DAETI_OK;
+}
+
+int daeti_get_time(daeti_ctx* c, double* t, int64_t* n_steps) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (t) *t = (double)c->nstep * c->dt_eff;
+    if (n_steps) *n_steps = c->nstep;
+    return DAETI_OK;
+}
+
+static int read_array(daeti_ctx* c, const void* src, const float* comp, void* out, int dtype, int on_device) {
+    if (!out || (dtype != DAETI_DTYPE_F64 && dtype != DAETI_DTYPE_F32)) return fail(c, DAETI_EINVAL, "bad output");
+    const int64_t N = c->n_nodes;
+    const size_t ob = dtype == DAETI_DTYPE_F64 ? 8 : 4;
+    if (on_device) {
+        launch_convert(src, c->s.prec, comp, out, dtype == DAETI_DTYPE_F32, N, c->stream);
+        CK(cudaGetLastError());
+        return DAETI_OK;
+    }
+    launch_convert(src, c->s.prec, comp, c->scratch, dtype == DAETI_DTYPE_F32, N, c->stream);
+    CK(cudaMemcpyAsync(out, c->scratch, ob * N, cudaMemcpyDeviceToHost, c->stream));
+    return daeti_synchronize(c);
+}
+
+int daeti_read_v(daeti_ctx* c, void* out, int dtype, int on_device) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    return read_array(c, c->s.V[c->cur], c->s.kahan ? c->s.C[c->cur] : nullptr, out, dtype, on_device);
+}
+
+int daeti_read_activation(daeti_ctx* c, void* out, int dtype, int on_device) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    return read_array(c, c->s.act, nullptr, out, dtype, on_device);
+}
+
+int daeti_read_state(daeti_ctx* c, double* out) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (!out) return fail(c, DAETI_EINVAL, "null output");
+    const int64_t N = c->n_nodes;
+    int rc = daeti_read_v(c, out, DAETI_DTYPE_F64, 0);
+    if (rc) return rc;
+    for (int k = 1; k < c->s.n_states; ++k) {
+        const char* src = (const char*)c->s.S + (size_t)(k - 1) * N * rsize(c);
+        launch_convert(src, c->s.prec, nullptr, c->scratch, 0, N, c->stream);
+        CK(cudaMemcpyAsync(out + (size_t)k * N, c->scratch, 8 * N, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return DAETI_OK;
+}
+
+// checkpoint layout: header (8 int64) | V | C | S | vsync | act | kk | counts | cursor
+static int64_t ckpt_bytes(const daeti_ctx* c) {
+    const int64_t N = c->n_nodes;
+    const int64_t R = (int64_t)rsize(c);
+    int64_t b = 64 + R * N;
+    if (c->s.kahan) b += 4 * N;
+    b += R * N * (c->s.n_states - 1) + 2 * R * N + N + 2 * 4 * 2 * DAETI_MAX_K;
+    return b;
+}
+
+int daeti_state_bytes(daeti_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    *bytes = ckpt_bytes(c);
+    return DAETI_OK;
+}
+
+int daeti_save_state(daeti_ctx* c, void* buf, int64_t buf_bytes) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (!buf || buf_bytes < ckpt_bytes(c)) return fail(c, DAETI_EINVAL, "checkpoint buffer too small");
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t N = c->n_nodes, R = (int64_t)rsize(c);
+    char* p = (char*)buf;
+    int64_t hdr[8] = {0x444145544931LL, N, c->s.n_states, c->s.prec, c->s.kahan, c->nstep, c->par, 0};
+    std::memcpy(p, hdr, 64);
+    p += 64;
+    CK(cpy_(c, p, c->s.V[c->cur], R * N, cudaMemcpyDeviceToHost));
+    p += R * N;
+    if (c->s.kahan) {
+        CK(cpy_(c, p, c->s.C[c->cur], 4 * N, cudaMemcpyDeviceToHost));
+        p += 4 * N;
+    }
+    CK(cpy_(c, p, c->s.S, R * N * (c->s.n_states - 1), cudaMemcpyDeviceToHost));
+    p += R * N * (c->s.n_states - 1);
+    CK(cpy_(c, p, c->s.vsync, R * N, cudaMemcpyDeviceToHost));
+    p += R * N;
+    CK(cpy_(c, p, c->s.act, R * N, cudaMemcpyDeviceToHost));
+    p += R * N;
+    CK(cpy_(c, p, c->s.kk, N, cudaMemcpyDeviceToHost));
+    p += N;
+    CK(cpy_(c, p, c->s.counts, 4 * 2 * DAETI_MAX_K, cudaMemcpyDeviceToHost));
+    p += 4 * 2 * DAETI_MAX_K;
+    CK(cpy_(c, p, c->s.cursor, 4 * 2 * DAETI_MAX_K, cudaMemcpyDeviceToHost));
+    return DAETI_OK;
+}
+
+int daeti_load_state(daeti_ctx* c, const void* buf, int64_t buf_bytes) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (!buf || buf_bytes < ckpt_bytes(c)) return fail(c, DAETI_EINVAL, "checkpoint buffer too small");
+    const int64_t N = c->n_nodes, R = (int64_t)rsize(c);
+    const char* p = (const char*)buf;
+    int64_t hdr[8];
+    std::memcpy(hdr, p, 64);
+    if (hdr[0] != 0x444145544931LL || hdr[1] != N || hdr[2] != c->s.n_states || hdr[3] != c->s.prec ||
+        hdr[4] != (int64_t)c->s.kahan)
+        return fail(c, DAETI_EINVAL, "checkpoint does not match this context");
+    CK(cudaStreamSynchronize(c->stream));
+    p += 64;
+    c->cur = 0;
+    CK(cpy_(c, c->s.V[0], p, R * N, cudaMemcpyHostToDevice));
+    p += R * N;
+    if (c->s.kahan) {
+        CK(cpy_(c, c->s.C[0], p, 4 * N, cudaMemcpyHostToDevice));
+        p += 4 * N;
+    }
+    CK(cpy_(c, c->s.S, p, R * N * (c->s.n_states - 1), cudaMemcpyHostToDevice));
+    p += R * N * (c->s.n_states - 1);
+    CK(cpy_(c, c->s.vsync, p, R * N, cudaMemcpyHostToDevice));
+    p += R * N;
+    CK(cpy_(c, c->s.act, p, R * N, cudaMemcpyHostToDevice));
+    p += R * N;
+    CK(cpy_(c, c->s.kk, p, N, cudaMemcpyHostToDevice));
+    p += N;
+    CK(cpy_(c, c->s.counts, p, 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
+    p += 4 * 2 * DAETI_MAX_K;
+    CK(cpy_(c, c->s.cursor, p, 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
+    CK(set_(c, c->s.flags, 0, 16));
+    c->nstep = hdr[5];
+    c->par = (int)hdr[6];
+    return DAETI_OK;
+}
+
+int daeti_get_substeps(daeti_ctx* c, int64_t* total) {
+    if (!c || !total) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    unsigned long long v = 0;
+    CK(cpy_(c, &v, c->s.substeps, 8, cudaMemcpyDeviceToHost));
+    *total = (int64_t)v;
+    return DAETI_OK;
+}
+
+int daeti_set_profiling(daeti_ctx* c, int enable) {
+    if (!c) return DAETI_EINVAL;
+    c->prof = enable != 0;
+    for (int i = 0; i < 3; ++i) {
+        c->ktime[i] = 0.0;
+        c->klaunch[i] = 0;
+    }
+    return DAETI_OK;
+}
+
+int daeti_get_kernel_time(daeti_ctx* c, int which, double* total_ms, int64_t* launches) {
+    if (!c || which < 0 || which > 2) return DAETI_EINVAL;
+    if (total_ms) *total_ms = c->ktime[which];
+    if (launches) *launches = c->klaunch[which];
+    return DAETI_OK;
+}
+
+int daeti_kernel_work(daeti_ctx* c, int which, double* bytes, double* flops) {
+    if (!c || which < 0 || which > 2) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    const double N = (double)c->n_nodes, R = (double)rsize(c);
+    const double comp = c->s.kahan ? 8.0 : 0.0;
+    double b = 0.0, f = 0.0;
+    if (which == 0) {
+        // every state read and written once per step A, k read, perm read
+        b = N * (2.0 * R * c->s.n_states + comp + 1.0 + (c->opt.bucket_k ? 4.0 : 0.0));
+        f = 0.0;   // sub-step counts are data dependent; the bench counts them
+    } else if (which == 1) {
+        // V read + written per sub-step (+ Kahan term); neighbours come from cache
+        b = N * (2.0 * R + comp);
+        if (c->op.kind == 1) b += (double)c->op.nnz_padded * (R + 4.0);
+        f = N * 2.0 * (c->op.kind == 0 ? (c->dim == 3 ? 26.0 : 8.0) : 15.0);
+    } else {
+        b = N * (1.0 + 4.0);
+    }
+    if (bytes) *bytes = b;
+    if (flops) *flops = f;
+    return DAETI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device-side shared definitions of libdaeti: parameter blocks, precision
+// helpers, the synchronisation epilogue run at t_n = n*dt (activation time,
+// next k, V(t_n) bookkeeping) and warp-aggregated bucket counting.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define DAETI_MAX_STIM 32
+#define DAETI_MAX_K 16
+
+namespace daeti {
+
+// Step index n of a launch: graph replays read a device counter and add
+// their offset inside the graph; plain launches pass the absolute index.
+struct StepRef {
+    const long long* base;
+    long long off;
+};
+
+__device__ __forceinline__ long long step_index(const StepRef& s) {
+    return (s.base ? *s.base : 0LL) + s.off;
+}
+
+// One stimulus (Section 3: 1-2 ms current at a node set; S1-S2 protocols).
+struct StimDev {
+    double t0, dur, amp, period;
+    int reps;
+    int pad;
+};
+
+// True if the stimulus is on at sub-step start time t (1e-9 ms guard).
+__device__ __forceinline__ bool stim_on(const StimDev& s, double t) {
+    for (int p = 0; p < s.reps; ++p) {
+        double a = s.t0 + p * s.period;
+        if (t >= a - 1e-9 && t < a + s.dur - 1e-9) return true;
+    }
+    return false;
+}
+
+// True if the stimulus is on at some instant of [t0, t1).
+__device__ __forceinline__ bool stim_overlaps(const StimDev& s, double t0, double t1) {
+    for (int p = 0; p < s.reps; ++p) {
+        double a = s.t0 + p * s.period - 1e-9;
+        double b = s.t0 + p * s.period + s.dur - 1e-9;
+        if (a < t1 && b > t0) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- precision
+template <typename R> struct Fm;
+template <> struct Fm<float> {
+    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+    static __device__ __forceinline__ float lg(float x) { return __logf(x); }
+    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
+};
+template <> struct Fm<double> {
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double lg(double x) { return log(x); }
+    static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double em1(double x) { return expm1(x); }
+};
+
+// v += d with optional Kahan compensation c (true value ~= v - c).
+template <typename R>
+__device__ __forceinline__ void add_comp(R& v, float* c, R d) {
+    if (c) {
+        R y = d - (R)(*c);
+        R t = v + y;
+        *c = (float)((t - v) - y);
+        v = t;
+    } else {
+        v += d;
+    }
+}
+
+// ------------------------------------------------------------ sync epilogue
+// Parameters of the synchronisation at t_{n+1} = (n+1) dt, run on V(t_{n+1})
+// right after the first diffusion half that ends there.
+template <typename R>
+struct SyncParams {
+    R* vsync;          // V at the previous synchronisation, updated in place
+    uint8_t* kk;       // sub-step count of the next step A
+    R* act;            // activation times (-1 = not yet)
+    int* counts;       // per-k node counts for the bucketing (nullable)
+    int* flags;        // flags[0] |= 1 on non-finite V
+    double dt;
+    R vscale;          // model units -> mV for the k rule
+    R vth;             // activation threshold
+    int kmax;
+    int adaptive;      // 0: k = 1 (OST)
+    StepRef step;      // step n whose second half ends at this synchronisation
+};
+
+// Section 2's k rule from the rate of the split solution over the last step
+// (reading R-k) and the first-upward-crossing activation time (R-LAT).
+template <typename R>
+__device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) {
+    R vold = p.vsync[i];
+    int k = 1;
+    if (p.adaptive) {
+        R rate = ((vnew - vold) / (R)p.dt) * p.vscale;
+        int k0 = rate > (R)0 ? 5 : 1;
+        R a = fabs(rate);
+        a = a < (R)1e6 ? a : (R)1e6;          // also maps NaN to 1e6
+        k = k0 + (int)floor(a);
+        k = k < p.kmax ? k : p.kmax;
+    }
+    p.kk[i] = (uint8_t)k;
+    R a0 = p.act[i];
+    if (a0 < (R)0 && vold < p.vth && vnew >= p.vth) {
+        double tprev = (double)step_index(p.step) * p.dt;
+        p.act[i] = (R)(tprev + p.dt * (double)((p.vth - vold) / (vnew - vold)));
+    }
+    p.vsync[i] = vnew;
+    if (!isfinite((double)vnew)) atomicOr(p.flags, 1);
+    return k;
+}
+
+// Warp-aggregated histogram of k into a shared array (lanes with k <= 0 skip).
+__device__ __forceinline__ void warp_count(int* sh_hist, int k, bool valid) {
+    unsigned active = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    unsigned peers = __match_any_sync(active, k);
+    int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&sh_hist[k], __popc(peers));
+}
+
+}  // namespace daeti

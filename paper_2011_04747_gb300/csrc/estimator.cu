@@ -1,0 +1,206 @@
+// FP64 stable-step estimator: Eq. 3's Gershgorin bound
+//   dt_s = 0.9 min_i m_ii / (k_ii + sum_{j != i} |k_ij|)
+// as a grid-wide min-reduction over rows, and the building blocks of a power
+// iteration for lambda_max(M_L^-1 K) (apply, M-weighted dot products,
+// scaling).  Also the state/dtype conversion used by the read functions.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace daeti {
+
+__device__ __forceinline__ void class_of(int i, int nx, int ny, int& x, int& y, int& z, int& cls) {
+    x = i % nx;
+    const int yz = i / nx;
+    y = yz % ny;
+    z = yz / ny;
+    const int cx = x == 0 ? 0 : (x == nx - 1 ? 2 : 1);
+    const int cy = y == 0 ? 0 : (y == ny - 1 ? 2 : 1);
+    cls = (z * 3 + cy) * 3 + cx;
+}
+
+// Non-negative doubles order like their bit patterns, so an integer atomicMin works.
+__device__ __forceinline__ void block_min_to(double v, unsigned long long* out) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 1e300;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) atomicMin(out, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+__global__ void gersh_table_kernel(EstOp op, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 1e300;
+    if (i < op.n) {
+        int x, y, z, cls;
+        class_of(i, op.nx, op.ny, x, y, z, cls);
+        const double* kr = op.ktab + (size_t)cls * 27;
+        const int self = op.dim == 3 ? 13 : 4;
+        double s = kr[self];
+        for (int j = 0; j < 27; ++j)
+            if (j != self) s += fabs(kr[j]);
+        if (s > 0.0) v = op.mtab[cls] / s;
+    }
+    block_min_to(v, out);
+}
+
+__global__ void gersh_sell_kernel(EstOp op, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 1e300;
+    if (i < op.n) {
+        const int chunk = i >> 5, lane = i & 31;
+        const int64_t off = op.chunk_ptr[chunk] + lane;
+        double s = op.kdiag[i];
+        for (int j = 0; j < op.chunk_w[chunk]; ++j) s += fabs(op.kval[off + 32 * (int64_t)j]);
+        if (s > 0.0) v = op.m[i] / s;
+    }
+    block_min_to(v, out);
+}
+
+void launch_gershgorin(const EstOp& op, unsigned long long* out_bits, cudaStream_t st) {
+    const int block = 256;
+    const int grid = (int)((op.n + block - 1) / block);
+    if (op.kind == 0)
+        gersh_table_kernel<<<grid, block, 0, st>>>(op, out_bits);
+    else
+        gersh_sell_kernel<<<grid, block, 0, st>>>(op, out_bits);
+}
+
+// y = M_L^-1 K x in FP64.
+__global__ void apply_table_kernel(EstOp op, const double* __restrict__ x, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= op.n) return;
+    int cx_, cy_, z, cls;
+    class_of(i, op.nx, op.ny, cx_, cy_, z, cls);
+    const int cx = cx_ == 0 ? 0 : (cx_ == op.nx - 1 ? 2 : 1);
+    const int cy = cy_ == 0 ? 0 : (cy_ == op.ny - 1 ? 2 : 1);
+    const double* kr = op.ktab + (size_t)cls * 27;
+    const int nxy = op.nx * op.ny;
+    double acc = 0.0;
+    const int zlo = op.dim == 3 ? -1 : 0, zhi = op.dim == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const bool ok = (dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
+                                (dy <= 0 || cy < 2) && (dz >= 0 || z > 0) && (dz <= 0 || z < op.nz - 1);
+                if (!ok) continue;
+                const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                acc += kr[j] * x[i + dx + dy * op.nx + dz * nxy];
+            }
+    y[i] = acc / op.mtab[cls];
+}
+
+__global__ void apply_sell_kernel(EstOp op, const double* __restrict__ x, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= op.n) return;
+    const int chunk = i >> 5, lane = i & 31;
+    const int64_t off = op.chunk_ptr[chunk] + lane;
+    double acc = op.kdiag[i] * x[i];
+    for (int j = 0; j < op.chunk_w[chunk]; ++j) {
+        const int64_t e = off + 32 * (int64_t)j;
+        acc += op.kval[e] * x[op.col[e]];
+    }
+    y[i] = acc / op.m[i];
+}
+
+void launch_apply_minvk(const EstOp& op, const double* x, double* y, cudaStream_t st) {
+    const int block = 256;
+    const int grid = (int)((op.n + block - 1) / block);
+    if (op.kind == 0)
+        apply_table_kernel<<<grid, block, 0, st>>>(op, x, y);
+    else
+        apply_sell_kernel<<<grid, block, 0, st>>>(op, x, y);
+}
+
+// out2[0] += sum m x y, out2[1] += sum m y y
+__global__ void mdots_kernel(int64_t n, const double* __restrict__ m, const double* __restrict__ x,
+                             const double* __restrict__ y, double* out2) {
+    __shared__ double sh[2][32];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a += m[i] * x[i] * y[i];
+        b += m[i] * y[i] * y[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < (int)(blockDim.x >> 5) ? sh[0][lane] : 0.0;
+        b = lane < (int)(blockDim.x >> 5) ? sh[1][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&out2[0], a);
+            atomicAdd(&out2[1], b);
+        }
+    }
+}
+
+void launch_mdots(int64_t n, const double* m, const double* x, const double* y, double* out2, cudaStream_t st) {
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    mdots_kernel<<<grid, 256, 0, st>>>(n, m, x, y, out2);
+}
+
+__global__ void scale_kernel(int64_t n, const double* __restrict__ y, double s, double* __restrict__ x) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = y[i] * s;
+}
+
+void launch_scale(int64_t n, const double* y, double s, double* x, cudaStream_t st) {
+    const int grid = (int)((n + 255) / 256);
+    if (grid) scale_kernel<<<grid, 256, 0, st>>>(n, y, s, x);
+}
+
+__global__ void node_mass_kernel(EstOp op, double* m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= op.n) return;
+    int x, y, z, cls;
+    class_of(i, op.nx, op.ny, x, y, z, cls);
+    m[i] = op.mtab[cls];
+}
+
+void launch_node_mass(const EstOp& op, double* m_out, cudaStream_t st) {
+    const int grid = (int)((op.n + 255) / 256);
+    if (grid) node_mass_kernel<<<grid, 256, 0, st>>>(op, m_out);
+}
+
+// dst = src (- comp), converted to double or float.
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ src, const float* __restrict__ comp, D* __restrict__ dst,
+                               int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = (double)src[i];
+    if (comp) v -= (double)comp[i];
+    dst[i] = (D)v;
+}
+
+void launch_convert(const void* src, int src_prec, const float* comp, void* dst, int dst_f32, int64_t n,
+                    cudaStream_t st) {
+    const int grid = (int)((n + 255) / 256);
+    if (!grid) return;
+    if (src_prec == P_F64) {
+        if (dst_f32) convert_kernel<double, float><<<grid, 256, 0, st>>>((const double*)src, comp, (float*)dst, n);
+        else convert_kernel<double, double><<<grid, 256, 0, st>>>((const double*)src, comp, (double*)dst, n);
+    } else {
+        if (dst_f32) convert_kernel<float, float><<<grid, 256, 0, st>>>((const float*)src, comp, (float*)dst, n);
+        else convert_kernel<float, double><<<grid, 256, 0, st>>>((const float*)src, comp, (double*)dst, n);
+    }
+}
+
+}  // namespace daeti

@@ -1,0 +1,105 @@
+// Host-visible launch interface of the libdaeti kernels (no device code).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace daeti {
+
+enum Prec { P_F64 = 0, P_F32 = 1 };
+enum Model { M_MS = 1, M_TP06 = 2 };
+
+// Device buffers of the time-stepping state (typed by the context's precision).
+struct DevState {
+    int prec = P_F32;        // arithmetic of state and operators
+    bool kahan = false;      // compensated V updates (float only)
+    int64_t n = 0;           // nodes
+    int n_states = 0;        // including V
+    void* V[2] = {nullptr, nullptr};      // ping-pong V
+    float* C[2] = {nullptr, nullptr};     // Kahan compensation (nullable)
+    void* S = nullptr;                    // other states, state-major, row stride n
+    void* vsync = nullptr;                // V at the last synchronisation
+    uint8_t* kk = nullptr;                // sub-step count of the next step A
+    void* act = nullptr;                  // activation times
+    int* perm = nullptr;                  // nodes grouped by k (n entries)
+    int* counts = nullptr;                // [2][DAETI_MAX_K] per-k counts (double-buffered)
+    int* cursor = nullptr;                // [2][DAETI_MAX_K] scatter cursors
+    unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
+    StimDev* stims = nullptr;             // stimulus table
+    int n_stims = 0;
+    long long* step_ctr = nullptr;        // device step counter used by graph replays
+    unsigned long long* substeps = nullptr;   // running total of node reaction sub-steps (bucketing)
+    int* flags = nullptr;                 // [0] non-finite, [1] timeout
+};
+
+struct ModelArgs {
+    int model = M_TP06;
+    double ms[5] = {0.3, 6.0, 120.0, 150.0, 0.13};   // tau_in, tau_out, tau_open, tau_close, v_gate
+    int celltype = 0;
+    int gate_rl = 1;
+};
+
+// Diffusion operator in one of two layouts.
+struct DiffOp {
+    int kind = 0;            // 0 structured stencil table, 1 SELL-32
+    int dim = 3;
+    int nx = 1, ny = 1, nz = 1;
+    void* coef = nullptr;    // table: [nz*9][27] off-diagonal dt_ad K_ij / m_i (self entry 0)
+    // SELL-32 (rows in chunks of 32, column-major inside a chunk)
+    int64_t n_chunks = 0;
+    int64_t* chunk_ptr = nullptr;   // start of chunk c in val/col
+    int* chunk_w = nullptr;         // width (entries per row) of chunk c
+    int* col = nullptr;
+    void* val = nullptr;            // off-diagonal dt_ad K_ij / m_i
+    int64_t nnz_padded = 0;
+};
+
+struct SyncArgs {
+    double dt = 0.1;
+    double vscale = 1.0;
+    double vth = -40.0;
+    int kmax = 10;
+    int adaptive = 1;
+};
+
+// Launchers.  `step` identifies the step whose work is launched.
+// Step A on V[buf] (and C[buf]).
+void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef step, bool use_perm,
+                     int buf, int block, cudaStream_t st);
+// One diffusion sub-step from V[src] to V[1-src]; with `sync`, the
+// synchronisation epilogue runs on the result (counts into counts[par]).
+void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par,
+                      const SyncArgs& sa, StepRef step, bool count, int block, cudaStream_t st);
+void launch_bucket_scatter(const DevState& s, int par, int kmax, int block, cudaStream_t st);
+void launch_tick(long long* ctr, long long inc, cudaStream_t st);
+void launch_set_counter(long long* ctr, long long value, cudaStream_t st);
+
+// FP64 stable-step estimator (Eq. 3) and power iteration on M_L^-1 K.
+struct EstOp {
+    int kind = 0;                    // 0 table, 1 SELL
+    int dim = 3, nx = 1, ny = 1, nz = 1;
+    const double* ktab = nullptr;    // table: [nz*9][27] K entries (with diagonal)
+    const double* mtab = nullptr;    // table: [nz*9] lumped mass
+    int64_t n_chunks = 0;
+    const int64_t* chunk_ptr = nullptr;
+    const int* chunk_w = nullptr;
+    const int* col = nullptr;
+    const double* kval = nullptr;    // SELL off-diagonal K
+    const double* kdiag = nullptr;   // K diagonal per row
+    const double* m = nullptr;       // lumped mass per row
+    int64_t n = 0;
+};
+void launch_gershgorin(const EstOp& op, unsigned long long* out_bits, cudaStream_t st);
+void launch_apply_minvk(const EstOp& op, const double* x, double* y, cudaStream_t st);
+void launch_mdots(int64_t n, const double* m, const double* x, const double* y, double* out2,
+                  cudaStream_t st);
+void launch_scale(int64_t n, const double* y, double s, double* x, cudaStream_t st);
+void launch_node_mass(const EstOp& op, double* m_out, cudaStream_t st);
+
+// Conversions between the state precision and the caller's dtype.
+void launch_convert(const void* src, int src_prec, const float* comp, void* dst, int dst_f32,
+                    int64_t n, cudaStream_t st);
+}  // namespace daeti

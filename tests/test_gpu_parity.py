@@ -1,0 +1,176 @@
+"""GPU (CUDA through the C ABI) vs CPU oracle, element by element.
+
+Tolerances: FP64 max|dV| <= 0.5 mV and activation-time error <= 0.1 ms;
+FP32 with compensated V: <= 2 mV and <= 0.5 ms.  Mitchell-Schaeffer voltages
+are dimensionless and compared in mV through V_mV = 100 v - 80.
+"""
+import numpy as np
+import pytest
+
+import inputs as I
+from parity_util import act_error, gpu_available, run_gpu, run_oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL = {"fp64": (0.5, 0.1), "fp32_kahan": (2.0, 0.5)}
+
+
+def _mv(wl):
+    return 100.0 if wl.model in ("ms", "cubic") else 1.0
+
+
+def _compare(wl, n_steps, every, precision, scheme_name="daeti", tol=None, **gpu_opts):
+    g, ga, stab, _ = run_gpu(wl, n_steps, every, precision=precision, scheme=scheme_name, **gpu_opts)
+    o, oa, sim = run_oracle(wl, n_steps, every, scheme_name=scheme_name)
+    assert stab["l"] == sim.l and stab["k_max"] == sim.k_max
+    assert abs(stab["dt_s"] - sim.dt_s) <= 1e-12 * sim.dt_s
+    assert abs(stab["dt"] - sim.dt) <= 1e-15
+    dv = float(np.max(np.abs(g - o))) * _mv(wl)
+    da, same, nboth = act_error(ga, oa)
+    tv, ta = tol or TOL[precision]
+    assert same, "activated node sets differ"
+    assert dv <= tv, f"max|dV| = {dv:.4g} mV"
+    assert da <= ta, f"max|d act| = {da:.4g} ms"
+    return dv, da, nboth
+
+
+def test_ms_square_full_config_fp64():
+    wl = I.ms_square_2d()                       # 41 x 41, 100 ms, dt = 0.1
+    dv, da, n = _compare(wl, 1000, 10, "fp64")
+    assert n == wl.n_nodes                       # the wave crosses the whole square
+
+
+def test_ms_square_full_config_fp32():
+    wl = I.ms_square_2d()
+    _compare(wl, 1000, 10, "fp32_kahan")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_tp06_slab_small(precision):
+    wl = I.tp06_slab_3d(21, 17, 6)              # ragged in x and y, 3D 27-point stencil
+    _compare(wl, 400, 20, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_sheet_with_diffusion_substeps(precision):
+    # h = 100 um, d0 = 0.0017, rho = 0.25: dt_s = 0.0132 ms, l = 3 (odd)
+    wl = I.aniso_sheet_2d(n=37, length=0.36, model="tp06", amp=60.0)
+    g, ga, stab, _ = run_gpu(wl, 1, 1, precision=precision)
+    assert stab["l"] == 3
+    _compare(wl, 300, 10, precision)
+
+
+def test_sheet_ceil_rounding_l4():
+    wl = I.aniso_sheet_2d(n=21, length=0.2, model="ms")
+    g, ga, stab, _ = run_gpu(wl, 200, 10, precision="fp64", l_rounding="ceil")
+    o, oa, sim = run_oracle(wl, 200, 10, l_round="ceil")
+    assert stab["l"] == sim.l == 4
+    assert float(np.max(np.abs(g - o))) * 100 <= 0.5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_tet_mesh_sell_path(precision):
+    wl = I.tet_slab_3d(13, 11, 6, h=0.02, fibrosis=0.3, scar_radius=0.05, s2_time=15.0)
+    _compare(wl, 300, 20, precision)
+
+
+def test_heterogeneous_grid_uses_sparse_path():
+    wl = I.ms_square_2d(n=23)
+    rng = np.random.default_rng(7)
+    wl.d_long = wl.d_long * rng.uniform(0.3, 1.7, wl.n_elems)
+    wl.d_trans = wl.d_long.copy()
+    _compare(wl, 400, 20, "fp64")
+
+
+@pytest.mark.parametrize("scheme_name", ["ost", "ostar"])
+def test_scheme_variants(scheme_name):
+    wl = I.aniso_sheet_2d(n=21, length=0.2, model="ms")
+    if scheme_name == "ost":
+        wl.dt = 0.01
+    _compare(wl, 300, 20, "fp64", scheme_name=scheme_name)
+
+
+def test_bucketing_and_graphs_do_not_change_results():
+    wl = I.tp06_slab_3d(15, 13, 5, t_end=10)
+    ref = None
+    for bucket in (True, False):
+        for graph in (0, 20):
+            g, ga, _, st = run_gpu(wl, 100, 50, precision="fp32_kahan", bucket_k=bucket, graph_steps=graph)
+            if ref is None:
+                ref = (g, ga, st)
+            else:
+                assert np.array_equal(g, ref[0]) and np.array_equal(ga, ref[1]) and np.array_equal(st, ref[2])
+
+
+def test_checkpoint_roundtrip_is_exact():
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = I.tp06_slab_3d(11, 11, 5)
+    a = binding.solver_from_workload(wl, precision="fp32_kahan")
+    a.daeti_advance(3.0)
+    ck = a.daeti_save_state()
+    a.daeti_advance(8.0)
+    va = a.daeti_read_v()
+    a.daeti_load_state(ck)
+    assert abs(a.time - 3.0) < 1e-12
+    a.daeti_advance(8.0)
+    assert np.array_equal(a.daeti_read_v(), va)
+    a.close()
+
+
+def test_error_paths():
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    s = binding.Solver()
+    with pytest.raises(binding.DaetiError) as e:
+        s.daeti_advance(1.0)
+    assert e.value.code == binding.ESTATE
+    s.close()
+    wl = I.ms_square_2d(n=11)
+    s = binding.solver_from_workload(wl, precision="fp64")
+    with pytest.raises(binding.DaetiError) as e:
+        s.daeti_advance(0.05)                    # not a whole number of steps
+    assert e.value.code == binding.EINVAL
+    bad = np.zeros((2, wl.n_nodes))
+    bad[0, 3] = np.nan
+    with pytest.raises(binding.DaetiError):
+        s.daeti_init_state(bad)
+    s.close()
+    # a blown-up stimulus makes V non-finite: reported at synchronisation, context stays usable
+    wl.stimuli[0].amplitude = 1e38
+    s = binding.solver_from_workload(wl, precision="fp32")
+    s.daeti_advance(2.0)
+    with pytest.raises(binding.DaetiError) as e:
+        s.daeti_synchronize()
+    assert e.value.code == binding.ENONFINITE
+    s.daeti_init_state()
+    s.close()
+
+
+def test_degenerate_inputs():
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    # smallest grid, no stimulus, zero conductivity: reaction only
+    wl = I.ms_square_2d(n=2)
+    wl.stimuli = []
+    wl.d_long[:] = 0.0
+    wl.d_trans[:] = 0.0
+    g, ga, stab, _ = run_gpu(wl, 20, 20, precision="fp64")
+    assert stab["l"] == 1
+    assert np.all(g == 0.0) and np.all(ga == -1.0)
+    # advancing by zero steps is a no-op
+    s = binding.solver_from_workload(I.ms_square_2d(n=5), precision="fp64")
+    s.daeti_advance(0.0)
+    assert s.time == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_full_slab_bench_config_first_steps(precision):
+    """The bench workload (101 x 101 x 26 TP06 slab) at full size, in the bench's
+    launch configuration (graphs, bucketing), over the stimulus and first upstrokes."""
+    wl = I.tp06_slab_3d()
+    _compare(wl, 30, 10, precision)
