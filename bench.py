@@ -156,7 +156,8 @@ def run_ours(args):
     n_steps = int(round(T_END / wl.dt))
 
     def make(prec):
-        s = binding.solver_from_workload(wl, precision=prec, graph_steps=args.graph_steps)
+        s = binding.solver_from_workload(wl, precision=prec, graph_steps=args.graph_steps,
+                                         bucket_k=bool(args.bucket))
         s.daeti_set_stream(stream)
         return s
 
@@ -237,15 +238,17 @@ def run_ours(args):
     s32.close()
 
     # ---- FP64 beside it -------------------------------------------------------------
-    s64 = make("fp64")
-    t64 = timed_runs(s64, max(1, args.steps // 2), 1)
-    v64 = s64.daeti_read_v()
-    a64 = s64.daeti_read_activation()
-    s64.close()
-    sec64 = sum(t64) / len(t64)
-    both = (a32 >= 0) & (a64 >= 0)
-    dv = float(np.max(np.abs(v32 - v64)))
-    dact = float(np.max(np.abs(a32[both] - a64[both]))) if both.any() else None
+    sec64, dv, dact = None, None, None
+    if not args.no_fp64:
+        s64 = make("fp64")
+        t64 = timed_runs(s64, max(1, args.steps // 2), 1)
+        v64 = s64.daeti_read_v()
+        a64 = s64.daeti_read_activation()
+        s64.close()
+        sec64 = sum(t64) / len(t64)
+        both = (a32 >= 0) & (a64 >= 0)
+        dv = float(np.max(np.abs(v32 - v64)))
+        dact = float(np.max(np.abs(a32[both] - a64[both]))) if both.any() else None
 
     # ---- roofline of the dominant kernel -----------------------------------------------
     peaks = _peaks()
@@ -271,8 +274,8 @@ def run_ours(args):
                    "precision": "fp32_kahan", "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "sim_ms_per_wall_s": T_END / sec32,
-        "fp64": {"value": world * n_nodes * n_steps / sec64, "ms_per_step": sec64 * 1e3,
-                 "sim_ms_per_wall_s": T_END / sec64},
+        "fp64": None if sec64 is None else {"value": world * n_nodes * n_steps / sec64,
+                                             "ms_per_step": sec64 * 1e3, "sim_ms_per_wall_s": T_END / sec64},
         "fp32_vs_fp64": {"max_abs_dv_mv_at_500ms": dv, "max_abs_dact_ms": dact},
         "reaction_substeps_per_node_step": sub_per_launch / n_nodes if sub_per_launch else None,
         "kernels": kt,
@@ -290,6 +293,22 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_run(args):
+    """A short plain run of the bench workload for external profilers."""
+    import inputs
+    from paper_2011_04747_gb300 import binding, build as _build
+
+    if not os.path.exists(binding.LIB_PATH):
+        _build.build()
+    wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
+    s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=args.graph_steps,
+                                     bucket_k=bool(args.bucket))
+    s.daeti_advance(args.profile_run)
+    s.daeti_synchronize()
+    s.close()
+    print(f"profile run: {args.profile_run} ms simulated")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,7 +317,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--graph-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--bucket", type=int, default=1, help="group nodes by k before step A (1) or not (0)")
+    ap.add_argument("--profile-run", type=float, default=0.0,
+                    help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
     args = ap.parse_args()
+    if args.profile_run > 0:
+        profile_run(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
