@@ -203,6 +203,42 @@ int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* 
  * at the current problem (the counts the roofline figures use). */
 int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free stable-step estimate (no counterpart in the paper: this is a
+ * deployment convenience, not part of the method).
+ *
+ * For callers that cannot call cudaMalloc (hosts that own all device memory
+ * through their own pool or budget, plugins that must not allocate after
+ * start-up, code that must avoid the implicit synchronisation of cudaMalloc /
+ * cudaFree).  Computes, for a structured grid whose conductivity is constant
+ * on each element layer, the same two numbers that daeti_prepare +
+ * daeti_get_stability report: dt_s of Eq. 3 (FP64 Gershgorin bound) and
+ * lambda_max of M_L^-1 K (FP64 power iteration, same start vector and
+ * stopping rule).  It calls no cudaMalloc, cudaFree or other allocating
+ * library routine: its work vectors live in one fixed __device__ array of
+ * about 13.6 MB that every GPU which loads libdaeti holds until the process
+ * exits.
+ *   - Limits: at most DAETI_NOALLOC_MAX_NODES nodes and
+ *     DAETI_NOALLOC_MAX_LAYERS node layers in z; larger grids return
+ *     DAETI_EINVAL with a message.  Conductivity varying inside an element
+ *     layer returns DAETI_EUNSUPPORTED.
+ *   - Arguments: as daeti_set_mesh_grid and daeti_set_conductivity (host
+ *     arrays, copied during the call); stream = cudaStream_t to run on (NULL =
+ *     legacy default stream); results in *dt_s and *lambda_max (host);
+ *     errbuf/errbuf_len: optional caller buffer for an error message.
+ *   - The first call on each device (with that device current) looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.  The call waits for its own work.
+ *   - Every call shares the one array and leaves its contents behind; calls
+ *     whose work overlaps on the GPU (from several host threads with
+ *     different streams) race on it.  Host-side calls are serialised. */
+#define DAETI_NOALLOC_MAX_NODES 524288
+#define DAETI_NOALLOC_MAX_LAYERS 512
+int daeti_grid_stability_noalloc(int dim, const int64_t n[3], double h, int64_t n_elem,
+                                 const double* d_long, const double* d_trans,
+                                 const double* fibre, void* stream, double* dt_s,
+                                 double* lambda_max, char* errbuf, int errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,8 @@ _SIGNATURES = {
     "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+    "daeti_grid_stability_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_double, ctypes.c_int64, _DP, _DP,
+                                                    _DP, _VP, _DP, _DP, ctypes.c_char_p, ctypes.c_int]),
 }
 
 
@@ -307,6 +309,25 @@ class Solver:
     @property
     def time(self):
         return self.daeti_get_time()[0]
+
+
+def daeti_grid_stability_noalloc(dim, n, h, d_long, d_trans=None, fibre=None, stream=None):
+    """Allocation-free (dt_s, lambda_max) of a layered structured grid; raises DaetiError."""
+    lib = load_library()
+    nn = _i64(list(n) + [1] * (3 - len(n)))
+    dl = _f64(d_long)
+    dtr = _f64(d_trans) if d_trans is not None else None
+    fb = _f64(fibre) if fibre is not None else None
+    handle = getattr(stream, "cuda_stream", stream)
+    dts, lam = ctypes.c_double(), ctypes.c_double()
+    err = ctypes.create_string_buffer(256)
+    rc = lib.daeti_grid_stability_noalloc(int(dim), _ptr(nn, ctypes.c_int64), float(h), dl.shape[0],
+                                          _ptr(dl, ctypes.c_double), _ptr(dtr, ctypes.c_double),
+                                          _ptr(fb, ctypes.c_double), _VP(int(handle) if handle else 0),
+                                          ctypes.byref(dts), ctypes.byref(lam), err, 256)
+    if rc != OK:
+        raise DaetiError(rc, err.value.decode())
+    return dts.value, lam.value
 
 
 def solver_from_workload(wl, **options) -> Solver:

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdaeti.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "reaction.cu", "diffusion.cu", "estimator.cu"]
+CU_SOURCES = ["api.cu", "reaction.cu", "diffusion.cu", "estimator.cu", "noalloc.cu"]
 CPP_SOURCES = ["assembly.cpp"]
 
 
