@@ -87,7 +87,7 @@ typedef struct daeti_options {
     int32_t graph_steps;       /* steps per captured CUDA graph (even, 0 = plain launches) */
     int32_t react_block;       /* threads per block of the reaction kernel (0 = default) */
     int32_t diff_block;        /* threads per block of the diffusion kernel (0 = default) */
-    int32_t fuse_diffusion;    /* 1: one launch per step B when l == 1 (both halves + sync) */
+    int32_t fuse_diffusion;    /* 1: last diffusion sub-step of step I inside the reaction launch */
 } daeti_options;
 
 typedef struct daeti_ctx daeti_ctx;
@@ -192,9 +192,30 @@ int daeti_load_state(daeti_ctx* ctx, const void* buf, int64_t buf_bytes);
  * (bucket_k = 1); waits for enqueued work. */
 int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
 
+/* Launch shapes (set by the caller or an autotuner; results do not depend on
+ * them).  react_block: threads per reaction block (32..128, multiple of 32);
+ * react_min_blocks: 8 or 10 resident reaction blocks per SM the register
+ * budget must allow (TP06 in float); diff_block: threads per diffusion
+ * block (32..256, multiple of 32);
+ * fuse_diffusion: run the last diffusion sub-step of step I inside the
+ * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
+ * steps per captured CUDA graph (rounded up to even, 0 = plain launches).
+ * set waits for enqueued work and drops captured graphs. */
+typedef struct daeti_tuning {
+    int32_t struct_size;       /* sizeof(daeti_tuning) */
+    int32_t react_block;
+    int32_t react_min_blocks;
+    int32_t diff_block;
+    int32_t fuse_diffusion;
+    int32_t bucket_k;
+    int32_t graph_steps;
+} daeti_tuning;
+int daeti_get_tuning(daeti_ctx* ctx, daeti_tuning* tuning);
+int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);
+
 /* Per-kernel timing (CUDA events around every launch of the plain-launch
  * path; graphs are not used while it is on).  which: 0 reaction,
- * 1 diffusion, 2 bucketing.  Returns total milliseconds and launch count
+ * 1 diffusion (plain sub-steps and fused step B), 2 other.  Returns total milliseconds and launch count
  * since profiling was enabled. */
 int daeti_set_profiling(daeti_ctx* ctx, int enable);
 int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* launches);

@@ -54,6 +54,20 @@ class daeti_options(ctypes.Structure):
     ]
 
 
+class daeti_tuning(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("react_block", ctypes.c_int32),
+        ("react_min_blocks", ctypes.c_int32),
+        ("diff_block", ctypes.c_int32),
+        ("fuse_diffusion", ctypes.c_int32),
+        ("bucket_k", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+    ]
+
+
+TUNING_FIELDS = ("react_block", "react_min_blocks", "diff_block", "fuse_diffusion", "bucket_k", "graph_steps")
+
 _lib = None
 
 _VP = ctypes.c_void_p
@@ -87,6 +101,8 @@ _SIGNATURES = {
     "daeti_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
     "daeti_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
     "daeti_get_substeps": (ctypes.c_int, [_VP, _I64P]),
+    "daeti_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(daeti_tuning)]),
+    "daeti_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(daeti_tuning)]),
     "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
@@ -290,6 +306,22 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self.lib.daeti_get_substeps(self.ctx, ctypes.byref(n)))
         return n.value
+
+    def daeti_get_tuning(self):
+        t = daeti_tuning()
+        self._check(self.lib.daeti_get_tuning(self.ctx, ctypes.byref(t)))
+        return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+    def daeti_set_tuning(self, **changes):
+        """Change launch shapes (keys of TUNING_FIELDS); returns the new tuning."""
+        cur = self.daeti_get_tuning()
+        cur.update(changes)
+        t = daeti_tuning()
+        t.struct_size = ctypes.sizeof(daeti_tuning)
+        for f in TUNING_FIELDS:
+            setattr(t, f, int(cur[f]))
+        self._check(self.lib.daeti_set_tuning(self.ctx, ctypes.byref(t)))
+        return self.daeti_get_tuning()
 
     def daeti_set_profiling(self, enable=True):
         self._check(self.lib.daeti_set_profiling(self.ctx, int(bool(enable))))

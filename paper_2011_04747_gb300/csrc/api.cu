@@ -53,10 +53,14 @@ struct daeti_ctx {
     int par = 0;
     void* scratch = nullptr;   // n doubles for conversions
     std::vector<void*> allocs;
-    // graph
-    cudaGraphExec_t gexec = nullptr;
-    int g_steps = 0;
-    int g_par = 0;
+    // launch shapes
+    ReactTuning rtune;
+    int diff_block = 256;
+    bool fused = true;          // last sub-step of step I inside the reaction launch
+    bool lists = true;
+    int graph_steps = 20;
+    // graphs of graph_steps steps, keyed by (start V buffer, list parity)
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
     // profiling
     bool prof = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -105,11 +109,16 @@ int dalloc(daeti_ctx* c, void** p, size_t bytes) {
     return DAETI_OK;
 }
 
+void drop_graphs(daeti_ctx* c) {
+    for (int i = 0; i < 4; ++i)
+        if (c->graphs[i]) {
+            cudaGraphExecDestroy(c->graphs[i]);
+            c->graphs[i] = nullptr;
+        }
+}
+
 void free_device(daeti_ctx* c) {
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     c->s = DevState();
@@ -140,56 +149,61 @@ int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
 
 StepRef plain_ref(int64_t n) { return StepRef{nullptr, (long long)n}; }
 
-// Launches of one Strang step (state at a synchronisation on entry and exit).
-void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed) {
-    const bool bucket = c->opt.bucket_k != 0 && c->sargs.adaptive;
-    int buf = c->cur;
-    auto tstart = [&](int) {
-        if (timed) cudaEventRecord(c->ev[0], st);
-    };
-    auto tstop = [&](int which) {
-        if (timed) {
-            cudaEventRecord(c->ev[1], st);
-            cudaEventSynchronize(c->ev[1]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-            c->ktime[which] += ms;
-            c->klaunch[which] += 1;
-        }
-    };
-    // step I (first diffusion half)
-    for (int i = 0; i < c->l; ++i) {
-        tstart(1);
-        launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, c->opt.diff_block, st);
-        tstop(1);
-        buf ^= 1;
+// ---- launch wrappers (optionally timed with events: 0 reaction, 1 diffusion, 2 other)
+struct Timer {
+    daeti_ctx* c;
+    cudaStream_t st;
+    bool on;
+    int which;
+    Timer(daeti_ctx* c_, cudaStream_t st_, bool on_, int which_) : c(c_), st(st_), on(on_), which(which_) {
+        if (on) cudaEventRecord(c->ev[0], st);
     }
-    // step II (reaction), nodes grouped by k
-    if (bucket) {
-        tstart(2);
-        launch_bucket_scatter(c->s, c->par, c->kmax, 256, st);
-        tstop(2);
+    ~Timer() {
+        if (!on) return;
+        cudaEventRecord(c->ev[1], st);
+        cudaEventSynchronize(c->ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        c->ktime[which] += ms;
+        c->klaunch[which] += 1;
     }
-    tstart(0);
-    launch_reaction(c->s, c->margs, c->dt_eff, ref, bucket, buf, c->opt.react_block, st);
-    tstop(0);
-    // step III (second half), synchronisation at its end
-    for (int i = 0; i < c->l; ++i) {
-        const bool last = i == c->l - 1;
-        tstart(1);
-        launch_diffusion(c->s, c->op, buf, last, c->par ^ 1, c->sargs, ref, bucket, c->opt.diff_block, st);
-        tstop(1);
-        buf ^= 1;
-    }
-    if (bucket) c->par ^= 1;
+};
+
+bool lists_mode(const daeti_ctx* c) { return c->lists && c->sargs.adaptive; }
+
+void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bool timed) {
+    Timer t(c, st, timed, 0);
+    launch_reaction(c->s, c->margs, c->dt_eff, ref, lists_mode(c), c->par, buf, fused, c->op, c->rtune, st);
 }
 
-int capture_graph(daeti_ctx* c) {
-    const int G = c->opt.graph_steps;
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
+void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
+    Timer t(c, st, timed, 1);
+    launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st);
+}
+
+// One Strang step from a synchronisation to the next: step I (l sub-steps,
+// the last one fused into the reaction launch unless disabled), step II,
+// step III (l sub-steps, synchronisation after the last).  V returns to
+// buffer c->cur (2l buffer flips).
+void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed) {
+    int buf = c->cur;
+    const int first = c->fused ? c->l - 1 : c->l;
+    for (int i = 0; i < first; ++i) {
+        L_diff(c, ref, buf, false, st, timed);
+        buf ^= 1;
     }
+    L_react(c, ref, buf, c->fused, st, timed);
+    if (c->fused) buf ^= 1;
+    for (int i = 0; i < c->l; ++i) {
+        L_diff(c, ref, buf, i == c->l - 1, st, timed);
+        buf ^= 1;
+    }
+    if (lists_mode(c)) c->par ^= 1;
+}
+
+// Capture graph_steps steps from the current list parity.
+int capture_graph(daeti_ctx* c, cudaGraphExec_t* out) {
+    const int G = c->graph_steps;
     const int par0 = c->par;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -198,14 +212,30 @@ int capture_graph(daeti_ctx* c) {
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->par = par0;   // capture only recorded the launches
     if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->gexec = nullptr;
+        *out = nullptr;
         return fail(c, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
-    c->g_steps = G;
-    c->g_par = par0;
+    return DAETI_OK;
+}
+
+// Replay whole graphs while at least `reserve` + graph_steps steps remain.
+int replay_graphs(daeti_ctx* c, int64_t& remaining, int64_t reserve, cudaStream_t st) {
+    const int G = c->graph_steps;
+    if (c->prof || G <= 0 || remaining - reserve < G) return DAETI_OK;
+    const int key = c->cur * 2 + c->par;
+    if (!c->graphs[key]) {
+        int rc = capture_graph(c, &c->graphs[key]);
+        if (rc) return rc;
+    }
+    launch_set_counter(c->s.step_ctr, c->nstep, st);
+    while (remaining - reserve >= G) {
+        CK(cudaGraphLaunch(c->graphs[key], st));
+        c->nstep += G;
+        remaining -= G;
+    }
     return DAETI_OK;
 }
 
@@ -256,6 +286,11 @@ int daeti_create(daeti_ctx** out, const daeti_options* opt) {
     }
     c->own_stream = true;
     for (int i = 0; i < 4; ++i) cudaEventCreate(&c->ev[i]);
+    if (o.react_block > 0) c->rtune.block = o.react_block;
+    if (o.diff_block > 0) c->diff_block = o.diff_block;
+    c->fused = o.fuse_diffusion != 0;
+    c->lists = o.bucket_k != 0;
+    c->graph_steps = o.graph_steps;
     *out = c;
     return DAETI_OK;
 }
@@ -590,12 +625,10 @@ int daeti_prepare(daeti_ctx* c) {
     if ((rc = dalloc(c, &c->s.vsync, R * N)) || (rc = dalloc(c, &c->s.act, R * N))) return rc;
     if ((rc = dalloc(c, &p, N))) return rc;
     c->s.kk = (uint8_t*)p;
-    if ((rc = dalloc(c, &p, 4 * N))) return rc;
-    c->s.perm = (int*)p;
     if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
     c->s.counts = (int*)p;
-    if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
-    c->s.cursor = (int*)p;
+    if ((rc = dalloc(c, &p, sizeof(int) * (size_t)(c->kmax + 1) * N))) return rc;
+    c->s.lists = (int*)p;
     if ((rc = dalloc(c, &p, 8))) return rc;
     c->s.step_ctr = (long long*)p;
     if ((rc = dalloc(c, &p, 16))) return rc;
@@ -671,6 +704,7 @@ int daeti_prepare(daeti_ctx* c) {
     c->sargs.vscale = c->model == DAETI_MODEL_MS ? 100.0 : 1.0;
     c->sargs.vth = std::isnan(c->opt.v_threshold) ? (c->model == DAETI_MODEL_MS ? 0.5 : -40.0) : c->opt.v_threshold;
     c->sargs.kmax = c->kmax;
+    c->rtune.kmax = c->kmax;
     c->prepared = true;
     return daeti_init_state(c, nullptr);
 }
@@ -723,10 +757,9 @@ int daeti_init_state(daeti_ctx* c, const double* state) {
     std::vector<double> neg(N, -1.0);
     if ((rc = upload_real(c, c->s.act, neg.data(), N))) return rc;
     CK(set_(c, c->s.kk, 1, N));
-    std::vector<int> cnt(2 * DAETI_MAX_K, 0);
-    cnt[1] = (int)N;
-    CK(cpy_(c, c->s.counts, cnt.data(), 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
-    CK(set_(c, c->s.cursor, 0, 4 * 2 * DAETI_MAX_K));
+    CK(set_(c, c->s.counts, 0, 4 * 2 * DAETI_MAX_K));
+    launch_rebuild_lists(c->s, 0, c->stream);   // every node in the k = 1 list
+    CK(cudaStreamSynchronize(c->stream));
     CK(set_(c, c->s.flags, 0, 16));
     CK(set_(c, c->s.step_ctr, 0, 8));
     CK(set_(c, c->s.substeps, 0, 8));
@@ -747,31 +780,17 @@ int daeti_advance(daeti_ctx* c, double t_end) {
         return fail(c, DAETI_EINVAL, "t_end is not a whole number of steps");
     if (target < c->nstep) return fail(c, DAETI_EINVAL, "t_end is before the current time");
     int64_t remaining = target - c->nstep;
+    if (remaining == 0) return DAETI_OK;
     cudaStream_t st = c->stream;
-    const int G = c->opt.graph_steps;
-    if (!c->prof && G > 0 && remaining >= G) {
-        if (!c->gexec || c->g_steps != G) {
-            int rc = capture_graph(c);
-            if (rc) return rc;
-        }
-        if (c->par != c->g_par) {
-            enqueue_step(c, plain_ref(c->nstep), st, false);
+    const bool timed = c->prof;
+    int rc;
+    while (remaining > 0) {
+        if ((rc = replay_graphs(c, remaining, 0, st))) return rc;
+        if (remaining > 0) {
+            enqueue_step(c, plain_ref(c->nstep), st, timed);
             c->nstep++;
             remaining--;
         }
-        if (remaining >= G) {
-            launch_set_counter(c->s.step_ctr, c->nstep, st);
-            while (remaining >= G) {
-                CK(cudaGraphLaunch(c->gexec, st));
-                c->nstep += G;
-                remaining -= G;
-            }
-        }
-    }
-    while (remaining > 0) {
-        enqueue_step(c, plain_ref(c->nstep), st, c->prof);
-        c->nstep++;
-        remaining--;
     }
     CK(cudaGetLastError());
     return DAETI_OK;
@@ -783,7 +802,8 @@ int daeti_synchronize(daeti_ctx* c) {
     if (c->prepared) {
         int f[4];
         CK(cpy_(c, f, c->s.flags, 16, cudaMemcpyDeviceToHost));
-        if (f[0]) return fail(c, DAETI_ENONFINITE, "V became non-finite");
+        if (f[0] & 1) return fail(c, DAETI_ENONFINITE, "V became non-finite");
+        if (f[0] & 2) return fail(c, DAETI_ECUDA, "k histogram inconsistent with k (internal error)");
         if (f[1]) return fail(c, DAETI_ETIMEOUT, "a bounded device wait gave up");
     }
     return DAETI_OK;
@@ -839,13 +859,13 @@ int daeti_read_state(daeti_ctx* c, double* out) {
     return DAETI_OK;
 }
 
-// checkpoint layout: header (8 int64) | V | C | S | vsync | act | kk | counts | cursor
+// checkpoint layout: header (8 int64) | V | C | S | vsync | act | kk | counts
 static int64_t ckpt_bytes(const daeti_ctx* c) {
     const int64_t N = c->n_nodes;
     const int64_t R = (int64_t)rsize(c);
     int64_t b = 64 + R * N;
     if (c->s.kahan) b += 4 * N;
-    b += R * N * (c->s.n_states - 1) + 2 * R * N + N + 2 * 4 * 2 * DAETI_MAX_K;
+    b += R * N * (c->s.n_states - 1) + 2 * R * N + N + 4 * 2 * DAETI_MAX_K;
     return b;
 }
 
@@ -881,8 +901,6 @@ int daeti_save_state(daeti_ctx* c, void* buf, int64_t buf_bytes) {
     CK(cpy_(c, p, c->s.kk, N, cudaMemcpyDeviceToHost));
     p += N;
     CK(cpy_(c, p, c->s.counts, 4 * 2 * DAETI_MAX_K, cudaMemcpyDeviceToHost));
-    p += 4 * 2 * DAETI_MAX_K;
-    CK(cpy_(c, p, c->s.cursor, 4 * 2 * DAETI_MAX_K, cudaMemcpyDeviceToHost));
     return DAETI_OK;
 }
 
@@ -914,12 +932,13 @@ int daeti_load_state(daeti_ctx* c, const void* buf, int64_t buf_bytes) {
     p += R * N;
     CK(cpy_(c, c->s.kk, p, N, cudaMemcpyHostToDevice));
     p += N;
-    CK(cpy_(c, c->s.counts, p, 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
-    p += 4 * 2 * DAETI_MAX_K;
-    CK(cpy_(c, c->s.cursor, p, 4 * 2 * DAETI_MAX_K, cudaMemcpyHostToDevice));
     CK(set_(c, c->s.flags, 0, 16));
     c->nstep = hdr[5];
     c->par = (int)hdr[6];
+    // the per-k lists follow from k
+    CK(set_(c, c->s.counts, 0, 4 * 2 * DAETI_MAX_K));
+    launch_rebuild_lists(c->s, c->par, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
     return DAETI_OK;
 }
 
@@ -953,22 +972,67 @@ int daeti_kernel_work(daeti_ctx* c, int which, double* bytes, double* flops) {
     if (!c || which < 0 || which > 2) return DAETI_EINVAL;
     if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
     const double N = (double)c->n_nodes, R = (double)rsize(c);
-    const double comp = c->s.kahan ? 8.0 : 0.0;
+    const double comp = c->s.kahan ? 8.0 : 0.0;   // Kahan term read + written
+    const double sync = 2.0 * R + 1.0 + R + (lists_mode(c) ? 4.0 : 0.0);   // vsync r/w, k w, act r, list w
     double b = 0.0, f = 0.0;
     if (which == 0) {
-        // every state read and written once per step A, k read, perm read
-        b = N * (2.0 * R * c->s.n_states + comp + 1.0 + (c->opt.bucket_k ? 4.0 : 0.0));
-        f = 0.0;   // sub-step counts are data dependent; the bench counts them
+        // every state read and written once per step A, plus the node's list entry
+        b = N * (2.0 * R * c->s.n_states + comp + (lists_mode(c) ? 4.0 : 1.0));
+        if (c->fused) {
+            // plus the fused diffusion sub-step: V and the Kahan term of the source buffer
+            b += N * (R + (c->s.kahan ? 4.0 : 0.0));
+            if (c->op.kind == 1) b += (double)c->op.nnz_padded * (R + 4.0);
+        }
     } else if (which == 1) {
-        // V read + written per sub-step (+ Kahan term); neighbours come from cache
+        // one sub-step launch: V and the Kahan term read and written once,
+        // neighbours from cache; the synchronising launch adds its epilogue
+        const double npts = c->op.kind == 0 ? (c->dim == 3 ? 26.0 : 8.0) : 15.0;
         b = N * (2.0 * R + comp);
         if (c->op.kind == 1) b += (double)c->op.nnz_padded * (R + 4.0);
-        f = N * 2.0 * (c->op.kind == 0 ? (c->dim == 3 ? 26.0 : 8.0) : 15.0);
+        f = N * 2.0 * npts;
     } else {
-        b = N * (1.0 + 4.0);
+        b = N * sync;
     }
     if (bytes) *bytes = b;
     if (flops) *flops = f;
+    return DAETI_OK;
+}
+
+int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
+    if (!c || !t) return DAETI_EINVAL;
+    t->struct_size = (int32_t)sizeof(daeti_tuning);
+    t->react_block = c->rtune.block;
+    t->react_min_blocks = c->rtune.min_blocks;
+    t->diff_block = c->diff_block;
+    t->fuse_diffusion = c->fused ? 1 : 0;
+    t->bucket_k = c->lists ? 1 : 0;
+    t->graph_steps = c->graph_steps;
+    return DAETI_OK;
+}
+
+int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
+    if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
+    if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block <= 0 ||
+        t->diff_block > 256 || t->diff_block % 32 || t->graph_steps < 0 ||
+        (t->react_min_blocks != 8 && t->react_min_blocks != 10))
+        return fail(c, DAETI_EINVAL, "bad tuning values");
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    drop_graphs(c);
+    c->rtune.block = t->react_block;
+    c->rtune.min_blocks = t->react_min_blocks;
+    c->diff_block = t->diff_block;
+    c->fused = t->fuse_diffusion != 0;
+    const bool new_lists = t->bucket_k != 0;
+    if (new_lists != c->lists && c->prepared) {
+        c->lists = new_lists;
+        // re-derive the lists of the next step A from k
+        CK(set_(c, c->s.counts, 0, 4 * 2 * DAETI_MAX_K));
+        launch_rebuild_lists(c->s, c->par, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->lists = new_lists;
+    c->graph_steps = t->graph_steps + (t->graph_steps % 2);
     return DAETI_OK;
 }
 

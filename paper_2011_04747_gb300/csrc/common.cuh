@@ -86,7 +86,9 @@ struct SyncParams {
     R* vsync;          // V at the previous synchronisation, updated in place
     uint8_t* kk;       // sub-step count of the next step A
     R* act;            // activation times (-1 = not yet)
-    int* counts;       // per-k node counts for the bucketing (nullable)
+    int* counts;       // per-k list lengths of the next step A (nullable: no lists)
+    int* lists;        // list of k starts at lists + k * n (k = 1..kmax)
+    int n;
     int* flags;        // flags[0] |= 1 on non-finite V
     double dt;
     R vscale;          // model units -> mV for the k rule
@@ -121,13 +123,34 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
     return k;
 }
 
-// Warp-aggregated histogram of k into a shared array (lanes with k <= 0 skip).
-__device__ __forceinline__ void warp_count(int* sh_hist, int k, bool valid) {
-    unsigned active = __ballot_sync(0xffffffffu, valid);
-    if (!valid) return;
-    unsigned peers = __match_any_sync(active, k);
-    int leader = __ffs(peers) - 1;
-    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&sh_hist[k], __popc(peers));
+// Block-cooperative append of node i (valid lanes) to the list of its k:
+// warp ranks by __match_any_sync, one shared atomic per (warp, k), one global
+// atomic per (block, k).  Every thread of the block must call it.
+__device__ __forceinline__ void block_append(int* counts, int* lists, int n, int i, int k, bool valid) {
+    __shared__ int blk[DAETI_MAX_K];
+    __shared__ int base[DAETI_MAX_K];
+    if (threadIdx.x < DAETI_MAX_K) blk[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    int rank = 0, wbase = 0;
+    if (valid) {
+        const unsigned peers = __match_any_sync(active, k);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        rank = __popc(peers & ((1u << lane) - 1u));
+        if (lane == leader) wbase = atomicAdd(&blk[k], __popc(peers));
+        wbase = __shfl_sync(peers, wbase, leader);
+    }
+    __syncthreads();
+    if (threadIdx.x < DAETI_MAX_K) {
+        const int c = blk[threadIdx.x];
+        base[threadIdx.x] = c ? atomicAdd(&counts[threadIdx.x], c) : 0;
+    }
+    __syncthreads();
+    if (valid) {
+        const int pos = base[k] + wbase + rank;
+        if (pos < n) lists[(size_t)k * n + pos] = i;
+    }
 }
 
 }  // namespace daeti

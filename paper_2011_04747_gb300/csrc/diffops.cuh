@@ -1,0 +1,115 @@
+// Per-node explicit diffusion sub-step on the two operator layouts, shared
+// by the diffusion kernels and the reaction kernel that fuses the last
+// sub-step of step I (so every path gives bit-identical results).
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace daeti {
+
+// Boundary class of a coordinate: 0 low face, 1 interior, 2 high face.
+__device__ __forceinline__ int bclass(int x, int n) { return x == 0 ? 0 : (x == n - 1 ? 2 : 1); }
+
+// One explicit sub-step at a node whose neighbour at offset (dx,dy,dz) is
+// fetch(dx,dy,dz).  Shared by the plain and the fused kernels so both give
+// bit-identical results.
+template <typename R, int DIM, bool KAHAN, class Fetch>
+__device__ __forceinline__ void stencil_update(const R* __restrict__ crow, int cx, int cy, int z, int nz, R vi,
+                                               float ci, const Fetch& fetch, R& vout, float& cout) {
+    R acc = (R)0;
+#pragma unroll
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const bool ok = (dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
+                                (dy <= 0 || cy < 2) && (DIM == 2 || ((dz >= 0 || z > 0) && (dz <= 0 || z < nz - 1)));
+                if (ok) {
+                    const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                    acc = fma(__ldg(crow + j), fetch(dx, dy, dz) - vi, acc);
+                }
+            }
+        }
+    }
+    R v = vi;
+    float cc = ci;
+    add_comp(v, KAHAN ? &cc : (float*)nullptr, -acc);
+    vout = v;
+    cout = cc;
+}
+
+// SELL-32 row i: V_i - sum_j a_ij (V_j - V_i) with compensation.
+template <typename R, bool KAHAN>
+__device__ __forceinline__ void sell_update(const int64_t* __restrict__ chunk_ptr, const int* __restrict__ chunk_w,
+                                            const int* __restrict__ col, const R* __restrict__ val,
+                                            const R* __restrict__ vin, int i, R vi, float ci, R& vout, float& cout) {
+    const int chunk = i >> 5;
+    const int lane = i & 31;
+    const int64_t off = chunk_ptr[chunk] + lane;
+    const int w = chunk_w[chunk];
+    R acc = (R)0;
+    for (int j = 0; j < w; ++j) {
+        const int cj = __ldg(col + off + 32 * (int64_t)j);
+        const R aj = __ldg(val + off + 32 * (int64_t)j);
+        acc = fma(aj, vin[cj] - vi, acc);
+    }
+    R v = vi;
+    float cc = ci;
+    add_comp(v, KAHAN ? &cc : (float*)nullptr, -acc);
+    vout = v;
+    cout = cc;
+}
+
+// Operator view passed to kernels.
+template <typename R>
+struct OpView {
+    int kind;             // 0 stencil table, 1 SELL-32
+    int nx, ny, nz;
+    const R* coef;
+    const int64_t* chunk_ptr;
+    const int* chunk_w;
+    const int* col;
+    const R* val;
+};
+
+// One sub-step at node i from vin (and cin), any layout.
+template <typename R, int DIM, bool KAHAN>
+__device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __restrict__ vin, const float* cin, int i,
+                                             R& vout, float& cout) {
+    const R vi = vin[i];
+    const float ci = KAHAN ? cin[i] : 0.f;
+    if (DIM == 0) {
+        sell_update<R, KAHAN>(op.chunk_ptr, op.chunk_w, op.col, op.val, vin, i, vi, ci, vout, cout);
+    } else {
+        const int x = i % op.nx;
+        const int yz = i / op.nx;
+        const int y = yz % op.ny;
+        const int z = yz / op.ny;
+        const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
+        const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
+        const int nxy = op.nx * op.ny;
+        const int nx = op.nx;
+        auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
+        stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
+    }
+}
+
+template <typename R>
+inline OpView<R> op_view(const DiffOp& op) {
+    OpView<R> v;
+    v.kind = op.kind;
+    v.nx = op.nx;
+    v.ny = op.ny;
+    v.nz = op.nz;
+    v.coef = (const R*)op.coef;
+    v.chunk_ptr = op.chunk_ptr;
+    v.chunk_w = op.chunk_w;
+    v.col = op.col;
+    v.val = (const R*)op.val;
+    return v;
+}
+
+}  // namespace daeti

@@ -24,9 +24,8 @@ struct DevState {
     void* vsync = nullptr;                // V at the last synchronisation
     uint8_t* kk = nullptr;                // sub-step count of the next step A
     void* act = nullptr;                  // activation times
-    int* perm = nullptr;                  // nodes grouped by k (n entries)
-    int* counts = nullptr;                // [2][DAETI_MAX_K] per-k counts (double-buffered)
-    int* cursor = nullptr;                // [2][DAETI_MAX_K] scatter cursors
+    int* lists = nullptr;                 // per-k node lists of the next step A: list k at lists + k*n
+    int* counts = nullptr;                // [2][DAETI_MAX_K] list lengths (double-buffered by step parity)
     unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
     StimDev* stims = nullptr;             // stimulus table
     int n_stims = 0;
@@ -65,15 +64,25 @@ struct SyncArgs {
     int adaptive = 1;
 };
 
+// Launch shape of the reaction kernel.
+struct ReactTuning {
+    int block = 128;        // threads per block (<= 128)
+    int min_blocks = 8;     // float TP06: resident 128-thread blocks per SM the registers must allow (8 or 10)
+    int kmax = 10;
+};
+
 // Launchers.  `step` identifies the step whose work is launched.
-// Step A on V[buf] (and C[buf]).
-void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef step, bool use_perm,
-                     int buf, int block, cudaStream_t st);
+// Step A.  fused = false: on V[src] in place.  fused = true: first one
+// diffusion sub-step V[src] -> node value, then step A, result in V[1-src].
+// With `lists`, nodes come from the per-k lists of parity `par` (lengths
+// counts[par]); counts[1-par] is cleared for the next synchronisation.
+void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef step, bool lists, int par, int src,
+                     bool fused, const DiffOp& op, const ReactTuning& tune, cudaStream_t st);
 // One diffusion sub-step from V[src] to V[1-src]; with `sync`, the
-// synchronisation epilogue runs on the result (counts into counts[par]).
-void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par,
-                      const SyncArgs& sa, StepRef step, bool count, int block, cudaStream_t st);
-void launch_bucket_scatter(const DevState& s, int par, int kmax, int block, cudaStream_t st);
+// synchronisation epilogue runs on the result (lists of parity `par`).
+void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
+                      StepRef step, bool lists, int block, cudaStream_t st);
+void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st);
 void launch_tick(long long* ctr, long long inc, cudaStream_t st);
 void launch_set_counter(long long* ctr, long long value, cudaStream_t st);
 

@@ -174,3 +174,35 @@ def test_full_slab_bench_config_first_steps(precision):
     launch configuration (graphs, bucketing), over the stimulus and first upstrokes."""
     wl = I.tp06_slab_3d()
     _compare(wl, 30, 10, precision)
+
+
+@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3"])
+def test_launch_shapes_do_not_change_results(wl_name):
+    """Fused or separate diffusion sub-step, register caps, block sizes, k lists and graphs
+    give bit-identical states."""
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = {"slab": I.tp06_slab_3d(23, 19, 9, t_end=12), "sheet2d": I.aniso_sheet_2d(n=41, length=1.0, model="tp06"),
+          "sheet_l3": I.aniso_sheet_2d(n=37, length=0.36, model="tp06")}[wl_name]
+    variants = [dict(),
+                dict(fuse_diffusion=0),
+                dict(react_min_blocks=10),
+                dict(react_min_blocks=10, react_block=64, fuse_diffusion=0),
+                dict(bucket_k=0, graph_steps=0),
+                dict(graph_steps=6, diff_block=128)]
+    ref = None
+    for prec in ("fp32_kahan", "fp64"):
+        ref = None
+        for v in variants:
+            s = binding.solver_from_workload(wl, precision=prec)
+            s.daeti_set_tuning(**v)
+            s.daeti_advance(3.0)
+            s.daeti_advance(7.0)        # two advances: prologue/epilogue of the fused path twice
+            out = (s.daeti_read_state(), s.daeti_read_activation())
+            s.close()
+            if ref is None:
+                ref = out
+            else:
+                assert np.array_equal(out[0], ref[0]), v
+                assert np.array_equal(out[1], ref[1]), v
