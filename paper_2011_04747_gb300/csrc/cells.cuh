@@ -57,17 +57,35 @@ struct TP06State {
     R V, Cai, CaSR, CaSS, Nai, Ki, m, h, j, xr1, xr2, xs, r, s, d, f, f2, fcass, RR;
 };
 
-// Gate update toward g_inf with time constant tau over dt.
+// Gate update toward g_inf with rate 1/tau over dt (Rush-Larsen or forward Euler).
 template <typename R>
-__device__ __forceinline__ R gate_step(R g, R ginf, R tau, R dt, int rl) {
+__device__ __forceinline__ R gate_rate(R g, R ginf, R rate, R dt, int rl) {
     typedef Fm<R> M;
-    if (rl) return ginf - (ginf - g) * M::ex(-M::dv(dt, tau));
-    return g + dt * M::dv(ginf - g, tau);
+    if (rl) return ginf - (ginf - g) * M::ex(-dt * rate);
+    return g + dt * rate * (ginf - g);
 }
 
+// x / (e^x - 1) given e = e^x, with its series near x = 0 (removable
+// singularity of I_CaL at V = 15 mV).
 template <typename R>
-__device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R J,
-                                             const TP06Params& prm) {
+__device__ __forceinline__ R x_over_expm1(R x, R e);
+template <>
+__device__ __forceinline__ float x_over_expm1<float>(float x, float e) {
+    if (fabsf(x) < 1e-2f) return 1.f - 0.5f * x + x * x * (1.f / 12.f) - x * x * x * x * (1.f / 720.f);
+    return __fdividef(x, e - 1.f);
+}
+template <>
+__device__ __forceinline__ double x_over_expm1<double>(double x, double e) {
+    if (fabs(x) < 1e-4) return 1.0 - 0.5 * x + x * x * (1.0 / 12.0);
+    return x / expm1(x);
+}
+
+// One sub-step.  The published rate expressions are regrouped so that each
+// gate and each saturating term costs a single reciprocal: time constants
+// enter as rates 1/tau, products of logistic factors are put over one
+// common denominator, and reversal potentials use ln(c_out) - ln(c_in).
+template <typename R>
+__device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
     typedef TP06Consts C;
     typedef Fm<R> M;
     const R one = (R)1;
@@ -76,47 +94,43 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const R V = x.V;
 
     // reversal potentials
-    const R EK = RTF * M::lg(M::dv((R)C::Ko, x.Ki));
-    const R ENa = RTF * M::lg(M::dv((R)C::Nao, x.Nai));
-    const R EKs = RTF * M::lg(M::dv((R)(C::Ko + C::pKNa * C::Nao), x.Ki + (R)C::pKNa * x.Nai));
-    const R ECa = (R)0.5 * RTF * M::lg(M::dv((R)C::Cao, x.Cai));
+    const R lnKi = M::lg(x.Ki);
+    const R EK = RTF * ((R)1.6863989535702288 - lnKi);   // ln(5.4)
+    const R ENa = RTF * ((R)4.941642422609304 - M::lg(x.Nai));   // ln(140)
+    const R EKs = RTF * ((R)2.2617630984737906 - M::lg(x.Ki + (R)C::pKNa * x.Nai));   // ln(5.4 + 0.03*140)
+    const R ECa = (R)0.5 * RTF * ((R)0.6931471805599453 - M::lg(x.Cai));   // ln(2)
 
-    // inward rectifier
+    // inward rectifier: x_K1 = a/(a+b) with a = 0.1/(1+e0), b = (3 e1 + e2)/(1+e3)
     const R vek = V - EK;
-    const R ak1 = M::dv((R)0.1, one + M::ex((R)0.06 * (vek - (R)200)));
-    const R bk1 = M::dv((R)3 * M::ex((R)0.0002 * (vek + (R)100)) + M::ex((R)0.1 * (vek - (R)10)),
-                        one + M::ex((R)-0.5 * vek));
-    const R xk1 = M::dv(ak1, ak1 + bk1);
+    const R e0 = M::ex((R)0.06 * (vek - (R)200));
+    const R e1 = M::ex((R)0.0002 * (vek + (R)100));
+    const R e2 = M::ex((R)0.1 * (vek - (R)10));
+    const R e3 = M::ex((R)-0.5 * vek);
+    const R ak = (R)0.1 * (one + e3);
+    const R xk1 = M::dv(ak, ak + ((R)3 * e1 + e2) * (one + e0));
 
     const R Gks = prm.celltype == 2 ? (R)0.098 : (R)0.392;
     const R Gto = prm.celltype == 0 ? (R)0.073 : (R)0.294;
-    const R sqk = (R)1;  // sqrt(Ko / 5.4) with Ko = 5.4
 
     const R INa = (R)C::GNa * x.m * x.m * x.m * x.h * x.j * (V - ENa);
-    // I_CaL with (V-15)/(exp(2(V-15)F/RT) - 1) written as (RT/2F) x/expm1(x)
+    // I_CaL = G d f f2 fCass 4 (V-15) F^2/RT (0.25 CaSS e^x - Cao)/(e^x - 1), x = 2 (V-15) F/RT
     const R xc = (R)2 * (V - (R)15) * FRT;
     const R exc = M::ex(xc);
-    R xq;
-    if (fabs(xc) < (R)1e-4) {
-        xq = one - (R)0.5 * xc + xc * xc * (R)(1.0 / 12.0);
-    } else {
-        xq = M::dv(xc, M::em1(xc));
-    }
     const R ICaL = (R)C::GCaL * x.d * x.f * x.f2 * x.fcass * (R)(2.0 * C::F_) *
-                   ((R)0.25 * x.CaSS * exc - (R)C::Cao) * xq;
+                   ((R)0.25 * x.CaSS * exc - (R)C::Cao) * x_over_expm1<R>(xc, exc);
     const R Ito = Gto * x.r * x.s * vek;
-    const R IKr = (R)C::GKr * sqk * x.xr1 * x.xr2 * vek;
+    const R IKr = (R)C::GKr * x.xr1 * x.xr2 * vek;   // sqrt(Ko/5.4) = 1
     const R IKs = Gks * x.xs * x.xs * (V - EKs);
-    const R IK1 = (R)C::GK1 * sqk * xk1 * vek;
-    const R e_g = M::ex((R)C::gam * V * FRT);
-    const R e_g1 = M::ex((R)(C::gam - 1.0) * V * FRT);
+    const R IK1 = (R)C::GK1 * xk1 * vek;             // sqrt(Ko/5.4) = 1
+    const R em = M::ex(-V * FRT);                    // e^{-VF/RT}
+    const R e_g = M::ex((R)C::gam * V * FRT);        // e^{gamma VF/RT}
+    const R e_g1 = e_g * em;                         // e^{(gamma-1) VF/RT}
     const R INaCa = M::dv((R)C::knaca * (e_g * x.Nai * x.Nai * x.Nai * (R)C::Cao -
                                          e_g1 * (R)(C::Nao * C::Nao * C::Nao) * x.Cai * (R)C::alf),
-                          (R)((C::KmNai * C::KmNai * C::KmNai + C::Nao * C::Nao * C::Nao) *
-                              (C::KmCa + C::Cao)) * (one + (R)C::ksat * e_g1));
+                          (R)((C::KmNai * C::KmNai * C::KmNai + C::Nao * C::Nao * C::Nao) * (C::KmCa + C::Cao)) *
+                              (one + (R)C::ksat * e_g1));
     const R INaK = M::dv((R)(C::knak * C::Ko / (C::Ko + C::KmK)) * x.Nai,
-                         (x.Nai + (R)C::KmNa) *
-                             (one + (R)0.1245 * M::ex((R)-0.1 * V * FRT) + (R)0.0353 * M::ex(-V * FRT)));
+                         (x.Nai + (R)C::KmNa) * (one + (R)0.1245 * M::ex((R)-0.1 * V * FRT) + (R)0.0353 * em));
     const R IpCa = M::dv((R)C::GpCa * x.Cai, (R)C::KpCa + x.Cai);
     const R IpK = M::dv((R)C::GpK * vek, one + M::ex(((R)25 - V) * (R)(1.0 / 5.98)));
     const R IbNa = (R)C::GbNa * (V - ENa);
@@ -126,16 +140,16 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const R dV = -Iion + J;
 
     // calcium handling
-    const R ecs = M::dv((R)C::EC, x.CaSR);
-    const R kcasr = (R)C::maxsr - M::dv((R)(C::maxsr - C::minsr), one + ecs * ecs);
-    const R k1 = M::dv((R)C::k1p, kcasr);
+    const R sr2 = x.CaSR * x.CaSR;
+    const R kcasr = (R)C::maxsr - M::dv((R)(C::maxsr - C::minsr) * sr2, sr2 + (R)(C::EC * C::EC));
     const R k2 = (R)C::k2p * kcasr;
     const R dRR = -k2 * x.CaSS * x.RR + (R)C::k4 * (one - x.RR);
     const R css2 = x.CaSS * x.CaSS;
-    const R O = M::dv(k1 * css2 * x.RR, (R)C::k3 + k1 * css2);
+    // O = k1 CaSS^2 RR / (k3 + k1 CaSS^2) with k1 = k1' / kcasr
+    const R O = M::dv((R)C::k1p * css2 * x.RR, (R)C::k3 * kcasr + (R)C::k1p * css2);
     const R Irel = (R)C::Vrel * O * (x.CaSR - x.CaSS);
-    const R kc = M::dv((R)C::Kup, x.Cai);
-    const R Iup = M::dv((R)C::Vmaxup, one + kc * kc);
+    const R ci2 = x.Cai * x.Cai;
+    const R Iup = M::dv((R)C::Vmaxup * ci2, ci2 + (R)(C::Kup * C::Kup));
     const R Ileak = (R)C::Vleak * (x.CaSR - x.Cai);
     const R Ixfer = (R)C::Vxfer * (x.CaSS - x.Cai);
     const R ci = x.Cai + (R)C::Kbufc;
@@ -152,102 +166,109 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const R dNai = -(INa + IbNa + (R)3 * INaK + (R)3 * INaCa) * (R)(C::Cm / (C::Vc * C::F_));
     const R dKi = -(IK1 + Ito + IKr + IKs - (R)2 * INaK + IpK - J) * (R)(C::Cm / (C::Vc * C::F_));
 
-    // gates: steady states and time constants at the start-of-sub-step V
-    const bool hi = V >= (R)-40;
+    // gates at the start-of-sub-step V
     const int rl = prm.gate_rl;
     {
-        const R em = one + M::ex(((R)-56.86 - V) * (R)(1.0 / 9.03));
-        const R minf = M::dv(one, em * em);
-        const R am = M::dv(one, one + M::ex(((R)-60 - V) * (R)0.2));
-        const R bm = M::dv((R)0.1, one + M::ex((V + (R)35) * (R)0.2)) +
-                     M::dv((R)0.1, one + M::ex((V - (R)50) * (R)0.005));
-        x.m = gate_step(x.m, minf, am * bm, dt, rl);
+        // m: tau = a b, a = 1/(1+ea), b = 0.1/(1+eb) + 0.1/(1+ec)
+        const R e_inf = one + M::ex(((R)-56.86 - V) * (R)(1.0 / 9.03));
+        const R minf = M::dv(one, e_inf * e_inf);
+        const R ea = one + M::ex(((R)-60 - V) * (R)0.2);
+        const R eb = one + M::ex((V + (R)35) * (R)0.2);
+        const R ec = one + M::ex((V - (R)50) * (R)0.005);
+        const R rate = M::dv(ea * eb * ec, (R)0.1 * (eb + ec));
+        x.m = gate_rate(x.m, minf, rate, dt, rl);
     }
     {
         const R eh = one + M::ex((V + (R)71.55) * (R)(1.0 / 7.43));
         const R hinf = M::dv(one, eh * eh);
-        R ah, bh, aj, bj;
-        if (hi) {
-            ah = (R)0;
-            bh = M::dv((R)0.77, (R)0.13 * (one + M::ex(-(V + (R)10.66) * (R)(1.0 / 11.1))));
-            aj = (R)0;
-            bj = M::dv((R)0.6 * M::ex((R)0.057 * V), one + M::ex((R)-0.1 * (V + (R)32)));
+        R rh, rj;
+        if (V >= (R)-40) {
+            // a_h = a_j = 0
+            rh = M::dv((R)(0.77 / 0.13), one + M::ex(-(V + (R)10.66) * (R)(1.0 / 11.1)));
+            rj = M::dv((R)0.6 * M::ex((R)0.057 * V), one + M::ex((R)-0.1 * (V + (R)32)));
         } else {
-            ah = (R)0.057 * M::ex(-(V + (R)80) * (R)(1.0 / 6.8));
-            bh = (R)2.7 * M::ex((R)0.079 * V) + (R)3.1e5 * M::ex((R)0.3485 * V);
-            aj = M::dv(((R)-2.5428e4 * M::ex((R)0.2444 * V) - (R)6.948e-6 * M::ex((R)-0.04391 * V)) *
-                           (V + (R)37.78),
-                       one + M::ex((R)0.311 * (V + (R)79.23)));
-            bj = M::dv((R)0.02424 * M::ex((R)-0.01052 * V), one + M::ex((R)-0.1378 * (V + (R)40.14)));
+            rh = (R)0.057 * M::ex(-(V + (R)80) * (R)(1.0 / 6.8)) + (R)2.7 * M::ex((R)0.079 * V) +
+                 (R)3.1e5 * M::ex((R)0.3485 * V);
+            const R da = one + M::ex((R)0.311 * (V + (R)79.23));
+            const R db = one + M::ex((R)-0.1378 * (V + (R)40.14));
+            const R na = ((R)-2.5428e4 * M::ex((R)0.2444 * V) - (R)6.948e-6 * M::ex((R)-0.04391 * V)) * (V + (R)37.78);
+            const R nb = (R)0.02424 * M::ex((R)-0.01052 * V);
+            rj = M::dv(na * db + nb * da, da * db);
         }
-        x.h = gate_step(x.h, hinf, M::dv(one, ah + bh), dt, rl);
-        x.j = gate_step(x.j, hinf, M::dv(one, aj + bj), dt, rl);
+        x.h = gate_rate(x.h, hinf, rh, dt, rl);
+        x.j = gate_rate(x.j, hinf, rj, dt, rl);
     }
     {
+        // xr1: tau = 450/(1+e1) * 6/(1+e2)
         const R inf = M::dv(one, one + M::ex(((R)-26 - V) * (R)(1.0 / 7.0)));
-        const R tau = M::dv((R)450, one + M::ex(((R)-45 - V) * (R)0.1)) *
-                      M::dv((R)6, one + M::ex((V + (R)30) * (R)(1.0 / 11.5)));
-        x.xr1 = gate_step(x.xr1, inf, tau, dt, rl);
+        const R rate = (one + M::ex(((R)-45 - V) * (R)0.1)) * (one + M::ex((V + (R)30) * (R)(1.0 / 11.5))) *
+                       (R)(1.0 / 2700.0);
+        x.xr1 = gate_rate(x.xr1, inf, rate, dt, rl);
     }
     {
+        // xr2: tau = 3/(1+e1) * 1.12/(1+e2)
         const R inf = M::dv(one, one + M::ex((V + (R)88) * (R)(1.0 / 24.0)));
-        const R tau = M::dv((R)3, one + M::ex(((R)-60 - V) * (R)0.05)) *
-                      M::dv((R)1.12, one + M::ex((V - (R)60) * (R)0.05));
-        x.xr2 = gate_step(x.xr2, inf, tau, dt, rl);
+        const R rate = (one + M::ex(((R)-60 - V) * (R)0.05)) * (one + M::ex((V - (R)60) * (R)0.05)) *
+                       (R)(1.0 / 3.36);
+        x.xr2 = gate_rate(x.xr2, inf, rate, dt, rl);
     }
     {
+        // xs: tau = 1400/sqrt(1+e1) / (1+e2) + 80
         const R inf = M::dv(one, one + M::ex(((R)-5 - V) * (R)(1.0 / 14.0)));
-        const R tau = (R)1400 * M::rsq(one + M::ex(((R)5 - V) * (R)(1.0 / 6.0))) *
-                          M::dv(one, one + M::ex((V - (R)35) * (R)(1.0 / 15.0))) +
-                      (R)80;
-        x.xs = gate_step(x.xs, inf, tau, dt, rl);
+        const R d2 = one + M::ex((V - (R)35) * (R)(1.0 / 15.0));
+        const R rate = M::dv(d2, (R)1400 * M::rsq(one + M::ex(((R)5 - V) * (R)(1.0 / 6.0))) + (R)80 * d2);
+        x.xs = gate_rate(x.xs, inf, rate, dt, rl);
     }
     {
         const R inf = M::dv(one, one + M::ex(((R)20 - V) * (R)(1.0 / 6.0)));
         const R v40 = V + (R)40;
-        const R tau = (R)9.5 * M::ex(-v40 * v40 * (R)(1.0 / 1800.0)) + (R)0.8;
-        x.r = gate_step(x.r, inf, tau, dt, rl);
+        const R rate = M::dv(one, (R)9.5 * M::ex(-v40 * v40 * (R)(1.0 / 1800.0)) + (R)0.8);
+        x.r = gate_rate(x.r, inf, rate, dt, rl);
     }
     {
-        R inf, tau;
+        R inf, rate;
         if (prm.celltype == 0) {
             inf = M::dv(one, one + M::ex((V + (R)28) * (R)0.2));
             const R v67 = V + (R)67;
-            tau = (R)1000 * M::ex(-v67 * v67 * (R)0.001) + (R)8;
+            rate = M::dv(one, (R)1000 * M::ex(-v67 * v67 * (R)0.001) + (R)8);
         } else {
             inf = M::dv(one, one + M::ex((V + (R)20) * (R)0.2));
             const R v45 = V + (R)45;
-            tau = (R)85 * M::ex(-v45 * v45 * (R)(1.0 / 320.0)) +
-                  M::dv((R)5, one + M::ex((V - (R)20) * (R)0.2)) + (R)3;
+            const R dd = one + M::ex((V - (R)20) * (R)0.2);
+            // tau = 85 e + 5/dd + 3
+            rate = M::dv(dd, ((R)85 * M::ex(-v45 * v45 * (R)(1.0 / 320.0)) + (R)3) * dd + (R)5);
         }
-        x.s = gate_step(x.s, inf, tau, dt, rl);
+        x.s = gate_rate(x.s, inf, rate, dt, rl);
     }
     {
+        // d: tau = (1.4/d1 + 0.25) (1.4/d2) + 1/d3
         const R inf = M::dv(one, one + M::ex(((R)-8 - V) * (R)(1.0 / 7.5)));
-        const R ad = M::dv((R)1.4, one + M::ex(((R)-35 - V) * (R)(1.0 / 13.0))) + (R)0.25;
-        const R bd = M::dv((R)1.4, one + M::ex((V + (R)5) * (R)0.2));
-        const R cd = M::dv(one, one + M::ex(((R)50 - V) * (R)0.05));
-        x.d = gate_step(x.d, inf, ad * bd + cd, dt, rl);
+        const R d1 = one + M::ex(((R)-35 - V) * (R)(1.0 / 13.0));
+        const R d2 = one + M::ex((V + (R)5) * (R)0.2);
+        const R d3 = one + M::ex(((R)50 - V) * (R)0.05);
+        const R rate = M::dv(d1 * d2 * d3, ((R)1.4 + (R)0.25 * d1) * (R)1.4 * d3 + d1 * d2);
+        x.d = gate_rate(x.d, inf, rate, dt, rl);
     }
     {
+        // f: tau = 1102.5 e + 200/f1 + 180/f2 + 20 ; f2: tau = 562 e' + 31/f1' + 80/f2
         const R inf = M::dv(one, one + M::ex((V + (R)20) * (R)(1.0 / 7.0)));
         const R v27 = V + (R)27;
-        const R tau = (R)1102.5 * M::ex(-v27 * v27 * (R)(1.0 / 225.0)) +
-                      M::dv((R)200, one + M::ex(((R)13 - V) * (R)0.1)) +
-                      M::dv((R)180, one + M::ex((V + (R)30) * (R)0.1)) + (R)20;
-        x.f = gate_step(x.f, inf, tau, dt, rl);
+        const R f1 = one + M::ex(((R)13 - V) * (R)0.1);
+        const R f2 = one + M::ex((V + (R)30) * (R)0.1);
+        const R tnum = ((R)1102.5 * M::ex(-v27 * v27 * (R)(1.0 / 225.0)) + (R)20) * f1 * f2 + (R)200 * f2 +
+                       (R)180 * f1;
+        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, rl);
         const R inf2 = M::dv((R)0.67, one + M::ex((V + (R)35) * (R)(1.0 / 7.0))) + (R)0.33;
-        const R tau2 = (R)562 * M::ex(-v27 * v27 * (R)(1.0 / 240.0)) +
-                       M::dv((R)31, one + M::ex(((R)25 - V) * (R)0.1)) +
-                       M::dv((R)80, one + M::ex((V + (R)30) * (R)0.1));
-        x.f2 = gate_step(x.f2, inf2, tau2, dt, rl);
+        const R g1 = one + M::ex(((R)25 - V) * (R)0.1);
+        const R tnum2 = (R)562 * M::ex(-v27 * v27 * (R)(1.0 / 240.0)) * g1 * f2 + (R)31 * f2 + (R)80 * g1;
+        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, rl);
     }
     {
-        const R q = x.CaSS * (R)20;  // CaSS / 0.05
+        // fCass: inf = 0.6/den + 0.4, tau = 80/den + 2, den = 1 + (CaSS/0.05)^2
+        const R q = x.CaSS * (R)20;
         const R den = one + q * q;
-        const R inf = M::dv((R)0.6, den) + (R)0.4;
-        const R tau = M::dv((R)80, den) + (R)2;
-        x.fcass = gate_step(x.fcass, inf, tau, dt, rl);
+        const R inv = M::dv(one, den);
+        x.fcass = gate_rate(x.fcass, (R)0.6 * inv + (R)0.4, M::dv(den, (R)80 + (R)2 * den), dt, rl);
     }
 
     // forward Euler for V, concentrations and RR

@@ -206,3 +206,23 @@ def test_launch_shapes_do_not_change_results(wl_name):
             else:
                 assert np.array_equal(out[0], ref[0]), v
                 assert np.array_equal(out[1], ref[1]), v
+
+
+@pytest.mark.parametrize("model,params", [("tp06", (0.0,)), ("tp06", (1.0,)), ("tp06", (2.0,)), ("ms", ())])
+def test_cell_models_fp64_tight(model, params):
+    """Reaction only (zero conductivity), every node paced: FP64 GPU cell models
+    against the oracle's transcription to 1e-6 mV over a full action potential."""
+    wl = I.ms_square_2d(n=3) if model == "ms" else I.tp06_slab_3d(3, 3, 3)
+    wl.model = model
+    wl.model_params = params or wl.model_params
+    wl.v_threshold = 0.5 if model == "ms" else -40.0
+    wl.d_long[:] = 0.0
+    wl.d_trans[:] = 0.0
+    amp = 1.0 if model == "ms" else 40.0
+    wl.stimuli = [I.Stimulus(np.arange(wl.n_nodes), 1.0, 2.0, amp, period=300.0, count=2)]
+    g, ga, _, gs = run_gpu(wl, 4000, 100, precision="fp64")
+    o, oa, sim = run_oracle(wl, 4000, 100)
+    scale = 100.0 if model == "ms" else 1.0
+    assert float(np.max(np.abs(g - o))) * scale <= 1e-6
+    np.testing.assert_allclose(gs, sim.S, rtol=1e-9, atol=1e-12)
+    assert np.all(ga >= 0) and float(np.max(np.abs(ga - oa))) <= 1e-9
