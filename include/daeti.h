@@ -148,6 +148,13 @@ int daeti_add_stimulus(daeti_ctx* ctx, const int64_t* nodes, int64_t n_nodes,
  * ENOMEM, ECUDA. */
 int daeti_prepare(daeti_ctx* ctx);
 
+/* Replace the conductivity after prepare (same mesh and layout) keeping the
+ * prepared schedule (dt, l, k_max): reassembles K, recomputes dt_s and
+ * lambda_max, and returns DAETI_EUNSTABLE if dt_ad * lambda_max >= 2.  The
+ * state is kept.  Used for parameter studies and gradient checks. */
+int daeti_update_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
+                              const double* d_trans, const double* fibre);
+
 /* Stability data computed by prepare (any pointer may be NULL). */
 int daeti_get_stability(daeti_ctx* ctx, double* dt_s, double* lambda_max, int* l,
                         int* k_max, double* dt_eff);
@@ -212,6 +219,28 @@ typedef struct daeti_tuning {
 } daeti_tuning;
 int daeti_get_tuning(daeti_ctx* ctx, daeti_tuning* tuning);
 int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);
+
+/* Discrete adjoint (Mitchell-Schaeffer cells, structured grid, isotropic
+ * per-element D).  From the current state, runs n_steps steps and returns
+ *   *loss = sum_j sum_s (v_{sensors[s]}(t_j) - data[j*n_sensors + s])^2
+ * with samples t_j after steps sample_every, 2*sample_every, ... (n_samples =
+ * n_steps / sample_every rows of data), and its gradient for the schedule the
+ * run chose (k per node and step, gate branch per sub-step, held fixed):
+ * grad_d[e] = dL/dD_e (n_elem doubles) and *grad_tau_close = dL/dtau_close.
+ * States are recomputed from n_slots device checkpoints (binomial schedule);
+ * one slot holds the start, n_slots >= 1.  Sensors must be distinct.  The
+ * context's state and time are unchanged on return.
+ * flags: DAETI_ADJ_RECORD (forward and loss only, recording the schedule),
+ * DAETI_ADJ_REPLAY (forward and loss only, with the recorded schedule; same
+ * sensors/samples/slots as the recording), DAETI_ADJ_NO_GRADIENT (forward and
+ * loss only).  Errors: EUNSUPPORTED (other models/meshes, anisotropy),
+ * ESTATE (replay without a recording). */
+#define DAETI_ADJ_RECORD 1
+#define DAETI_ADJ_REPLAY 2
+#define DAETI_ADJ_NO_GRADIENT 4
+int daeti_adjoint(daeti_ctx* ctx, const int64_t* sensors, int n_sensors, int sample_every,
+                  const double* data, int64_t n_steps, int n_slots, int flags, double* loss,
+                  double* grad_d, double* grad_tau_close);
 
 /* Per-kernel timing (CUDA events around every launch of the plain-launch
  * path; graphs are not used while it is on).  which: 0 reaction,

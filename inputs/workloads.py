@@ -290,7 +290,9 @@ def ms_adjoint_2d(n: int = 256, h: float = 0.025, t_end: float = 200.0, n_sensor
     """Adjoint workload: n x n MS tissue with a log-normal nodal D field.
 
     Returns (workload, nodal_D, sensors, sample_dt).  Element D is the mean of
-    its 4 nodal values (done by the consumers, not here).
+    its 4 nodal values (done by the consumers, not here).  The left-column
+    stimulus uses twice the square's amplitude (the field lowers D in places,
+    which raises the capture threshold).
     """
     d_node = lognormal_field_2d(n, h, seed_index=seed_index)
     rng = np.random.default_rng(SEED_BASE + 10 + seed_index)
@@ -301,7 +303,7 @@ def ms_adjoint_2d(n: int = 256, h: float = 0.025, t_end: float = 200.0, n_sensor
         name=f"ms_adjoint_{n}x{n}", model="ms", model_params=MS_DEFAULT_PARAMS, t_end=t_end,
         v_threshold=0.5, dim=2, n=(n, n, 1), h=h,
         d_long=np.zeros(ne), d_trans=np.zeros(ne), fibre=np.tile([1.0, 0.0, 0.0], (ne, 1)),
-        stimuli=[Stimulus(left, 0.0, 1.0, 0.1)],
+        stimuli=[Stimulus(left, 0.0, 1.0, 2.0 * MS_SQUARE_AMP)],
     )
     return wl, d_node, sensors, sample_dt
 

@@ -1,0 +1,79 @@
+"""torch.autograd wrapper of the discrete adjoint (libdaeti's daeti_adjoint).
+
+``MonodomainMisfit.apply(d_node, tau_close, problem)`` returns the sensor
+misfit L = sum_j sum_s (v_s(t_j) - d_js)^2 of a Mitchell-Schaeffer tissue on
+a structured grid whose element conductivity is the mean of its nodal values,
+and back-propagates dL/d(d_node) and dL/d(tau_close).  The library computes the
+loss and both gradients in one call (forward with binomial checkpoints, then
+the reverse sweep); this wrapper only moves arrays and applies the chain rule
+of the element mean.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import binding
+
+
+@dataclasses.dataclass
+class MisfitProblem:
+    dim: int
+    n: tuple
+    h: float
+    ms_params: tuple            # tau_in, tau_out, tau_open, tau_close (replaced), v_gate
+    stimuli: list               # objects with nodes, t_start, duration, amplitude, period, count
+    sensors: np.ndarray
+    data: np.ndarray            # (n_samples, n_sensors)
+    n_steps: int
+    sample_every: int = 10
+    n_slots: int = 32
+    precision: str = "fp32_kahan"
+    dt: float = 0.1
+
+    def elements(self):
+        nx, ny = self.n[0], self.n[1]
+        nz = self.n[2] if self.dim == 3 else 1
+        ez_n = nz - 1 if self.dim == 3 else 1
+        ez, ey, ex = np.meshgrid(np.arange(ez_n), np.arange(ny - 1), np.arange(nx - 1), indexing="ij")
+        base = (ex + nx * (ey + ny * ez)).ravel()
+        offs = [(a & 1) + nx * ((a >> 1) & 1) + nx * ny * ((a >> 2) & 1) for a in range(2 ** self.dim)]
+        return base[:, None] + np.array(offs)[None, :]
+
+
+def _solve(problem: MisfitProblem, d_node: np.ndarray, tau_close: float):
+    conn = problem.elements()
+    d_elem = d_node[conn].mean(axis=1)
+    params = list(problem.ms_params)
+    params[3] = float(tau_close)
+    s = binding.Solver(precision=problem.precision, dt=problem.dt, graph_steps=0)
+    try:
+        s.daeti_set_mesh_grid(problem.dim, problem.n, problem.h)
+        s.daeti_set_conductivity(d_elem, d_elem, None)
+        s.daeti_set_cell_model("ms", tuple(params))
+        for st in problem.stimuli:
+            s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
+        s.daeti_prepare()
+        loss, g_elem, g_tau = s.daeti_adjoint(problem.sensors, problem.data, problem.n_steps,
+                                              problem.sample_every, problem.n_slots, 0, n_elem=conn.shape[0])
+    finally:
+        s.close()
+    g_node = np.zeros(d_node.shape[0])
+    np.add.at(g_node, conn, (g_elem / conn.shape[1])[:, None])
+    return loss, g_node, g_tau
+
+
+class MonodomainMisfit(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, d_node: torch.Tensor, tau_close: torch.Tensor, problem: MisfitProblem):
+        loss, g_node, g_tau = _solve(problem, d_node.detach().cpu().double().numpy(), float(tau_close))
+        ctx.save_for_backward(torch.as_tensor(g_node, dtype=d_node.dtype, device=d_node.device),
+                              torch.as_tensor(g_tau, dtype=tau_close.dtype, device=tau_close.device))
+        return torch.as_tensor(loss, dtype=torch.float64, device=d_node.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g_node, g_tau = ctx.saved_tensors
+        return grad_out.to(g_node.dtype) * g_node, grad_out.to(g_tau.dtype) * g_tau, None

@@ -23,7 +23,8 @@ SCHEME_DAETI, SCHEME_OSTAR, SCHEME_OST = 0, 1, 2
 L_FLOOR, L_CEIL = 0, 1
 MODEL_MS, MODEL_TP06 = 1, 2
 DTYPE_F64, DTYPE_F32 = 0, 1
-KERNEL_REACTION, KERNEL_DIFFUSION, KERNEL_BUCKET = 0, 1, 2
+KERNEL_REACTION, KERNEL_DIFFUSION, KERNEL_OTHER = 0, 1, 2
+ADJ_RECORD, ADJ_REPLAY, ADJ_NO_GRADIENT = 1, 2, 4
 
 _PREC = {"fp64": FP64, "fp32_kahan": FP32_KAHAN, "fp32": FP32}
 _SCHEME = {"daeti": SCHEME_DAETI, "ostar": SCHEME_OSTAR, "ost": SCHEME_OST}
@@ -106,6 +107,9 @@ _SIGNATURES = {
     "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+    "daeti_update_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
+    "daeti_adjoint": (ctypes.c_int, [_VP, _I64P, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_int, _DP, _DP, _DP]),
     "daeti_grid_stability_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_double, ctypes.c_int64, _DP, _DP,
                                                     _DP, _VP, _DP, _DP, ctypes.c_char_p, ctypes.c_int]),
 }
@@ -301,6 +305,25 @@ class Solver:
     def daeti_load_state(self, buf):
         b = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(self.lib.daeti_load_state(self.ctx, b.ctypes.data_as(_VP), b.shape[0]))
+
+    def daeti_update_conductivity(self, d_long, d_trans=None, fibre=None):
+        dl = _f64(d_long)
+        dtr = _f64(d_trans) if d_trans is not None else None
+        fb = _f64(fibre) if fibre is not None else None
+        self._check(self.lib.daeti_update_conductivity(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
+                                                       _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
+
+    def daeti_adjoint(self, sensors, data, n_steps, sample_every, n_slots=32, flags=0, n_elem=None):
+        """Returns (loss, dL/dD_e (n_elem,) or None, dL/dtau_close or None)."""
+        sn = _i64(sensors)
+        dd = _f64(data).reshape(-1)
+        loss = ctypes.c_double()
+        gt = ctypes.c_double()
+        grad = None if flags else np.empty(int(n_elem), dtype=np.float64)
+        self._check(self.lib.daeti_adjoint(self.ctx, _ptr(sn, ctypes.c_int64), sn.shape[0], int(sample_every),
+                                           _ptr(dd, ctypes.c_double), int(n_steps), int(n_slots), int(flags),
+                                           ctypes.byref(loss), _ptr(grad, ctypes.c_double), ctypes.byref(gt)))
+        return loss.value, grad, (None if flags else gt.value)
 
     def daeti_get_substeps(self):
         n = ctypes.c_int64()

@@ -1,0 +1,577 @@
+// Discrete adjoint of the split step (Section 2's scheme, Mitchell-Schaeffer
+// cells, structured grids with isotropic per-element D): gradients of
+//   L = sum_j sum_s (v_s(t_j) - d_js)^2
+// with respect to the element conductivities D_e and tau_close, for the
+// schedule the forward run chose (k per node and step, gate branch per
+// sub-step; these discrete choices are held fixed).
+//
+// Reverse sweep per step (costate of v kept as mu = M_L^-1 lambda while it
+// crosses diffusion, because (I - dt_ad M^-1 K)^T = M (I - dt_ad M^-1 K) M^-1
+// for symmetric K: the transposed sub-step is the forward sub-step on mu):
+//   step III^T: for each sub-step, dL/dD_e += -dt_ad mu_out^T K_e v_in, mu <- D mu
+//   step II^T : per node, the k forward-Euler sub-steps are recomputed in
+//               registers and reversed (reaction Jacobian-transpose products),
+//               dL/dtau_close accumulated
+//   step I^T  : as step III^T.
+// States are recomputed from device checkpoints placed by a binomial
+// (revolve-type) schedule: with s free slots and t steps, the next checkpoint
+// goes d = max(1, t - C(s-1+r, s-1)) steps ahead, r the least repetition
+// number with C(s+r, s) >= t.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cells.cuh"
+#include "context.h"
+#include "diffops.cuh"
+
+using namespace daeti_host;
+
+struct AdjointBuffers {
+    int64_t n = 0, n_elem = 0, n_steps_hist = 0;
+    int n_slots = 0, l = 0, n_sensors = 0, n_samples = 0;
+    bool kahan = false;
+    int prec = 0;
+    std::vector<void*> allocs;
+    // snapshots: V, C, h, vsync, act, kk per slot
+    std::vector<void*> sV, sC, sH, sVs, sA, sK;
+    std::vector<int64_t> slot_step;
+    // per-step intermediates
+    std::vector<void*> d1, d2;          // inputs of the diffusion sub-steps
+    void *rv = nullptr, *rh = nullptr;  // reaction input v, h
+    float* rc = nullptr;                // reaction input Kahan term
+    uint8_t* kused = nullptr;
+    void* vend = nullptr;
+    // costate and gradients
+    void* mu[2] = {nullptr, nullptr};
+    void* lamh = nullptr;
+    void* mR = nullptr;                  // lumped mass in the state precision
+    double* g_elem = nullptr;
+    double* acc = nullptr;               // [0] loss, [1] dL/dtau_close
+    int* sensors = nullptr;
+    void* data = nullptr;
+    // recorded schedule
+    uint8_t* hist_k = nullptr;
+    uint16_t* hist_b = nullptr;
+};
+
+namespace daeti_host {
+void free_adjoint(daeti_ctx* c) {
+    if (!c->adj) return;
+    for (void* p : c->adj->allocs) cudaFree(p);
+    delete c->adj;
+    c->adj = nullptr;
+}
+}  // namespace daeti_host
+
+namespace {
+
+// --------------------------------------------------------------- kernels
+template <typename R>
+struct AdjReactArgs {
+    int n;
+    R* V;
+    float* C;
+    R* H;
+    const uint8_t* kk;
+    uint8_t* hist_k;
+    uint16_t* hist_b;
+    const unsigned* stim_mask;
+    const StimDev* stims;
+    int n_stims;
+    double t_n, dt;
+    double dtk[DAETI_MAX_K];
+    R dtkr[DAETI_MAX_K];
+    R r_in, r_out, r_open, r_close, vgate;
+};
+
+template <typename R>
+__device__ __forceinline__ R adj_stim(unsigned mask, const StimDev* stims, double t) {
+    R J = (R)0;
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (stim_on(stims[b], t)) J += (R)stims[b].amp;
+    }
+    return J;
+}
+
+// Step A of the adjoint's forward: MODE 0 decide, 1 decide and record, 2 replay.
+template <typename R, bool KAHAN, int MODE>
+__global__ void adj_react_fwd(AdjReactArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int k = MODE == 2 ? a.hist_k[i] : a.kk[i];
+    const unsigned smask = a.n_stims ? a.stim_mask[i] : 0u;
+    const uint16_t rb = MODE == 2 ? a.hist_b[i] : 0;
+    R v = a.V[i], h = a.H[i];
+    float c = KAHAN ? a.C[i] : 0.f;
+    float* cp = KAHAN ? &c : nullptr;
+    uint16_t bits = 0;
+    for (int s = 0; s < k; ++s) {
+        const R J = smask ? adj_stim<R>(smask, a.stims, a.t_n + (double)s * a.dtk[k]) : (R)0;
+        const bool low = MODE == 2 ? ((rb >> s) & 1) != 0 : v < a.vgate;
+        bits |= (uint16_t)(low ? 1u << s : 0u);
+        ms_substep_b(v, cp, h, a.dtkr[k], J, a.r_in, a.r_out, a.r_open, a.r_close, low);
+    }
+    a.V[i] = v;
+    a.H[i] = h;
+    if (KAHAN) a.C[i] = c;
+    if (MODE == 1) {
+        a.hist_k[i] = (uint8_t)k;
+        a.hist_b[i] = bits;
+    }
+}
+
+// Reverse of step A per node: recompute the sub-steps, then transpose them.
+template <typename R, bool KAHAN>
+__global__ void adj_react_bwd(AdjReactArgs<R> a, const R* __restrict__ rv, const float* __restrict__ rc,
+                              const R* __restrict__ rh, const uint8_t* __restrict__ kused, R* mu, R* lamh,
+                              const R* __restrict__ m, double* g_tau) {
+    __shared__ double red[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double gt = 0.0;
+    if (i < a.n) {
+        const int k = kused[i];
+        const unsigned smask = a.n_stims ? a.stim_mask[i] : 0u;
+        R vs[DAETI_MAX_K], hs[DAETI_MAX_K];
+        bool lows[DAETI_MAX_K];
+        R v = rv[i], h = rh[i];
+        float c = KAHAN ? rc[i] : 0.f;
+        float* cp = KAHAN ? &c : nullptr;
+        const R dt = a.dtkr[k];
+#pragma unroll 1
+        for (int s = 0; s < k; ++s) {
+            const R J = smask ? adj_stim<R>(smask, a.stims, a.t_n + (double)s * a.dtk[k]) : (R)0;
+            const bool low = v < a.vgate;
+            vs[s] = v;
+            hs[s] = h;
+            lows[s] = low;
+            ms_substep_b(v, cp, h, dt, J, a.r_in, a.r_out, a.r_open, a.r_close, low);
+        }
+        R lv = mu[i] * m[i];
+        R lh = lamh[i];
+#pragma unroll 1
+        for (int s = k - 1; s >= 0; --s) {
+            const R vi = vs[s], hi = hs[s];
+            const R fv = hi * ((R)2 * vi - (R)3 * vi * vi) * a.r_in - a.r_out;
+            const R fh = vi * vi * ((R)1 - vi) * a.r_in;
+            const R gh = lows[s] ? -a.r_open : -a.r_close;
+            if (!lows[s]) gt += (double)lh * (double)dt * (double)hi * (double)a.r_close * (double)a.r_close;
+            const R nlv = ((R)1 + dt * fv) * lv;
+            lh = dt * fh * lv + ((R)1 + dt * gh) * lh;
+            lv = nlv;
+        }
+        mu[i] = lv / m[i];
+        lamh[i] = lh;
+    }
+    for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        gt = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
+        if (threadIdx.x == 0 && gt != 0.0) atomicAdd(g_tau, gt);
+    }
+}
+
+struct Kref {
+    double k[64];
+};
+
+// dL/dD_e += -dt_ad mu_out^T K_e v_in on element e of a structured grid.
+template <typename R>
+__global__ void adj_dgrad(int64_t n_elem, int dim, int nx, int ny, const R* __restrict__ mu,
+                          const R* __restrict__ vin, double dt_ad, Kref kr, double* g) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    const int ex = (int)(e % (nx - 1));
+    const int64_t t = e / (nx - 1);
+    const int ey = (int)(t % (ny - 1));
+    const int ez = (int)(t / (ny - 1));
+    const int nl = 1 << dim;
+    int node[8];
+    for (int a = 0; a < nl; ++a)
+        node[a] = (ex + (a & 1)) + nx * ((ey + ((a >> 1) & 1)) + ny * (ez + ((a >> 2) & 1)));
+    double s = 0.0;
+    for (int a = 0; a < nl; ++a) {
+        double r = 0.0;
+        for (int b = 0; b < nl; ++b) r += kr.k[a * nl + b] * (double)vin[node[b]];
+        s += (double)mu[node[a]] * r;
+    }
+    g[e] += -dt_ad * s;
+}
+
+template <typename R>
+__global__ void adj_loss_inject(int n_s, const int* __restrict__ sensors, const R* __restrict__ v,
+                                const R* __restrict__ d, const R* __restrict__ m, R* mu, double* loss, int inject) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n_s; q += blockDim.x) {
+        const int i = sensors[q];
+        const double r = (double)v[i] - (double)d[q];
+        acc += r * r;
+        if (inject) mu[i] += (R)(2.0 * r) / m[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) loss[0] += acc;
+    }
+}
+
+// --------------------------------------------------------------- host side
+template <typename R>
+AdjReactArgs<R> react_args(daeti_ctx* c, int buf, int64_t step, uint8_t* hk, uint16_t* hb) {
+    AdjReactArgs<R> a;
+    a.n = (int)c->n_nodes;
+    a.V = (R*)c->s.V[buf];
+    a.C = c->s.kahan ? c->s.C[buf] : nullptr;
+    a.H = (R*)c->s.S;
+    a.kk = c->s.kk;
+    a.hist_k = hk;
+    a.hist_b = hb;
+    a.stim_mask = c->s.stim_mask;
+    a.stims = c->s.stims;
+    a.n_stims = c->s.stim_mask ? c->s.n_stims : 0;
+    a.dt = c->dt_eff;
+    a.t_n = (double)step * c->dt_eff;
+    for (int k = 0; k < DAETI_MAX_K; ++k) {
+        a.dtk[k] = k ? c->dt_eff / k : c->dt_eff;
+        a.dtkr[k] = (R)a.dtk[k];
+    }
+    a.r_in = (R)(1.0 / c->margs.ms[0]);
+    a.r_out = (R)(1.0 / c->margs.ms[1]);
+    a.r_open = (R)(1.0 / c->margs.ms[2]);
+    a.r_close = (R)(1.0 / c->margs.ms[3]);
+    a.vgate = (R)c->margs.ms[4];
+    return a;
+}
+
+struct Adj {
+    daeti_ctx* c;
+    AdjointBuffers* b;
+    cudaStream_t st;
+    int64_t n0;          // absolute step index of the adjoint's step 0
+    int sample_every;
+    int mode;            // 0 decide, 1 record, 2 replay
+    int mu_cur = 0;
+    int64_t fwd_steps = 0;
+    size_t R() const { return rsize(c); }
+
+    void copy(void* dst, const void* src, size_t bytes) { cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st); }
+
+    void save(int slot, int64_t step) {
+        const size_t N = c->n_nodes, r = R();
+        copy(b->sV[slot], c->s.V[c->cur], N * r);
+        if (b->kahan) copy(b->sC[slot], c->s.C[c->cur], N * 4);
+        copy(b->sH[slot], c->s.S, N * r);
+        copy(b->sVs[slot], c->s.vsync, N * r);
+        copy(b->sA[slot], c->s.act, N * r);
+        copy(b->sK[slot], c->s.kk, N);
+        b->slot_step[slot] = step;
+    }
+    void restore(int slot) {
+        const size_t N = c->n_nodes, r = R();
+        copy(c->s.V[c->cur], b->sV[slot], N * r);
+        if (b->kahan) copy(c->s.C[c->cur], b->sC[slot], N * 4);
+        copy(c->s.S, b->sH[slot], N * r);
+        copy(c->s.vsync, b->sVs[slot], N * r);
+        copy(c->s.act, b->sA[slot], N * r);
+        copy(c->s.kk, b->sK[slot], N);
+    }
+
+    template <typename T, bool K>
+    void react_fwd(int buf, int64_t j) {
+        const int n = (int)c->n_nodes;
+        uint8_t* hk = b->hist_k ? b->hist_k + (size_t)j * n : nullptr;
+        uint16_t* hb = b->hist_b ? b->hist_b + (size_t)j * n : nullptr;
+        AdjReactArgs<T> a = react_args<T>(c, buf, n0 + j, hk, hb);
+        const int grid = (n + 127) / 128;
+        if (mode == 2) adj_react_fwd<T, K, 2><<<grid, 128, 0, st>>>(a);
+        else if (mode == 1) adj_react_fwd<T, K, 1><<<grid, 128, 0, st>>>(a);
+        else adj_react_fwd<T, K, 0><<<grid, 128, 0, st>>>(a);
+    }
+
+    // One forward step j (from the synchronisation at t_j), optionally keeping
+    // every intermediate the reverse of this step needs.
+    void fwd_step(int64_t j, bool store) {
+        const size_t N = c->n_nodes, r = R();
+        const StepRef ref{nullptr, (long long)(n0 + j)};
+        int buf = c->cur;
+        for (int i = 0; i < c->l; ++i) {
+            if (store) copy(b->d1[i], c->s.V[buf], N * r);
+            launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
+            buf ^= 1;
+        }
+        if (store) {
+            copy(b->rv, c->s.V[buf], N * r);
+            if (b->kahan) copy(b->rc, c->s.C[buf], N * 4);
+            copy(b->rh, c->s.S, N * r);
+            copy(b->kused, c->s.kk, N);
+        }
+        if (c->s.prec == P_F64) react_fwd<double, false>(buf, j);
+        else if (c->s.kahan) react_fwd<float, true>(buf, j);
+        else react_fwd<float, false>(buf, j);
+        for (int i = 0; i < c->l; ++i) {
+            if (store) copy(b->d2[i], c->s.V[buf], N * r);
+            launch_diffusion(c->s, c->op, buf, i == c->l - 1, 0, c->sargs, ref, false, 256, st);
+            buf ^= 1;
+        }
+        if (store) copy(b->vend, c->s.V[buf], N * r);
+        ++fwd_steps;
+    }
+
+    // Loss term of the sample taken at the end of step j (and, with inject, its adjoint source).
+    template <typename T>
+    void loss_at(int64_t j, const void* v, bool inject) {
+        if ((j + 1) % sample_every) return;
+        const int64_t q = (j + 1) / sample_every - 1;
+        if (q >= b->n_samples) return;
+        adj_loss_inject<T><<<1, 256, 0, st>>>(b->n_sensors, b->sensors, (const T*)v,
+                                              (const T*)b->data + (size_t)q * b->n_sensors, (const T*)b->mR,
+                                              (T*)b->mu[mu_cur], b->acc, inject ? 1 : 0);
+    }
+
+    template <typename T>
+    void dgrad(const void* vin) {
+        Kref kr;
+        std::memcpy(kr.k, c->kref, sizeof(kr.k));
+        const int64_t ne = c->n_elem;
+        adj_dgrad<T><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, c->dim, (int)c->n[0], (int)c->n[1],
+                                                                   (const T*)b->mu[mu_cur], (const T*)vin,
+                                                                   c->dt_ad, kr, b->g_elem);
+    }
+
+    void mu_substep() {
+        DevState view = c->s;
+        view.V[0] = b->mu[0];
+        view.V[1] = b->mu[1];
+        view.C[0] = view.C[1] = nullptr;
+        view.kahan = false;
+        launch_diffusion(view, c->op, mu_cur, false, 0, c->sargs, StepRef{nullptr, 0}, false, 256, st);
+        mu_cur ^= 1;
+    }
+
+    template <typename T, bool K>
+    void react_bwd(int64_t j) {
+        const int n = (int)c->n_nodes;
+        AdjReactArgs<T> a = react_args<T>(c, c->cur, n0 + j, nullptr, nullptr);
+        adj_react_bwd<T, K><<<(n + 127) / 128, 128, 0, st>>>(a, (const T*)b->rv, b->rc, (const T*)b->rh, b->kused,
+                                                            (T*)b->mu[mu_cur], (T*)b->lamh, (const T*)b->mR,
+                                                            b->acc + 1);
+    }
+
+    // Reverse of step j (the intermediates of fwd_step(j, true) are in place).
+    template <typename T, bool K>
+    void rev_step_t(int64_t j) {
+        loss_at<T>(j, b->vend, true);
+        for (int i = c->l - 1; i >= 0; --i) {
+            dgrad<T>(b->d2[i]);
+            mu_substep();
+        }
+        react_bwd<T, K>(j);
+        for (int i = c->l - 1; i >= 0; --i) {
+            dgrad<T>(b->d1[i]);
+            mu_substep();
+        }
+    }
+    void rev_step(int64_t j) {
+        if (c->s.prec == P_F64) rev_step_t<double, false>(j);
+        else if (c->s.kahan) rev_step_t<float, true>(j);
+        else rev_step_t<float, false>(j);
+    }
+
+    static double beta(int s, int r) {   // C(s + r, s), saturating
+        double v = 1.0;
+        for (int i = 1; i <= s; ++i) {
+            v = v * (double)(r + i) / (double)i;
+            if (v > 1e18) return 1e18;
+        }
+        return v;
+    }
+
+    int free_slot() {
+        for (int q = 0; q < b->n_slots; ++q)
+            if (b->slot_step[q] < 0) return q;
+        return -1;
+    }
+
+    // Reverse steps [a, e) given a checkpoint of step a in slot sa.
+    void reverse(int64_t a, int64_t e, int sa) {
+        const int64_t t = e - a;
+        if (t == 1) {
+            restore(sa);
+            fwd_step(a, true);
+            rev_step(a);
+            return;
+        }
+        const int q = free_slot();
+        if (q < 0) {
+            for (int64_t j = e - 1; j >= a; --j) {
+                restore(sa);
+                for (int64_t p = a; p < j; ++p) fwd_step(p, false);
+                fwd_step(j, true);
+                rev_step(j);
+            }
+            return;
+        }
+        int free = 0;
+        for (int p = 0; p < b->n_slots; ++p) free += b->slot_step[p] < 0;
+        int r = 0;
+        while (beta(free, r) < (double)t) ++r;
+        int64_t d = t - (int64_t)beta(free - 1, r);
+        if (d < 1) d = 1;
+        if (d > t - 1) d = t - 1;
+        restore(sa);
+        for (int64_t p = a; p < a + d; ++p) fwd_step(p, false);
+        save(q, a + d);
+        reverse(a + d, e, q);
+        b->slot_step[q] = -1;
+        reverse(a, a + d, sa);
+    }
+};
+
+int ensure_buffers(daeti_ctx* c, int n_slots, int n_sensors, int n_samples, int64_t hist_steps, bool keep) {
+    AdjointBuffers* b = c->adj;
+    const int64_t N = c->n_nodes;
+    const bool same = b && b->n == N && b->n_slots == n_slots && b->l == c->l && b->n_sensors == n_sensors &&
+                      b->n_samples == n_samples && b->n_steps_hist >= hist_steps && b->prec == c->s.prec &&
+                      b->kahan == c->s.kahan;
+    if (same) return DAETI_OK;
+    if (keep) return fail(c, DAETI_ESTATE, "replay must use the sensors, samples and slots of the recording");
+    free_adjoint(c);
+    b = c->adj = new AdjointBuffers();
+    b->n = N;
+    b->n_elem = c->n_elem;
+    b->n_slots = n_slots;
+    b->l = c->l;
+    b->n_sensors = n_sensors;
+    b->n_samples = n_samples;
+    b->n_steps_hist = hist_steps;
+    b->prec = c->s.prec;
+    b->kahan = c->s.kahan;
+    const size_t r = rsize(c);
+    auto al = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+        b->allocs.push_back(p);
+        return p;
+    };
+    bool ok = true;
+    for (int q = 0; q < n_slots; ++q) {
+        b->sV.push_back(al(N * r));
+        b->sC.push_back(b->kahan ? al(N * 4) : nullptr);
+        b->sH.push_back(al(N * r));
+        b->sVs.push_back(al(N * r));
+        b->sA.push_back(al(N * r));
+        b->sK.push_back(al(N));
+        ok = ok && b->sV.back() && b->sH.back() && b->sVs.back() && b->sA.back() && b->sK.back() &&
+             (!b->kahan || b->sC.back());
+    }
+    b->slot_step.assign(n_slots, -1);
+    for (int i = 0; i < c->l; ++i) {
+        b->d1.push_back(al(N * r));
+        b->d2.push_back(al(N * r));
+        ok = ok && b->d1.back() && b->d2.back();
+    }
+    b->rv = al(N * r);
+    b->rh = al(N * r);
+    b->rc = b->kahan ? (float*)al(N * 4) : nullptr;
+    b->kused = (uint8_t*)al(N);
+    b->vend = al(N * r);
+    b->mu[0] = al(N * r);
+    b->mu[1] = al(N * r);
+    b->lamh = al(N * r);
+    b->mR = al(N * r);
+    b->g_elem = (double*)al(8 * c->n_elem);
+    b->acc = (double*)al(16);
+    b->sensors = (int*)al(4 * (size_t)std::max(1, n_sensors));
+    b->data = al(r * (size_t)std::max(1, n_sensors) * std::max(1, n_samples));
+    if (hist_steps > 0) {
+        b->hist_k = (uint8_t*)al((size_t)hist_steps * N);
+        b->hist_b = (uint16_t*)al((size_t)hist_steps * N * 2);
+        ok = ok && b->hist_k && b->hist_b;
+    }
+    ok = ok && b->rv && b->rh && b->kused && b->vend && b->mu[0] && b->mu[1] && b->lamh && b->mR && b->g_elem &&
+         b->acc && b->sensors && b->data && (!b->kahan || b->rc);
+    if (!ok) {
+        free_adjoint(c);
+        return fail(c, DAETI_ENOMEM, "adjoint buffers");
+    }
+    return DAETI_OK;
+}
+
+}  // namespace
+
+extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors, int sample_every, const double* data,
+                             int64_t n_steps, int n_slots, int flags, double* loss, double* grad_d,
+                             double* grad_tau_close) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (c->model != DAETI_MODEL_MS || c->mesh_kind != 1)
+        return fail(c, DAETI_EUNSUPPORTED, "the adjoint supports Mitchell-Schaeffer on structured grids");
+    for (int64_t e = 0; e < c->n_elem; ++e)
+        if (c->dl[e] != c->dtr[e]) return fail(c, DAETI_EUNSUPPORTED, "the adjoint needs isotropic elements");
+    if (n_steps < 1 || n_sensors < 1 || n_sensors > 65536 || sample_every < 1 || !sensors || !data || n_slots < 1)
+        return fail(c, DAETI_EINVAL, "bad adjoint arguments");
+    const bool record = (flags & DAETI_ADJ_RECORD) != 0, replay = (flags & DAETI_ADJ_REPLAY) != 0;
+    const bool no_grad = (flags & DAETI_ADJ_NO_GRADIENT) != 0 || replay || record;
+    if (record && replay) return fail(c, DAETI_EINVAL, "record and replay are exclusive");
+    for (int q = 0; q < n_sensors; ++q)
+        if (sensors[q] < 0 || sensors[q] >= c->n_nodes) return fail(c, DAETI_EINVAL, "sensor out of range");
+    const int n_samples = (int)(n_steps / sample_every);
+    if (replay && (!c->adj || !c->adj->hist_k || c->adj->n_steps_hist < n_steps))
+        return fail(c, DAETI_ESTATE, "replay needs a recorded schedule of at least n_steps");
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    const int64_t hist = (record || replay) ? std::max<int64_t>(n_steps, c->adj ? c->adj->n_steps_hist : 0) : 0;
+    if ((rc = ensure_buffers(c, n_slots, n_sensors, n_samples, replay ? c->adj->n_steps_hist : hist, replay)))
+        return rc;
+    AdjointBuffers* b = c->adj;
+    const int64_t N = c->n_nodes;
+    const size_t r = rsize(c);
+    cudaStream_t st = c->stream;
+    // inputs in the state precision
+    std::vector<int> hs(sensors, sensors + n_sensors);
+    CK(cpy_(c, b->sensors, hs.data(), 4 * (size_t)n_sensors, cudaMemcpyHostToDevice));
+    if (n_samples > 0) {
+        int e2 = upload_real(c, b->data, data, (int64_t)n_samples * n_sensors);
+        if (e2) return e2;
+    }
+    if ((rc = upload_real(c, b->mR, c->mass.data(), N))) return rc;
+    CK(cudaMemsetAsync(b->acc, 0, 16, st));
+
+    Adj A{c, b, st, c->nstep, sample_every, record ? 1 : (replay ? 2 : 0)};
+    std::fill(b->slot_step.begin(), b->slot_step.end(), -1);
+    A.save(0, 0);
+    if (no_grad) {
+        for (int64_t j = 0; j < n_steps; ++j) {
+            A.fwd_step(j, false);
+            if (c->s.prec == P_F64) A.loss_at<double>(j, c->s.V[c->cur], false);
+            else A.loss_at<float>(j, c->s.V[c->cur], false);
+        }
+    } else {
+        CK(cudaMemsetAsync(b->mu[0], 0, N * r, st));
+        CK(cudaMemsetAsync(b->mu[1], 0, N * r, st));
+        CK(cudaMemsetAsync(b->lamh, 0, N * r, st));
+        CK(cudaMemsetAsync(b->g_elem, 0, 8 * (size_t)c->n_elem, st));
+        A.reverse(0, n_steps, 0);
+    }
+    A.restore(0);   // the context keeps its starting state
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    double acc[2];
+    CK(cpy_(c, acc, b->acc, 16, cudaMemcpyDeviceToHost));
+    if (loss) *loss = acc[0];
+    if (!no_grad) {
+        if (grad_tau_close) *grad_tau_close = acc[1];
+        if (grad_d) CK(cpy_(c, grad_d, b->g_elem, 8 * (size_t)c->n_elem, cudaMemcpyDeviceToHost));
+    }
+    c->adj_fwd_steps = A.fwd_steps;
+    return DAETI_OK;
+}

@@ -8,80 +8,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/daeti.h"
 #include "assembly.h"
-#include "kernels.h"
+#include "context.h"
 
-using namespace daeti;
+using namespace daeti_host;
 
-struct StimHost {
-    std::vector<int64_t> nodes;
-    double t0, dur, amp, period;
-    int count;
-};
-
-struct daeti_ctx {
-    daeti_options opt;
-    std::string err;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    bool own_stream = false;
-    // inputs
-    int mesh_kind = 0;   // 1 grid, 2 tets
-    int dim = 0;
-    int64_t n[3] = {1, 1, 1};
-    double h = 0.0;
-    int64_t n_nodes = 0, n_elem = 0;
-    std::vector<double> xyz;
-    std::vector<int64_t> tets;
-    bool have_cond = false;
-    std::vector<double> dl, dtr, fib;
-    bool fib_null = true;
-    int model = 0;
-    std::vector<double> params;
-    std::vector<StimHost> stims;
-    // prepared
-    bool prepared = false;
-    DevState s;
-    DiffOp op;
-    ModelArgs margs;
-    SyncArgs sargs;
-    double dt_eff = 0.1, dt_s = 0.0, lam = 0.0, dt_ad = 0.0;
-    int l = 1, kmax = 1;
-    int64_t nstep = 0;
-    int cur = 0;
-    int par = 0;
-    void* scratch = nullptr;   // n doubles for conversions
-    std::vector<void*> allocs;
-    // launch shapes
-    ReactTuning rtune;
-    int diff_block = 256;
-    bool fused = true;          // last sub-step of step I inside the reaction launch
-    bool lists = true;
-    int graph_steps = 20;
-    // graphs of graph_steps steps, keyed by (start V buffer, list parity)
-    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
-    // profiling
-    bool prof = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double ktime[3] = {0, 0, 0};
-    int64_t klaunch[3] = {0, 0, 0};
-};
-
-namespace {
+namespace daeti_host {
 
 int fail(daeti_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
     return code;
 }
-
-#define CK(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess)                                                                     \
-            return fail(c, e_ == cudaErrorMemoryAllocation ? DAETI_ENOMEM : DAETI_ECUDA,           \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
-    } while (0)
 
 // Copies and fills on the context's stream, completed before returning (the
 // legacy default stream does not order against the library's streams).
@@ -109,31 +46,7 @@ int dalloc(daeti_ctx* c, void** p, size_t bytes) {
     return DAETI_OK;
 }
 
-void drop_graphs(daeti_ctx* c) {
-    for (int i = 0; i < 4; ++i)
-        if (c->graphs[i]) {
-            cudaGraphExecDestroy(c->graphs[i]);
-            c->graphs[i] = nullptr;
-        }
-}
-
-void free_device(daeti_ctx* c) {
-    drop_graphs(c);
-    for (void* p : c->allocs) cudaFree(p);
-    c->allocs.clear();
-    c->s = DevState();
-    c->op = DiffOp();
-    c->scratch = nullptr;
-    c->prepared = false;
-}
-
 size_t rsize(const daeti_ctx* c) { return c->s.prec == P_F64 ? 8 : 4; }
-
-int n_states_of(int model) { return model == DAETI_MODEL_MS ? 2 : 19; }
-
-// published initial states
-const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
-                              0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
 
 // host double -> device in state precision
 int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
@@ -146,6 +59,36 @@ int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
     }
     return DAETI_OK;
 }
+
+}  // namespace daeti_host
+
+namespace {
+
+void drop_graphs(daeti_ctx* c) {
+    for (int i = 0; i < 4; ++i)
+        if (c->graphs[i]) {
+            cudaGraphExecDestroy(c->graphs[i]);
+            c->graphs[i] = nullptr;
+        }
+}
+
+void free_device(daeti_ctx* c) {
+    drop_graphs(c);
+    free_adjoint(c);
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->s = DevState();
+    c->op = DiffOp();
+    c->scratch = nullptr;
+    c->prepared = false;
+}
+
+
+int n_states_of(int model) { return model == DAETI_MODEL_MS ? 2 : 19; }
+
+// published initial states
+const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
+                              0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
 
 StepRef plain_ref(int64_t n) { return StepRef{nullptr, (long long)n}; }
 
@@ -466,24 +409,13 @@ static int power_iteration(daeti_ctx* c, const EstOp& est, const double* d_m, do
     return DAETI_OK;
 }
 
-int daeti_prepare(daeti_ctx* c) {
-    if (!c) return DAETI_EINVAL;
-    if (c->prepared) return fail(c, DAETI_ESTATE, "already prepared");
-    if (!c->mesh_kind || !c->have_cond || !c->model)
-        return fail(c, DAETI_ESTATE, "prepare needs mesh, conductivity and cell model");
+// Assemble K and M_L for the current conductivity; FP64 dt_s (Eq. 3) and
+// lambda_max on the GPU; host copy of the lumped mass.
+static int assemble_and_estimate(daeti_ctx* c, GridTable& tab, bool& table, CsrK& K) {
     const int64_t N = c->n_nodes;
-    c->s = DevState();
-    c->s.prec = c->opt.precision == DAETI_FP64 ? P_F64 : P_F32;
-    c->s.kahan = c->opt.precision == DAETI_FP32_KAHAN;
-    c->s.n = N;
-    c->s.n_states = n_states_of(c->model);
     const double* fib = c->fib_null ? nullptr : c->fib.data();
-
-    // ---- assembly and FP64 stable-step estimate
-    GridTable tab;
-    bool table = false;
-    CsrK K;
     std::string err;
+    table = false;
     if (c->mesh_kind == 1) table = build_grid_table(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, tab);
     if (!table) {
         bool ok = c->mesh_kind == 1
@@ -491,6 +423,20 @@ int daeti_prepare(daeti_ctx* c) {
                       : assemble_tet_csr(N, c->xyz.data(), c->n_elem, c->tets.data(), c->dl.data(), c->dtr.data(),
                                          fib, K, err);
         if (!ok) return fail(c, DAETI_EINVAL, err);
+    }
+    c->mass.assign(N, 0.0);
+    if (table) {
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t x = i % c->n[0], y = (i / c->n[0]) % c->n[1], z = i / (c->n[0] * c->n[1]);
+            const int cx = x == 0 ? 0 : (x == c->n[0] - 1 ? 2 : 1), cy = y == 0 ? 0 : (y == c->n[1] - 1 ? 2 : 1);
+            c->mass[i] = tab.m[(z * 3 + cy) * 3 + cx];
+        }
+    } else {
+        c->mass = K.m;
+    }
+    if (c->mesh_kind == 1) {
+        double I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        box_stiffness(c->dim, c->h, I3, c->kref);
     }
     EstOp est;
     est.n = N;
@@ -506,7 +452,9 @@ int daeti_prepare(daeti_ctx* c) {
         tmp.clear();
     };
     Sell32 sell;
-    double* d_m = nullptr;
+    double* d_m = (double*)tmalloc(N * 8);
+    if (!d_m) return fail(c, DAETI_ENOMEM, "estimator buffers");
+    cpy_(c, d_m, c->mass.data(), N * 8, cudaMemcpyHostToDevice);
     if (table) {
         est.kind = 0;
         est.dim = c->dim;
@@ -515,8 +463,7 @@ int daeti_prepare(daeti_ctx* c) {
         est.nz = tab.nz;
         double* kt = (double*)tmalloc(tab.K.size() * 8);
         double* mt = (double*)tmalloc(tab.m.size() * 8);
-        d_m = (double*)tmalloc(N * 8);
-        if (!kt || !mt || !d_m) {
+        if (!kt || !mt) {
             free_tmp();
             return fail(c, DAETI_ENOMEM, "estimator buffers");
         }
@@ -524,7 +471,6 @@ int daeti_prepare(daeti_ctx* c) {
         cpy_(c, mt, tab.m.data(), tab.m.size() * 8, cudaMemcpyHostToDevice);
         est.ktab = kt;
         est.mtab = mt;
-        launch_node_mass(est, d_m, c->stream);
         est.m = d_m;
     } else {
         csr_to_sell32(K, nullptr, sell);
@@ -535,8 +481,7 @@ int daeti_prepare(daeti_ctx* c) {
         int* col = (int*)tmalloc(sell.col.size() * 4);
         double* kv = (double*)tmalloc(sell.val.size() * 8);
         double* kd = (double*)tmalloc(N * 8);
-        d_m = (double*)tmalloc(N * 8);
-        if (!cp || !cw || !col || !kv || !kd || !d_m) {
+        if (!cp || !cw || !col || !kv || !kd) {
             free_tmp();
             return fail(c, DAETI_ENOMEM, "estimator buffers");
         }
@@ -545,7 +490,6 @@ int daeti_prepare(daeti_ctx* c) {
         cpy_(c, col, sell.col.data(), sell.col.size() * 4, cudaMemcpyHostToDevice);
         cpy_(c, kv, sell.val.data(), sell.val.size() * 8, cudaMemcpyHostToDevice);
         cpy_(c, kd, sell.diag.data(), N * 8, cudaMemcpyHostToDevice);
-        cpy_(c, d_m, K.m.data(), N * 8, cudaMemcpyHostToDevice);
         est.chunk_ptr = cp;
         est.chunk_w = cw;
         est.col = col;
@@ -574,14 +518,80 @@ int daeti_prepare(daeti_ctx* c) {
         std::memcpy(&mn, &hb, 8);
         c->dt_s = 0.9 * mn;
     }
-    {
-        int rc = power_iteration(c, est, d_m, &c->lam);
-        if (rc) {
-            free_tmp();
-            return rc;
-        }
-    }
+    int rc = power_iteration(c, est, d_m, &c->lam);
     free_tmp();
+    return rc;
+}
+
+// Time-stepping operator a_ij = dt_ad k_ij / m_i in the state precision;
+// allocates on the first call, overwrites in place afterwards.
+static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const CsrK& K) {
+    const int64_t N = c->n_nodes;
+    const size_t R = rsize(c);
+    int rc = 0;
+    void* p = nullptr;
+    const bool fresh = c->op.coef == nullptr && c->op.val == nullptr;
+    if (table) {
+        if (!fresh && c->op.kind != 0) return fail(c, DAETI_EINVAL, "operator layout changed");
+        c->op.kind = 0;
+        c->op.dim = c->dim;
+        c->op.nx = tab.nx;
+        c->op.ny = tab.ny;
+        c->op.nz = tab.nz;
+        std::vector<double> A(tab.K.size(), 0.0);
+        const int self = c->dim == 3 ? 13 : 4;
+        for (size_t cls = 0; cls < tab.m.size(); ++cls)
+            for (int j = 0; j < 27; ++j)
+                if (j != self) A[cls * 27 + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
+        if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
+        if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
+    } else {
+        if (!fresh && c->op.kind != 1) return fail(c, DAETI_EINVAL, "operator layout changed");
+        std::vector<double> scale(N);
+        for (int64_t i = 0; i < N; ++i) scale[i] = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
+        Sell32 sa;
+        csr_to_sell32(K, scale.data(), sa);
+        c->op.kind = 1;
+        c->op.n_chunks = sa.n_chunks;
+        if (fresh) {
+            c->op.nnz_padded = (int64_t)sa.col.size();
+            if ((rc = dalloc(c, &p, sa.chunk_ptr.size() * 8))) return rc;
+            c->op.chunk_ptr = (int64_t*)p;
+            CK(cpy_(c, p, sa.chunk_ptr.data(), sa.chunk_ptr.size() * 8, cudaMemcpyHostToDevice));
+            if ((rc = dalloc(c, &p, sa.chunk_w.size() * 4))) return rc;
+            c->op.chunk_w = (int*)p;
+            CK(cpy_(c, p, sa.chunk_w.data(), sa.chunk_w.size() * 4, cudaMemcpyHostToDevice));
+            if ((rc = dalloc(c, &p, sa.col.size() * 4))) return rc;
+            c->op.col = (int*)p;
+            CK(cpy_(c, p, sa.col.data(), sa.col.size() * 4, cudaMemcpyHostToDevice));
+            if ((rc = dalloc(c, &c->op.val, R * sa.val.size()))) return rc;
+        } else if ((int64_t)sa.col.size() != c->op.nnz_padded) {
+            return fail(c, DAETI_EINVAL, "operator pattern changed");
+        }
+        if ((rc = upload_real(c, c->op.val, sa.val.data(), (int64_t)sa.val.size()))) return rc;
+    }
+    return DAETI_OK;
+}
+
+int daeti_prepare(daeti_ctx* c) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "already prepared");
+    if (!c->mesh_kind || !c->have_cond || !c->model)
+        return fail(c, DAETI_ESTATE, "prepare needs mesh, conductivity and cell model");
+    const int64_t N = c->n_nodes;
+    c->s = DevState();
+    c->op = DiffOp();
+    c->s.prec = c->opt.precision == DAETI_FP64 ? P_F64 : P_F32;
+    c->s.kahan = c->opt.precision == DAETI_FP32_KAHAN;
+    c->s.n = N;
+    c->s.n_states = n_states_of(c->model);
+
+    // ---- assembly and FP64 stable-step estimate
+    GridTable tab;
+    bool table = false;
+    CsrK K;
+    int rc = assemble_and_estimate(c, tab, table, K);
+    if (rc) return rc;
 
     // ---- scheme: effective dt, l, k_max (Section 2, Section 3)
     double dt = c->opt.dt;
@@ -612,7 +622,6 @@ int daeti_prepare(daeti_ctx* c) {
 
     // ---- device state
     const size_t R = rsize(c);
-    int rc = 0;
     void* p = nullptr;
     if ((rc = dalloc(c, &c->s.V[0], R * N)) || (rc = dalloc(c, &c->s.V[1], R * N))) return rc;
     if (c->s.kahan) {
@@ -657,41 +666,7 @@ int daeti_prepare(daeti_ctx* c) {
         c->s.n_stims = (int)sd.size();
     }
 
-    // ---- time-stepping operator a_ij = dt_ad k_ij / m_i in state precision
-    c->op = DiffOp();
-    if (table) {
-        c->op.kind = 0;
-        c->op.dim = c->dim;
-        c->op.nx = tab.nx;
-        c->op.ny = tab.ny;
-        c->op.nz = tab.nz;
-        std::vector<double> A(tab.K.size(), 0.0);
-        const int self = c->dim == 3 ? 13 : 4;
-        for (size_t cls = 0; cls < tab.m.size(); ++cls)
-            for (int j = 0; j < 27; ++j)
-                if (j != self) A[cls * 27 + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
-        if ((rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
-        if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
-    } else {
-        std::vector<double> scale(N);
-        for (int64_t i = 0; i < N; ++i) scale[i] = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
-        Sell32 sa;
-        csr_to_sell32(K, scale.data(), sa);
-        c->op.kind = 1;
-        c->op.n_chunks = sa.n_chunks;
-        c->op.nnz_padded = (int64_t)sa.col.size();
-        if ((rc = dalloc(c, &p, sa.chunk_ptr.size() * 8))) return rc;
-        c->op.chunk_ptr = (int64_t*)p;
-        CK(cpy_(c, p, sa.chunk_ptr.data(), sa.chunk_ptr.size() * 8, cudaMemcpyHostToDevice));
-        if ((rc = dalloc(c, &p, sa.chunk_w.size() * 4))) return rc;
-        c->op.chunk_w = (int*)p;
-        CK(cpy_(c, p, sa.chunk_w.data(), sa.chunk_w.size() * 4, cudaMemcpyHostToDevice));
-        if ((rc = dalloc(c, &p, sa.col.size() * 4))) return rc;
-        c->op.col = (int*)p;
-        CK(cpy_(c, p, sa.col.data(), sa.col.size() * 4, cudaMemcpyHostToDevice));
-        if ((rc = dalloc(c, &c->op.val, R * sa.val.size()))) return rc;
-        if ((rc = upload_real(c, c->op.val, sa.val.data(), (int64_t)sa.val.size()))) return rc;
-    }
+    if ((rc = upload_operator(c, tab, table, K))) return rc;
 
     // ---- model and synchronisation arguments
     c->margs = ModelArgs();
@@ -707,6 +682,34 @@ int daeti_prepare(daeti_ctx* c) {
     c->rtune.kmax = c->kmax;
     c->prepared = true;
     return daeti_init_state(c, nullptr);
+}
+
+int daeti_update_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long, const double* d_trans,
+                              const double* fibre) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (n_elem != c->n_elem || !d_long) return fail(c, DAETI_EINVAL, "n_elem does not match the mesh");
+    for (int64_t e = 0; e < n_elem; ++e) {
+        const double a = d_long[e], b = d_trans ? d_trans[e] : d_long[e];
+        if (!(a >= 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b))
+            return fail(c, DAETI_EINVAL, "conductivities must be finite and >= 0");
+    }
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    c->dl.assign(d_long, d_long + n_elem);
+    c->dtr.assign(d_trans ? d_trans : d_long, (d_trans ? d_trans : d_long) + n_elem);
+    c->fib_null = fibre == nullptr;
+    if (fibre) c->fib.assign(fibre, fibre + 3 * n_elem);
+    else c->fib.clear();
+    GridTable tab;
+    bool table = false;
+    CsrK K;
+    if ((rc = assemble_and_estimate(c, tab, table, K))) return rc;
+    // the schedule (dt, l) stays as prepared; it must remain stable
+    if (c->dt_ad * c->lam >= 2.0)
+        return fail(c, DAETI_EUNSTABLE, "new conductivity: dt_ad * lambda_max >= 2 with the prepared l");
+    drop_graphs(c);
+    return upload_operator(c, tab, table, K);
 }
 
 int daeti_get_stability(daeti_ctx* c, double* dt_s, double* lambda_max, int* l, int* k_max, double* dt_eff) {

@@ -14,15 +14,22 @@ struct MSParams {
     double tau_in, tau_out, tau_open, tau_close, v_gate;
 };
 
-// One Mitchell-Schaeffer forward-Euler sub-step: v' = h v^2 (1-v)/tau_in -
-// v/tau_out + J; h' = (1-h)/tau_open if v < v_gate else -h/tau_close.
+// One Mitchell-Schaeffer forward-Euler sub-step with the gate branch given:
+// v' = h v^2 (1-v)/tau_in - v/tau_out + J; h' = (1-h)/tau_open if `low`
+// (v < v_gate) else -h/tau_close.
+template <typename R>
+__device__ __forceinline__ void ms_substep_b(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out, R r_open,
+                                             R r_close, bool low) {
+    R dv = h * v * v * ((R)1 - v) * r_in - v * r_out + J;
+    R dh = low ? ((R)1 - h) * r_open : -h * r_close;
+    add_comp(v, cv, dt * dv);
+    h += dt * dh;
+}
+
 template <typename R>
 __device__ __forceinline__ void ms_substep(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out,
                                            R r_open, R r_close, R v_gate) {
-    R dv = h * v * v * ((R)1 - v) * r_in - v * r_out + J;
-    R dh = (v < v_gate) ? ((R)1 - h) * r_open : -h * r_close;
-    add_comp(v, cv, dt * dv);
-    h += dt * dh;
+    ms_substep_b(v, cv, h, dt, J, r_in, r_out, r_open, r_close, v < v_gate);
 }
 
 // ------------------------------------------------------------------ TP06

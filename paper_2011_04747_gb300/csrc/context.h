@@ -1,0 +1,90 @@
+// Private definition of the libdaeti context and host helpers shared by the
+// C-ABI translation units (api.cu, adjoint.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/daeti.h"
+#include "kernels.h"
+
+using namespace daeti;
+
+struct StimHost {
+    std::vector<int64_t> nodes;
+    double t0, dur, amp, period;
+    int count;
+};
+
+struct daeti_ctx {
+    daeti_options opt;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool own_stream = false;
+    // inputs
+    int mesh_kind = 0;   // 1 grid, 2 tets
+    int dim = 0;
+    int64_t n[3] = {1, 1, 1};
+    double h = 0.0;
+    int64_t n_nodes = 0, n_elem = 0;
+    std::vector<double> xyz;
+    std::vector<int64_t> tets;
+    bool have_cond = false;
+    std::vector<double> dl, dtr, fib;
+    bool fib_null = true;
+    int model = 0;
+    std::vector<double> params;
+    std::vector<StimHost> stims;
+    // prepared
+    bool prepared = false;
+    DevState s;
+    DiffOp op;
+    ModelArgs margs;
+    SyncArgs sargs;
+    double dt_eff = 0.1, dt_s = 0.0, lam = 0.0, dt_ad = 0.0;
+    int l = 1, kmax = 1;
+    int64_t nstep = 0;
+    int cur = 0;
+    int par = 0;
+    void* scratch = nullptr;   // n doubles for conversions
+    std::vector<double> mass;  // lumped mass per node (host, FP64)
+    double kref[64];           // unit-D element stiffness of a grid element (adjoint)
+    struct AdjointBuffers* adj = nullptr;   // adjoint work buffers (adjoint.cu)
+    int64_t adj_fwd_steps = 0;              // forward steps run by the last adjoint call
+    std::vector<void*> allocs;
+    // launch shapes
+    ReactTuning rtune;
+    int diff_block = 256;
+    bool fused = true;          // last sub-step of step I inside the reaction launch
+    bool lists = true;
+    int graph_steps = 20;
+    // graphs of graph_steps steps, keyed by (start V buffer, list parity)
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    // profiling
+    bool prof = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double ktime[3] = {0, 0, 0};
+    int64_t klaunch[3] = {0, 0, 0};
+};
+
+namespace daeti_host {
+
+int fail(daeti_ctx* c, int code, const std::string& msg);
+cudaError_t cpy_(daeti_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);
+cudaError_t set_(daeti_ctx* c, void* dst, int v, size_t bytes);
+int dalloc(daeti_ctx* c, void** p, size_t bytes);
+size_t rsize(const daeti_ctx* c);
+int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count);
+void free_adjoint(daeti_ctx* c);
+
+}  // namespace daeti_host
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return daeti_host::fail(c, e_ == cudaErrorMemoryAllocation ? DAETI_ENOMEM : DAETI_ECUDA, \
+                                    std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
