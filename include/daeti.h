@@ -242,6 +242,28 @@ int daeti_adjoint(daeti_ctx* ctx, const int64_t* sensors, int n_sensors, int sam
                   const double* data, int64_t n_steps, int n_slots, int flags, double* loss,
                   double* grad_d, double* grad_tau_close);
 
+/* Batch of independent tissues advanced together (one launch per phase of
+ * the split step over all tissues, CUDA graphs over runs of steps).  Each
+ * tissue is described by a daeti_ctx that received a structured grid,
+ * conductivity (constant on each z layer), a cell model and stimuli but need
+ * not be prepared; daeti_batch_add copies that description (the context may
+ * be destroyed afterwards).  Restrictions: tissues of one cell model share its
+ * parameters, all tissues get the same l, at most 32 distinct stimuli.
+ * Results per tissue equal advancing that tissue alone with the same
+ * options.  tissue indices follow the order of daeti_batch_add. */
+typedef struct daeti_batch daeti_batch;
+int daeti_batch_create(daeti_batch** out, const daeti_options* opt);
+int daeti_batch_destroy(daeti_batch* batch);
+const char* daeti_batch_last_error(const daeti_batch* batch);
+int daeti_batch_set_stream(daeti_batch* batch, void* cuda_stream);
+int daeti_batch_add(daeti_batch* batch, const daeti_ctx* tissue);
+int daeti_batch_prepare(daeti_batch* batch);
+int daeti_batch_advance(daeti_batch* batch, double t_end);
+int daeti_batch_synchronize(daeti_batch* batch);
+int daeti_batch_info(daeti_batch* batch, int64_t* n_nodes, int* n_tissues, int* l, double* dt);
+int daeti_batch_read_v(daeti_batch* batch, int tissue, double* out);
+int daeti_batch_read_activation(daeti_batch* batch, int tissue, double* out);
+
 /* Per-kernel timing (CUDA events around every launch of the plain-launch
  * path; graphs are not used while it is on).  which: 0 reaction,
  * 1 diffusion (plain sub-steps and fused step B), 2 other.  Returns total milliseconds and launch count

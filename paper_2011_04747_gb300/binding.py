@@ -110,6 +110,17 @@ _SIGNATURES = {
     "daeti_update_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
     "daeti_adjoint": (ctypes.c_int, [_VP, _I64P, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_int, _DP, _DP, _DP]),
+    "daeti_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(daeti_options)]),
+    "daeti_batch_destroy": (ctypes.c_int, [_VP]),
+    "daeti_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "daeti_batch_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "daeti_batch_add": (ctypes.c_int, [_VP, _VP]),
+    "daeti_batch_prepare": (ctypes.c_int, [_VP]),
+    "daeti_batch_advance": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "daeti_batch_synchronize": (ctypes.c_int, [_VP]),
+    "daeti_batch_info": (ctypes.c_int, [_VP, _I64P, _IP, _IP, _DP]),
+    "daeti_batch_read_v": (ctypes.c_int, [_VP, ctypes.c_int, _DP]),
+    "daeti_batch_read_activation": (ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     "daeti_grid_stability_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_double, ctypes.c_int64, _DP, _DP,
                                                     _DP, _VP, _DP, _DP, ctypes.c_char_p, ctypes.c_int]),
 }
@@ -364,6 +375,87 @@ class Solver:
     @property
     def time(self):
         return self.daeti_get_time()[0]
+
+
+class Batch:
+    """Many tissues advanced together (daeti_batch_*).  Tissues are added as
+    unprepared Solver descriptions (mesh, conductivity, model, stimuli)."""
+
+    def __init__(self, precision="fp32_kahan", dt=0.1, dt0=0.01, graph_steps=20, stream=None, **opts):
+        self.lib = load_library()
+        o = daeti_options()
+        self.lib.daeti_default_options(ctypes.byref(o))
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.dt, o.dt0, o.graph_steps = float(dt), float(dt0), int(graph_steps)
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = _VP()
+        rc = self.lib.daeti_batch_create(ctypes.byref(h), ctypes.byref(o))
+        if rc != OK:
+            raise DaetiError(rc, "daeti_batch_create failed")
+        self.b = h
+        self.sizes = []
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            self._check(self.lib.daeti_batch_set_stream(self.b, _VP(int(handle) if handle else 0)))
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.daeti_batch_last_error(self.b)
+            raise DaetiError(rc, msg.decode() if msg else "")
+
+    def daeti_batch_add(self, solver):
+        self._check(self.lib.daeti_batch_add(self.b, solver.ctx))
+        self.sizes.append(solver.n_nodes)
+
+    def daeti_batch_prepare(self):
+        self._check(self.lib.daeti_batch_prepare(self.b))
+
+    def daeti_batch_advance(self, t_end):
+        self._check(self.lib.daeti_batch_advance(self.b, float(t_end)))
+
+    def daeti_batch_synchronize(self):
+        self._check(self.lib.daeti_batch_synchronize(self.b))
+
+    def daeti_batch_info(self):
+        n, t, l, dt = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.daeti_batch_info(self.b, ctypes.byref(n), ctypes.byref(t), ctypes.byref(l),
+                                              ctypes.byref(dt)))
+        return {"n_nodes": n.value, "n_tissues": t.value, "l": l.value, "dt": dt.value}
+
+    def daeti_batch_read_v(self, tissue):
+        out = np.empty(self.sizes[tissue], dtype=np.float64)
+        self._check(self.lib.daeti_batch_read_v(self.b, int(tissue), _ptr(out, ctypes.c_double)))
+        return out
+
+    def daeti_batch_read_activation(self, tissue):
+        out = np.empty(self.sizes[tissue], dtype=np.float64)
+        self._check(self.lib.daeti_batch_read_activation(self.b, int(tissue), _ptr(out, ctypes.c_double)))
+        return out
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.daeti_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def describe_workload(wl, **options) -> Solver:
+    """An unprepared Solver holding a workload's description (for Batch)."""
+    opts = dict(dt=wl.dt, dt0=wl.dt0, v_threshold=wl.v_threshold)
+    opts.update(options)
+    s = Solver(**opts)
+    s.daeti_set_mesh_grid(wl.dim, wl.n, wl.h)
+    s.daeti_set_conductivity(wl.d_long, wl.d_trans, wl.fibre)
+    s.daeti_set_cell_model(wl.model, tuple(wl.model_params))
+    for st in wl.stimuli:
+        s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
+    return s
 
 
 def daeti_grid_stability_noalloc(dim, n, h, d_long, d_trans=None, fibre=None, stream=None):

@@ -14,7 +14,8 @@ LIB = os.path.join(HERE, "libdaeti.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["api.cu", "reaction_ms.cu", "reaction_tp06_f32k.cu", "reaction_tp06_f32.cu", "reaction_tp06_f64.cu",
-              "diffusion.cu", "estimator.cu", "noalloc.cu", "adjoint.cu"]
+              "diffusion.cu", "estimator.cu", "noalloc.cu", "adjoint.cu",
+              "batch.cu"]
 CPP_SOURCES = ["assembly.cpp"]
 
 

@@ -60,6 +60,10 @@ int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
     return DAETI_OK;
 }
 
+// published initial states
+const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
+                              0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
+
 }  // namespace daeti_host
 
 namespace {
@@ -85,10 +89,6 @@ void free_device(daeti_ctx* c) {
 
 
 int n_states_of(int model) { return model == DAETI_MODEL_MS ? 2 : 19; }
-
-// published initial states
-const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
-                              0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
 
 StepRef plain_ref(int64_t n) { return StepRef{nullptr, (long long)n}; }
 

@@ -78,6 +78,7 @@ int dalloc(daeti_ctx* c, void** p, size_t bytes);
 size_t rsize(const daeti_ctx* c);
 int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count);
 void free_adjoint(daeti_ctx* c);
+extern const double TP06_INIT[19];   // published TP06 initial state (state order of cells.cuh)
 
 }  // namespace daeti_host
 
