@@ -1,18 +1,20 @@
-"""Throughput of the dual adaptive explicit monodomain solver on the 3D slab.
+"""Throughput of the dual adaptive explicit monodomain solver.
 
-Workload (one bench "step"): the anisotropic TP06 slab, 101 x 101 x 26 nodes
-(265 226), h = 0.02 cm, fibres rotating -60..+60 deg through the wall, corner
-stimulus, 500 ms simulated with the 0.1 ms splitting step (5 000 Strang
-steps) from the published initial state.  Metric: node-steps/s =
-nodes x Strang steps / wall-second (whole job), and simulated ms per wall-s;
-FP32 (compensated V) is the headline, FP64 is measured beside it together
-with the FP32-vs-FP64 difference in mV and ms.
+Headline workload (one bench "step"): the anisotropic TP06 slab, 101 x 101 x
+26 nodes (265 226), h = 0.02 cm, fibres rotating -60..+60 deg through the
+wall, corner stimulus, 500 ms simulated with the 0.1 ms splitting step (5 000
+Strang steps) from the published initial state.  Metric: node-steps/s =
+nodes x Strang steps / wall-second (whole job) and simulated ms per wall-s;
+FP32 with compensated V is the headline, FP64 is measured beside it with the
+FP32-vs-FP64 difference in mV and ms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload slab|slab_l|square|sheet|tets|batch|adjoint]
 
 ``--impl reference`` times the CPU oracle (plain FP64 numpy, one host core) on
-a bounded sample of the same workload: the full slab over the first 2 ms of
-the simulation (20 Strang steps) per bench step.
+a bounded sample of the same workload.  Other workloads print their own line
+(they are not the headline).  Under torchrun every rank runs its own replica
+(weak scaling, no data-path collective); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -32,12 +34,14 @@ UNIT = "node-steps/s"
 SLAB = dict(nx=101, ny=101, nz=26, h=0.02)
 T_END = 500.0
 ORACLE_SAMPLE_STEPS = 20
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+XU_LANES_PER_SM = 16
+TP06_XU_PER_SUBSTEP = 94.0     # exp/log/reciprocal/rsqrt per TP06 sub-step, counted from cells.cuh
 
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    return rank, world
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
 def _clock_sampler(path):
@@ -73,8 +77,7 @@ def _clock_summary(path, dev_index):
         pass
     if not sm:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-            "samples": len(sm)}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def _peaks():
@@ -84,8 +87,9 @@ def _peaks():
         return {}
 
 
+# ------------------------------------------------------------------ reference arm
 def run_reference(args):
-    """CPU oracle on a bounded sample of the slab workload."""
+    """CPU oracle on a bounded sample of the slab workload (rank 0 only)."""
     rank, world = _dist()
     if rank != 0:
         return
@@ -94,18 +98,17 @@ def run_reference(args):
 
     wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
     times = []
-    n_nodes = wl.n_nodes
     for it in range(args.warmup + args.steps):
         sim = scheme.simulation_from_workload(wl)
         t0 = time.perf_counter()
         sim.run(ORACLE_SAMPLE_STEPS)
-        dt = time.perf_counter() - t0
         if it >= args.warmup:
-            times.append(dt)
+            times.append(time.perf_counter() - t0)
     sec = sum(times) / len(times)
-    value = n_nodes * ORACLE_SAMPLE_STEPS / sec
-    sample = f"full slab ({n_nodes} nodes), first {ORACLE_SAMPLE_STEPS} Strang steps (2 ms incl. the stimulus) per step"
-    line = {
+    value = wl.n_nodes * ORACLE_SAMPLE_STEPS / sec
+    sample = (f"full slab ({wl.n_nodes} nodes), first {ORACLE_SAMPLE_STEPS} Strang steps (2 ms, stimulus on) "
+              f"per step, numpy FP64 on one host core")
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -113,188 +116,332 @@ def run_reference(args):
         "sim_ms_per_wall_s": ORACLE_SAMPLE_STEPS * 0.1 / sec,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    }), flush=True)
 
 
-def _cpu_baseline_sample():
-    import inputs
+def _cpu_baseline_sample(wl, steps=ORACLE_SAMPLE_STEPS):
     from oracle import scheme
 
-    wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
     sim = scheme.simulation_from_workload(wl)
     t0 = time.perf_counter()
-    sim.run(ORACLE_SAMPLE_STEPS)
+    sim.run(steps)
     sec = time.perf_counter() - t0
-    return {"value": wl.n_nodes * ORACLE_SAMPLE_STEPS / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"full slab, first {ORACLE_SAMPLE_STEPS} Strang steps (2 ms), numpy FP64, {sec:.1f} s"}
+    return {"value": wl.n_nodes * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{wl.name}: first {steps} Strang steps, numpy FP64, one host core, {sec:.1f} s"}
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+# ------------------------------------------------------------------ our arm
+class Env:
+    def __init__(self, args):
+        import torch
+        import torch.distributed as dist
 
-    import inputs
-    from paper_2011_04747_gb300 import binding, build as _build
+        from paper_2011_04747_gb300 import binding, build as _build
 
-    rank, world = _dist()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if not os.path.exists(binding.LIB_PATH):
-        if rank == 0:
-            _build.build()
-        if world > 1:
-            dist.barrier()
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+        self.torch, self.dist, self.binding = torch, dist, binding
+        self.rank, self.world = _dist()
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if self.world > 1:
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(self.local)
+        if not os.path.exists(binding.LIB_PATH):
+            if self.rank == 0:
+                _build.build()
+            if self.world > 1:
+                dist.barrier()
+        self.dev = torch.device("cuda", self.local)
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device=self.dev)
 
-    wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
-    n_nodes = wl.n_nodes
-    n_steps = int(round(T_END / wl.dt))
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
 
-    def make(prec):
-        s = binding.solver_from_workload(wl, precision=prec, graph_steps=args.graph_steps,
-                                         bucket_k=bool(args.bucket))
-        s.daeti_set_stream(stream)
-        return s
+    def max_over_ranks(self, x):
+        if self.world == 1:
+            return x
+        t = self.torch.tensor([x], device=self.dev, dtype=self.torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
 
-    flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device=dev)   # > L2 (129 MB)
-
-    def timed_runs(solver, k, w):
-        ck = solver.daeti_save_state()                  # initial state
+    def timed(self, fn, k, w, reset=None):
+        """Average seconds of fn() over k timed repetitions after w warm-ups,
+        CUDA events on the launching stream, L2 flushed before each one."""
+        torch = self.torch
         times = []
         for it in range(w + k):
-            solver.daeti_load_state(ck)
-            flush.fill_(float(it))
-            torch.cuda.synchronize(dev)
-            if world > 1:
-                dist.barrier()
+            if reset:
+                reset()
+            self.flush.fill_(float(it))
+            torch.cuda.synchronize(self.dev)
+            self.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solver.daeti_advance(T_END)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            torch.cuda.synchronize(self.dev)
             if it >= w:
                 times.append(e0.elapsed_time(e1) / 1e3)
-        solver.daeti_synchronize()
-        return times
+        return self.max_over_ranks(sum(times) / len(times))
 
-    # ---- FP32 (headline) ------------------------------------------------------------
+
+def _reaction_roofline(solver, clocks, sub_per_step):
+    """ALU roofline of the reaction kernel from the per-launch event-timed pass."""
+    ms, nl = solver.daeti_get_kernel_time(0)
+    bytes_launch, ops_per_sub = solver.daeti_kernel_work(0)
+    avg_s = ms / max(nl, 1) / 1e3
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = ops_per_sub * sub_per_step / avg_s / 1e12
+    xu_peak = SM_COUNT * XU_LANES_PER_SM * mhz * 1e6
+    fused = solver.daeti_get_tuning()["fuse_diffusion"]
+    label = "reaction (TP06, FP32" + (", with the fused diffusion sub-step)" if fused else ")")
+    return {"bound": "alu", "kernel": label, "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "avg_launch_us": avg_s * 1e6, "ops_per_node_substep": ops_per_sub,
+            "substeps_per_launch": sub_per_step,
+            "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled), 1 op/lane/cycle",
+            "xu_frac": TP06_XU_PER_SUBSTEP * sub_per_step / avg_s / xu_peak,
+            "bytes_per_launch": bytes_launch,
+            "bytes_frac_of_measured_hbm": bytes_launch / avg_s / 1e9 / _peaks().get("hbm_gbs", 6786.9)}
+
+
+def bench_slab(args, env):
+    import numpy as np
+
+    import inputs
+    from paper_2011_04747_gb300 import autotune
+
+    binding = env.binding
+    wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
+    n_nodes, n_steps = wl.n_nodes, int(round(T_END / wl.dt))
+
+    def make(prec):
+        s = binding.solver_from_workload(wl, precision=prec, graph_steps=args.graph_steps, bucket_k=bool(args.bucket))
+        s.daeti_set_stream(env.stream)
+        return s
+
     s32 = make("fp32_kahan")
+    tune = None
+    if not args.no_autotune:
+        rep = autotune.autotune(s32, sim_ms=20.0, extra_key="|slab")
+        tune = {k: rep[k] for k in ("cached", "candidates", "rejected") if k in rep}
+        s32.daeti_set_stream(env.stream)
     stab = s32.daeti_get_stability()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    ck = s32.daeti_save_state()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{env.rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     sampler, fh = _clock_sampler(clk_path)
-    t32 = timed_runs(s32, args.steps, args.warmup)
+    sec32 = env.timed(lambda: s32.daeti_advance(T_END), args.steps, args.warmup,
+                      reset=lambda: s32.daeti_load_state(ck))
     if sampler:
         sampler.terminate()
         sampler.wait()
         fh.close()
-    clocks = _clock_summary(clk_path, local)
+    clocks = _clock_summary(clk_path, env.local)
     v32 = s32.daeti_read_v()
     a32 = s32.daeti_read_activation()
-    sub32 = s32.daeti_get_substeps()
-    sec32 = sum(t32) / len(t32)
-    if world > 1:
-        tt = torch.tensor([sec32], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        sec32 = float(tt.item())
-    value = world * n_nodes * n_steps / sec32
+    sub_total = s32.daeti_get_substeps()          # counted since the last load_state: one 500 ms run
+    sub_per_step = sub_total / n_steps if sub_total else 0.0
+    value = env.world * n_nodes * n_steps / sec32
 
-    # ---- per-kernel timing pass (CUDA events around every launch, no graph) ------------
-    ck = None
+    # per-kernel timing pass (events around every launch, plain launches)
+    s32.daeti_load_state(ck)
     s32.daeti_set_profiling(True)
-    s32.daeti_init_state()
     s32.daeti_advance(T_END)
     s32.daeti_synchronize()
     kt = {}
-    for which, name in ((0, "reaction"), (1, "diffusion"), (2, "bucket")):
+    for which, name in ((0, "reaction"), (1, "diffusion")):
         ms, nl = s32.daeti_get_kernel_time(which)
         b, f = s32.daeti_kernel_work(which)
         kt[name] = {"total_ms": ms, "launches": nl, "avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b}
+    roof = _reaction_roofline(s32, clocks, sub_per_step)
+    d = kt["diffusion"]
+    d["bytes_GBs"] = d["bytes_per_launch"] / (d["avg_us"] * 1e-6) / 1e9
     s32.daeti_set_profiling(False)
 
-    # ---- e2e through the C ABI with host buffers -----------------------------------
-    state0 = None
-    e2e_times = []
+    # e2e through the C ABI with host buffers
+    e2e = []
     for it in range(2 + max(1, args.steps // 2)):
-        torch.cuda.synchronize(dev)
+        env.torch.cuda.synchronize(env.dev)
         t0 = time.perf_counter()
-        s32.daeti_init_state(state0)                    # host -> device
+        s32.daeti_init_state(None)              # host -> device
         s32.daeti_advance(T_END)
-        vh = s32.daeti_read_v()                         # device -> host (waits)
-        ah = s32.daeti_read_activation()
-        t1 = time.perf_counter()
+        s32.daeti_read_v()                      # device -> host (waits)
+        s32.daeti_read_activation()
         if it >= 2:
-            e2e_times.append(t1 - t0)
-    n_states = s32.n_states
-    h2d = n_nodes * (n_states + 2) * 4
-    d2h = 2 * n_nodes * 8
-    e2e_val = world * n_nodes * n_steps / (sum(e2e_times) / len(e2e_times))
+            e2e.append(time.perf_counter() - t0)
+    e2e_val = env.world * n_nodes * n_steps / env.max_over_ranks(sum(e2e) / len(e2e))
+    ns = s32.n_states
+    tuning_used = s32.daeti_get_tuning()
     s32.close()
 
-    # ---- FP64 beside it -------------------------------------------------------------
-    sec64, dv, dact = None, None, None
+    sec64 = dv = dact = None
     if not args.no_fp64:
         s64 = make("fp64")
-        t64 = timed_runs(s64, max(1, args.steps // 2), 1)
-        v64 = s64.daeti_read_v()
-        a64 = s64.daeti_read_activation()
+        sec64 = env.timed(lambda: s64.daeti_advance(T_END), max(1, args.steps // 2), 1,
+                          reset=lambda: s64.daeti_init_state(None))
+        v64, a64 = s64.daeti_read_v(), s64.daeti_read_activation()
         s64.close()
-        sec64 = sum(t64) / len(t64)
         both = (a32 >= 0) & (a64 >= 0)
         dv = float(np.max(np.abs(v32 - v64)))
         dact = float(np.max(np.abs(a32[both] - a64[both]))) if both.any() else None
 
-    # ---- roofline of the dominant kernel -----------------------------------------------
-    peaks = _peaks()
-    dom = max(("reaction", "diffusion", "bucket"), key=lambda k: kt[k]["total_ms"])
-    sub_per_launch = sub32 / max(len(t32) + args.warmup, 1) / n_steps if sub32 else None
-    if dom == "diffusion":
-        roof = {"bound": "hbm", "achieved": kt[dom]["bytes_per_launch"] / (kt[dom]["avg_us"] * 1e-6) / 1e9,
-                "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
-    else:
-        roof = {"bound": "hbm", "achieved": kt[dom]["bytes_per_launch"] / (kt[dom]["avg_us"] * 1e-6) / 1e9,
-                "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = dom
-
-    launches_per_step = 2 * stab["l"] + 2
+    launches_per_step = 2 * stab["l"] + (0 if tuning_used["fuse_diffusion"] else 1)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": env.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec32 * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "tp06_slab_101x101x26_h0.02_500ms", "nodes": n_nodes, "strang_steps": n_steps,
                    "dt_ms": wl.dt, "l": stab["l"], "k_max": stab["k_max"], "dt_s_ms": stab["dt_s"],
                    "precision": "fp32_kahan", "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
-        "sim_ms_per_wall_s": T_END / sec32,
-        "fp64": None if sec64 is None else {"value": world * n_nodes * n_steps / sec64,
+                   "parallelism": f"replicas x{env.world}", "tuning": tuning_used, "autotune": tune},
+        "sim_ms_per_wall_s": env.world * T_END / sec32,
+        "fp64": None if sec64 is None else {"value": env.world * n_nodes * n_steps / sec64,
                                              "ms_per_step": sec64 * 1e3, "sim_ms_per_wall_s": T_END / sec64},
         "fp32_vs_fp64": {"max_abs_dv_mv_at_500ms": dv, "max_abs_dact_ms": dact},
-        "reaction_substeps_per_node_step": sub_per_launch / n_nodes if sub_per_launch else None,
-        "kernels": kt,
-        "roofline": roof,
-        "clocks": clocks,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (launches_per_step * n_steps + n_steps // max(args.graph_steps, 1)) * args.steps,
+        "reaction_substeps_per_node_step": sub_per_step / n_nodes if sub_per_step else None,
+        "kernels": kt, "roofline": roof, "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n_nodes * (ns + 2) * 4,
+                "d2h_bytes_per_step": 2 * n_nodes * 8},
+        "gpu_launches": (launches_per_step * n_steps + n_steps // max(tuning_used["graph_steps"], 1) + 2) * args.steps,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline_sample()
-    if rank == 0:
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline_sample(wl)
+    return line
+
+
+def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_sample=10):
+    """node-steps/s of one single-tissue workload (not the headline)."""
+    binding = env.binding
+    t_end = t_end or wl.t_end
+    s = binding.solver_from_workload(wl, precision=precision, graph_steps=args.graph_steps)
+    s.daeti_set_stream(env.stream)
+    st = s.daeti_get_stability()
+    ck = s.daeti_save_state()
+    sec = env.timed(lambda: s.daeti_advance(t_end), args.steps, args.warmup, reset=lambda: s.daeti_load_state(ck))
+    n_steps = int(round(t_end / st["dt"]))
+    s.daeti_load_state(ck)
+    s.daeti_set_profiling(True)
+    s.daeti_advance(min(t_end, 20 * st["dt"]))
+    ms, nl = s.daeti_get_kernel_time(1)
+    b, _ = s.daeti_kernel_work(1)
+    s.daeti_set_profiling(False)
+    s.close()
+    diff = {"avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b,
+            "GBs": b / (ms / max(nl, 1) / 1e3) / 1e9 if ms else None}
+    if diff["GBs"]:
+        diff["frac_of_measured_hbm"] = diff["GBs"] / _peaks().get("hbm_gbs", 6786.9)
+    line = {"metric": UNIT + " (" + name + ")", "value": env.world * wl.n_nodes * n_steps / sec, "unit": UNIT,
+            "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
+            "data": "synthetic", "config": {"workload": name, "nodes": wl.n_nodes, "strang_steps": n_steps,
+                                            "l": st["l"], "dt_s_ms": st["dt_s"]},
+            "sim_ms_per_wall_s": t_end / sec, "diffusion_launch": diff}
+    if env.rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline_sample(wl, steps_sample)
+    return line
+
+
+def bench_batch(args, env):
+    """512 uneven tissues in one batched launch sequence vs the same tissues run one by one."""
+    import inputs
+
+    binding = env.binding
+    wls = inputs.batch_tissues()
+    t_end = 300.0
+    n_nodes = sum(w.n_nodes for w in wls)
+    n_steps = int(round(t_end / 0.1))
+    batch = binding.Batch(precision="fp32_kahan", graph_steps=args.graph_steps, stream=env.stream)
+    for w in wls:
+        d = binding.describe_workload(w)
+        batch.daeti_batch_add(d)
+        d.close()
+    batch.daeti_batch_prepare()
+    sec_b = env.timed(lambda: batch.daeti_batch_advance(t_end), 1, 0)
+    batch.close()
+    solvers = [binding.solver_from_workload(w, precision="fp32_kahan", graph_steps=args.graph_steps) for w in wls]
+    for s in solvers:
+        s.daeti_set_stream(env.stream)
+
+    def seq():
+        for s in solvers:
+            s.daeti_advance(t_end)
+
+    sec_s = env.timed(seq, 1, 0)
+    for s in solvers:
+        s.close()
+    return {"metric": "aggregate node-steps/s, 512 batched tissues (MS/TP06 mixed, 32^2..256^2, 300 ms)",
+            "value": env.world * n_nodes * n_steps / sec_b, "unit": UNIT, "n_gpus": env.world,
+            "steps": 1, "warmup": 0, "ms_per_step": sec_b * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_512_tissues_300ms", "nodes": n_nodes, "strang_steps": n_steps},
+            "sequential": {"value": n_nodes * n_steps / sec_s, "ms": sec_s * 1e3},
+            "batched_over_sequential": sec_s / sec_b}
+
+
+def bench_adjoint(args, env):
+    """Gradient evaluations per second and adjoint/forward time ratio, 256^2 MS, 2000 steps, 32 slots."""
+    import numpy as np
+
+    import inputs
+
+    binding = env.binding
+    wl, d_node, sensors, _ = inputs.ms_adjoint_2d()
+    nx = wl.n[0]
+    ey, ex = np.meshgrid(np.arange(nx - 1), np.arange(nx - 1), indexing="ij")
+    base = (ex + nx * ey).ravel()
+    conn = base[:, None] + np.array([0, 1, nx, nx + 1])[None, :]
+    de = d_node[conn].mean(axis=1)
+    wl.d_long, wl.d_trans, wl.fibre = de, de, None
+    s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=args.graph_steps)
+    s.daeti_set_stream(env.stream)
+    data = np.zeros((200, len(sensors)))
+    t_fwd = env.timed(lambda: s.daeti_adjoint(sensors, data, 2000, 10, 32, flags=4), args.steps, 1)
+    t_adj = env.timed(lambda: s.daeti_adjoint(sensors, data, 2000, 10, 32, n_elem=len(de)), args.steps, 1)
+    t_plain = env.timed(lambda: s.daeti_advance(s.time + 200.0), args.steps, 1)
+    s.close()
+    return {"metric": "gradient evaluations/s (256x256 MS, 2000 steps, 32 slots, FP32)",
+            "value": 1.0 / t_adj, "unit": "gradients/s", "n_gpus": env.world, "steps": args.steps, "warmup": 1,
+            "ms_per_step": t_adj * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": "ms_adjoint_256x256_2000steps"},
+            "adjoint_over_forward": t_adj / t_fwd, "adjoint_over_plain_advance": t_adj / t_plain,
+            "forward_ms": t_fwd * 1e3, "plain_advance_ms": t_plain * 1e3}
+
+
+def run_ours(args):
+    import inputs
+
+    env = Env(args)
+    wk = args.workload
+    if wk == "slab":
+        line = bench_slab(args, env)
+    elif wk == "slab_l":
+        line = bench_simple(args, env, inputs.tp06_slab_3d(401, 401, 26, t_end=50.0), "tp06_slab_401x401x26_50ms",
+                            t_end=50.0, steps_sample=2)
+    elif wk == "square":
+        line = bench_simple(args, env, inputs.ms_square_2d(), "ms_square_41x41_100ms", precision="fp64",
+                            steps_sample=1000)
+    elif wk == "sheet":
+        line = bench_simple(args, env, inputs.aniso_sheet_2d(t_end=50.0), "tp06_sheet_501x501_h0.01_50ms",
+                            t_end=50.0, steps_sample=5)
+    elif wk == "tets":
+        line = bench_simple(args, env, inputs.tet_slab_3d(t_end=50.0), "tp06_tet_slab_201x201x51_50ms",
+                            t_end=50.0, steps_sample=2)
+    elif wk == "batch":
+        line = bench_batch(args, env)
+    else:
+        line = bench_adjoint(args, env)
+    if env.rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    if env.world > 1:
+        env.dist.barrier()
+        env.dist.destroy_process_group()
 
 
 def profile_run(args):
-    """A short plain run of the bench workload for external profilers."""
+    """A short plain run of the headline workload for external profilers."""
     import inputs
     from paper_2011_04747_gb300 import binding, build as _build
 
@@ -315,17 +462,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="slab",
+                    choices=["slab", "slab_l", "square", "sheet", "tets", "batch", "adjoint"])
     ap.add_argument("--graph-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--bucket", type=int, default=1, help="group nodes by k before step A (1) or not (0)")
     ap.add_argument("--profile-run", type=float, default=0.0,
                     help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
     args = ap.parse_args()
     if args.profile_run > 0:
         profile_run(args)
-        return
-    if args.impl == "reference":
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

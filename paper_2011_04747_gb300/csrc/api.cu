@@ -936,6 +936,7 @@ int daeti_load_state(daeti_ctx* c, const void* buf, int64_t buf_bytes) {
     CK(cpy_(c, c->s.kk, p, N, cudaMemcpyHostToDevice));
     p += N;
     CK(set_(c, c->s.flags, 0, 16));
+    CK(set_(c, c->s.substeps, 0, 8));
     c->nstep = hdr[5];
     c->par = (int)hdr[6];
     // the per-k lists follow from k
@@ -979,8 +980,11 @@ int daeti_kernel_work(daeti_ctx* c, int which, double* bytes, double* flops) {
     const double sync = 2.0 * R + 1.0 + R + (lists_mode(c) ? 4.0 : 0.0);   // vsync r/w, k w, act r, list w
     double b = 0.0, f = 0.0;
     if (which == 0) {
-        // every state read and written once per step A, plus the node's list entry
+        // every state read and written once per step A, plus the node's list entry;
+        // flops: arithmetic operations per node sub-step of the cell model, counted
+        // from cells.cuh (add/sub/mul/fma and each exp, log, reciprocal, rsqrt as one)
         b = N * (2.0 * R * c->s.n_states + comp + (lists_mode(c) ? 4.0 : 1.0));
+        f = c->model == DAETI_MODEL_TP06 ? 450.0 : 20.0;
         if (c->fused) {
             // plus the fused diffusion sub-step: V and the Kahan term of the source buffer
             b += N * (R + (c->s.kahan ? 4.0 : 0.0));
