@@ -131,6 +131,17 @@ def _cpu_baseline_sample(wl, steps=ORACLE_SAMPLE_STEPS):
 
 
 # ------------------------------------------------------------------ our arm
+def max_over_ranks(dist, x, device, world):
+    """The slowest rank's time: whole-job throughput divides by it."""
+    if world == 1:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Env:
     def __init__(self, args):
         import torch
@@ -158,11 +169,7 @@ class Env:
             self.dist.barrier()
 
     def max_over_ranks(self, x):
-        if self.world == 1:
-            return x
-        t = self.torch.tensor([x], device=self.dev, dtype=self.torch.float64)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(self.dist, x, self.dev, self.world)
 
     def timed(self, fn, k, w, reset=None):
         """Average seconds of fn() over k timed repetitions after w warm-ups,

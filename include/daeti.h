@@ -202,8 +202,9 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
 /* Launch shapes (set by the caller or an autotuner; results do not depend on
  * them).  react_block: threads per reaction block (32..128, multiple of 32);
  * react_min_blocks: 8 or 10 resident reaction blocks per SM the register
- * budget must allow (TP06 in float); diff_block: threads per diffusion
- * block (32..256, multiple of 32);
+ * budget must allow (TP06 in float); diff_block: threads per block of the
+ * one-thread-per-node diffusion kernel (32..256, multiple of 32; default
+ * 256), or 0 for the shared-memory tiled kernel on structured grids;
  * fuse_diffusion: run the last diffusion sub-step of step I inside the
  * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
  * steps per captured CUDA graph (rounded up to even, 0 = plain launches).
@@ -271,8 +272,10 @@ int daeti_batch_read_activation(daeti_batch* batch, int tissue, double* out);
 int daeti_set_profiling(daeti_ctx* ctx, int enable);
 int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* launches);
 
-/* Algorithmic bytes and FP32/FP64 operations of one launch of kernel `which`
- * at the current problem (the counts the roofline figures use). */
+/* Algorithmic bytes of one launch of kernel `which` at the current problem
+ * and its arithmetic operations: for which = 1 (diffusion) per launch, for
+ * which = 0 (reaction) per node sub-step (multiply by daeti_get_substeps per
+ * launch); add/sub/mul/fma and each exp, log, reciprocal, rsqrt count one. */
 int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
 
 /* ---------------------------------------------------------------------------

@@ -56,7 +56,7 @@ struct daeti_ctx {
     std::vector<void*> allocs;
     // launch shapes
     ReactTuning rtune;
-    int diff_block = 256;
+    int diff_block = 256;       // 0: shared-memory tiles on structured grids
     bool fused = true;          // last sub-step of step I inside the reaction launch
     bool lists = true;
     int graph_steps = 20;

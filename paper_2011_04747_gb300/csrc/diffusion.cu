@@ -12,6 +12,8 @@
 // epilogue (activation time, k of the next step A, per-k node lists).  The
 // last sub-step of each step I is fused into the reaction launch
 // (reaction.cu).
+#include <algorithm>
+
 #include "diffops.cuh"
 
 namespace daeti {
@@ -31,6 +33,72 @@ __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const
         if (SYNC) k = sync_node(sp, i, v);
     }
     if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, valid);
+}
+
+// Structured grids: a block owns a TX x TY tile in x-y and marches through a
+// run of z planes, keeping three planes of V (tile plus a one-node halo) in
+// shared memory; the 27 (9) neighbours then come from shared memory and every
+// V value is read from global memory about once per plane it feeds.
+constexpr int TX = 32, TY = 8;
+
+template <typename R, int DIM, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, int n, int zrun,
+                                                               const R* __restrict__ vin, R* vout,
+                                                               const float* cin, float* cout, SyncParams<R> sp) {
+    constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;
+    constexpr int NP = DIM == 3 ? 3 : 1;
+    __shared__ R buf[NP][PLANE];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const int z_begin = DIM == 3 ? blockIdx.z * zrun : 0;
+    const int z_end = DIM == 3 ? min(nz, z_begin + zrun) : 1;
+    const int nxy = nx * ny;
+
+    auto load_plane = [&](int z) {
+        R* dst = buf[DIM == 3 ? (z % 3) : 0];
+        for (int q = threadIdx.x; q < PLANE; q += TX * TY) {
+            const int lx = q % PX, ly = q / PX;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && z >= 0 && z < nz;
+            dst[q] = in ? vin[gx + nx * gy + nxy * z] : (R)0;
+        }
+    };
+    if (DIM == 3) {
+        if (z_begin - 1 >= 0) load_plane(z_begin - 1);
+        load_plane(z_begin);
+    }
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool col_in = gx < nx && gy < ny;
+    const int cx = gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1);
+    const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
+    const int li = (ty + 1) * PX + (tx + 1);
+    for (int z = z_begin; z < z_end; ++z) {
+        if (DIM == 3) {
+            if (z + 1 < nz) load_plane(z + 1);
+        } else {
+            load_plane(0);
+        }
+        __syncthreads();
+        int k = 1;
+        int i = 0;
+        if (col_in) {
+            i = gx + nx * gy + nxy * z;
+            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
+            auto fetch = [&](int dx, int dy, int dz) {
+                return buf[DIM == 3 ? ((z + dz + 3) % 3) : 0][li + dx + dy * PX];
+            };
+            R v;
+            float cc;
+            stencil_update<R, DIM, KAHAN>(crow, cx, cy, z, nz, buf[DIM == 3 ? (z % 3) : 0][li],
+                                          KAHAN ? cin[i] : 0.f, fetch, v, cc);
+            vout[i] = v;
+            if (KAHAN) cout[i] = cc;
+            if (SYNC) k = sync_node(sp, i, v);
+        }
+        if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, col_in);
+        __syncthreads();   // the plane z - 1 buffer is refilled next
+    }
 }
 
 template <typename R>
@@ -59,10 +127,37 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, const Op
     else substep_kernel<R, DIM, KAHAN, false><<<grid, block, 0, st>>>(op, n, vin, vout, cin, cout, sp);
 }
 
+template <typename R, int DIM, bool KAHAN>
+static void tiled_launch(bool sync, cudaStream_t st, const OpView<R>& op, const DiffOp& dop, int n, const R* vin,
+                         R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
+    const int gx = (dop.nx + TX - 1) / TX, gy = (dop.ny + TY - 1) / TY;
+    int zrun = 1, gz = 1;
+    if (DIM == 3) {
+        // enough blocks to fill the GPU (about 8 per SM), long z runs otherwise
+        const long tiles = (long)gx * gy;
+        zrun = (int)std::max<long>(1, std::min<long>(dop.nz, (tiles * dop.nz + 1215) / 1216));
+        gz = (dop.nz + zrun - 1) / zrun;
+    }
+    const dim3 grid(gx, gy, gz);
+    if (sync) tiled_substep_kernel<R, DIM, KAHAN, true><<<grid, TX * TY, 0, st>>>(op, n, zrun, vin, vout, cin, cout, sp);
+    else tiled_substep_kernel<R, DIM, KAHAN, false><<<grid, TX * TY, 0, st>>>(op, n, zrun, vin, vout, cin, cout, sp);
+}
+
 template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
                        StepRef step, bool lists, int block, cudaStream_t st) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
+    if (dop.kind == 0 && block == 0) {
+        // structured grid, shared-memory tiles
+        const OpView<R> op = op_view<R>(dop);
+        const R* vin = (const R*)s.V[src];
+        R* vout = (R*)s.V[1 - src];
+        const float* cin = KAHAN ? s.C[src] : nullptr;
+        float* cout = KAHAN ? s.C[1 - src] : nullptr;
+        if (dop.dim == 2) tiled_launch<R, 2, KAHAN>(sync, st, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        else tiled_launch<R, 3, KAHAN>(sync, st, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        return;
+    }
     if (block <= 0) block = 256;
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
