@@ -37,12 +37,16 @@ struct AdjointBuffers {
     // snapshots: V, C, h, vsync, act, kk per slot
     std::vector<void*> sV, sC, sH, sVs, sA, sK;
     std::vector<int64_t> slot_step;
-    // per-step intermediates
-    std::vector<void*> d1, d2;          // inputs of the diffusion sub-steps
-    void *rv = nullptr, *rh = nullptr;  // reaction input v, h
-    float* rc = nullptr;                // reaction input Kahan term
-    uint8_t* kused = nullptr;
-    void* vend = nullptr;
+    // per-step intermediates: the forward of a step being reversed writes every
+    // sub-step's result to its own buffer (pools P, CP), so no copies are needed
+    std::vector<void*> P;               // 2l + 1 V buffers
+    std::vector<float*> CP;             // 2l + 1 Kahan buffers (FP32 + Kahan)
+    void* Hout = nullptr;               // reaction output h (the state h is its input)
+    uint8_t* kk_next = nullptr;         // k written by the synchronisation of that step
+    std::vector<const void*> d1, d2;    // inputs of the diffusion sub-steps (aliases)
+    const void *rv = nullptr, *rh = nullptr, *vend = nullptr;
+    const float* rc = nullptr;
+    const uint8_t* kused = nullptr;
     // costate and gradients
     void* mu[2] = {nullptr, nullptr};
     void* lamh = nullptr;
@@ -54,11 +58,16 @@ struct AdjointBuffers {
     // recorded schedule
     uint8_t* hist_k = nullptr;
     uint16_t* hist_b = nullptr;
+    // the whole gradient sweep as one CUDA graph (the binomial schedule is
+    // fixed by n_steps, n_slots and the sampling), keyed by those and the start step
+    cudaGraphExec_t graph = nullptr;
+    int64_t gkey[5] = {-1, -1, -1, -1, -1};
 };
 
 namespace daeti_host {
 void free_adjoint(daeti_ctx* c) {
     if (!c->adj) return;
+    if (c->adj->graph) cudaGraphExecDestroy(c->adj->graph);
     for (void* p : c->adj->allocs) cudaFree(p);
     delete c->adj;
     c->adj = nullptr;
@@ -74,6 +83,9 @@ struct AdjReactArgs {
     R* V;
     float* C;
     R* H;
+    R* Vo;        // outputs (equal to the inputs for in-place steps)
+    float* Co;
+    R* Ho;
     const uint8_t* kk;
     uint8_t* hist_k;
     uint16_t* hist_b;
@@ -115,9 +127,9 @@ __global__ void adj_react_fwd(AdjReactArgs<R> a) {
         bits |= (uint16_t)(low ? 1u << s : 0u);
         ms_substep_b(v, cp, h, a.dtkr[k], J, a.r_in, a.r_out, a.r_open, a.r_close, low);
     }
-    a.V[i] = v;
-    a.H[i] = h;
-    if (KAHAN) a.C[i] = c;
+    a.Vo[i] = v;
+    a.Ho[i] = h;
+    if (KAHAN) a.Co[i] = c;
     if (MODE == 1) {
         a.hist_k[i] = (uint8_t)k;
         a.hist_b[i] = bits;
@@ -232,6 +244,9 @@ AdjReactArgs<R> react_args(daeti_ctx* c, int buf, int64_t step, uint8_t* hk, uin
     a.V = (R*)c->s.V[buf];
     a.C = c->s.kahan ? c->s.C[buf] : nullptr;
     a.H = (R*)c->s.S;
+    a.Vo = a.V;
+    a.Co = a.C;
+    a.Ho = a.H;
     a.kk = c->s.kk;
     a.hist_k = hk;
     a.hist_b = hb;
@@ -286,43 +301,90 @@ struct Adj {
     }
 
     template <typename T, bool K>
-    void react_fwd(int buf, int64_t j) {
+    void react_fwd(int buf, int64_t j, void* vin = nullptr, float* cin = nullptr, void* vout = nullptr,
+                   float* cout = nullptr, void* hout = nullptr) {
         const int n = (int)c->n_nodes;
         uint8_t* hk = b->hist_k ? b->hist_k + (size_t)j * n : nullptr;
         uint16_t* hb = b->hist_b ? b->hist_b + (size_t)j * n : nullptr;
         AdjReactArgs<T> a = react_args<T>(c, buf, n0 + j, hk, hb);
+        if (vin) {
+            a.V = (T*)vin;
+            a.C = cin;
+            a.Vo = (T*)vout;
+            a.Co = cout;
+            a.Ho = (T*)hout;
+        }
         const int grid = (n + 127) / 128;
         if (mode == 2) adj_react_fwd<T, K, 2><<<grid, 128, 0, st>>>(a);
         else if (mode == 1) adj_react_fwd<T, K, 1><<<grid, 128, 0, st>>>(a);
         else adj_react_fwd<T, K, 0><<<grid, 128, 0, st>>>(a);
     }
 
-    // One forward step j (from the synchronisation at t_j), optionally keeping
-    // every intermediate the reverse of this step needs.
+    // One diffusion sub-step from `in` to `out` (and the Kahan terms), with the
+    // synchronisation epilogue when `sync` (k written to `kk_out`).
+    void diffuse_view(const void* in, void* out, const float* cin, float* cout, bool sync, StepRef ref,
+                      uint8_t* kk_out) {
+        DevState v = c->s;
+        v.V[0] = const_cast<void*>(in);
+        v.V[1] = out;
+        v.C[0] = const_cast<float*>(cin);
+        v.C[1] = cout;
+        if (kk_out) v.kk = kk_out;
+        launch_diffusion(v, c->op, 0, sync, 0, c->sargs, ref, false, 256, st);
+    }
+
+    // One forward step j (from the synchronisation at t_j).  With `store`, every
+    // sub-step writes a fresh buffer so that all intermediates the reverse of
+    // this step needs stay in place (the state itself is restored from a
+    // checkpoint afterwards).
     void fwd_step(int64_t j, bool store) {
-        const size_t N = c->n_nodes, r = R();
         const StepRef ref{nullptr, (long long)(n0 + j)};
-        int buf = c->cur;
-        for (int i = 0; i < c->l; ++i) {
-            if (store) copy(b->d1[i], c->s.V[buf], N * r);
-            launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
-            buf ^= 1;
+        if (!store) {
+            int buf = c->cur;
+            for (int i = 0; i < c->l; ++i) {
+                launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
+                buf ^= 1;
+            }
+            if (c->s.prec == P_F64) react_fwd<double, false>(buf, j);
+            else if (c->s.kahan) react_fwd<float, true>(buf, j);
+            else react_fwd<float, false>(buf, j);
+            for (int i = 0; i < c->l; ++i) {
+                launch_diffusion(c->s, c->op, buf, i == c->l - 1, 0, c->sargs, ref, false, 256, st);
+                buf ^= 1;
+            }
+            ++fwd_steps;
+            return;
         }
-        if (store) {
-            copy(b->rv, c->s.V[buf], N * r);
-            if (b->kahan) copy(b->rc, c->s.C[buf], N * 4);
-            copy(b->rh, c->s.S, N * r);
-            copy(b->kused, c->s.kk, N);
+        const int l = c->l;
+        const void* x = c->s.V[c->cur];
+        const float* cx = b->kahan ? c->s.C[c->cur] : nullptr;
+        for (int i = 0; i < l; ++i) {
+            b->d1[i] = x;
+            diffuse_view(x, b->P[i], cx, b->kahan ? b->CP[i] : nullptr, false, ref, nullptr);
+            x = b->P[i];
+            cx = b->kahan ? b->CP[i] : nullptr;
         }
-        if (c->s.prec == P_F64) react_fwd<double, false>(buf, j);
-        else if (c->s.kahan) react_fwd<float, true>(buf, j);
-        else react_fwd<float, false>(buf, j);
-        for (int i = 0; i < c->l; ++i) {
-            if (store) copy(b->d2[i], c->s.V[buf], N * r);
-            launch_diffusion(c->s, c->op, buf, i == c->l - 1, 0, c->sargs, ref, false, 256, st);
-            buf ^= 1;
+        b->rv = x;
+        b->rc = cx;
+        b->rh = c->s.S;
+        b->kused = c->s.kk;
+        void* y = b->P[l];
+        float* cy = b->kahan ? b->CP[l] : nullptr;
+        if (c->s.prec == P_F64) react_fwd<double, false>(c->cur, j, const_cast<void*>(x), nullptr, y, nullptr, b->Hout);
+        else if (c->s.kahan)
+            react_fwd<float, true>(c->cur, j, const_cast<void*>(x), const_cast<float*>(cx), y, cy, b->Hout);
+        else react_fwd<float, false>(c->cur, j, const_cast<void*>(x), nullptr, y, nullptr, b->Hout);
+        const void* yi = y;
+        const float* cyi = cy;
+        for (int i = 0; i < l; ++i) {
+            b->d2[i] = yi;
+            void* o = b->P[l + 1 + i];
+            float* co = b->kahan ? b->CP[l + 1 + i] : nullptr;
+            diffuse_view(yi, o, cyi, co, i == l - 1, ref, b->kk_next);
+            yi = o;
+            cyi = co;
         }
-        if (store) copy(b->vend, c->s.V[buf], N * r);
+        b->vend = yi;
         ++fwd_steps;
     }
 
@@ -474,16 +536,15 @@ int ensure_buffers(daeti_ctx* c, int n_slots, int n_sensors, int n_samples, int6
              (!b->kahan || b->sC.back());
     }
     b->slot_step.assign(n_slots, -1);
-    for (int i = 0; i < c->l; ++i) {
-        b->d1.push_back(al(N * r));
-        b->d2.push_back(al(N * r));
-        ok = ok && b->d1.back() && b->d2.back();
+    b->d1.assign(c->l, nullptr);
+    b->d2.assign(c->l, nullptr);
+    for (int i = 0; i < 2 * c->l + 1; ++i) {
+        b->P.push_back(al(N * r));
+        b->CP.push_back(b->kahan ? (float*)al(N * 4) : nullptr);
+        ok = ok && b->P.back() && (!b->kahan || b->CP.back());
     }
-    b->rv = al(N * r);
-    b->rh = al(N * r);
-    b->rc = b->kahan ? (float*)al(N * 4) : nullptr;
-    b->kused = (uint8_t*)al(N);
-    b->vend = al(N * r);
+    b->Hout = al(N * r);
+    b->kk_next = (uint8_t*)al(N);
     b->mu[0] = al(N * r);
     b->mu[1] = al(N * r);
     b->lamh = al(N * r);
@@ -497,8 +558,8 @@ int ensure_buffers(daeti_ctx* c, int n_slots, int n_sensors, int n_samples, int6
         b->hist_b = (uint16_t*)al((size_t)hist_steps * N * 2);
         ok = ok && b->hist_k && b->hist_b;
     }
-    ok = ok && b->rv && b->rh && b->kused && b->vend && b->mu[0] && b->mu[1] && b->lamh && b->mR && b->g_elem &&
-         b->acc && b->sensors && b->data && (!b->kahan || b->rc);
+    ok = ok && b->Hout && b->kk_next && b->mu[0] && b->mu[1] && b->lamh && b->mR && b->g_elem && b->acc &&
+         b->sensors && b->data;
     if (!ok) {
         free_adjoint(c);
         return fail(c, DAETI_ENOMEM, "adjoint buffers");
@@ -547,22 +608,51 @@ extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors
     CK(cudaMemsetAsync(b->acc, 0, 16, st));
 
     Adj A{c, b, st, c->nstep, sample_every, record ? 1 : (replay ? 2 : 0)};
-    std::fill(b->slot_step.begin(), b->slot_step.end(), -1);
-    A.save(0, 0);
     if (no_grad) {
+        std::fill(b->slot_step.begin(), b->slot_step.end(), -1);
+        A.save(0, 0);
         for (int64_t j = 0; j < n_steps; ++j) {
             A.fwd_step(j, false);
             if (c->s.prec == P_F64) A.loss_at<double>(j, c->s.V[c->cur], false);
             else A.loss_at<float>(j, c->s.V[c->cur], false);
         }
+        A.restore(0);   // the context keeps its starting state
     } else {
-        CK(cudaMemsetAsync(b->mu[0], 0, N * r, st));
-        CK(cudaMemsetAsync(b->mu[1], 0, N * r, st));
-        CK(cudaMemsetAsync(b->lamh, 0, N * r, st));
-        CK(cudaMemsetAsync(b->g_elem, 0, 8 * (size_t)c->n_elem, st));
-        A.reverse(0, n_steps, 0);
+        const int64_t key[5] = {n_steps, n_slots, sample_every, n_samples, c->nstep * 2 + c->cur};
+        if (!b->graph || std::memcmp(key, b->gkey, sizeof(key)) != 0) {
+            if (b->graph) {
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+            // record the sweep on the capture stream: costates and gradients
+            // cleared, start saved, binomial reverse sweep, start restored
+            Adj G{c, b, c->cap_stream, c->nstep, sample_every, 0};
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaMemsetAsync(b->acc, 0, 16, c->cap_stream);
+            cudaMemsetAsync(b->mu[0], 0, N * r, c->cap_stream);
+            cudaMemsetAsync(b->mu[1], 0, N * r, c->cap_stream);
+            cudaMemsetAsync(b->lamh, 0, N * r, c->cap_stream);
+            cudaMemsetAsync(b->g_elem, 0, 8 * (size_t)c->n_elem, c->cap_stream);
+            std::fill(b->slot_step.begin(), b->slot_step.end(), -1);
+            G.save(0, 0);
+            G.reverse(0, n_steps, 0);
+            G.restore(0);
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("adjoint capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->graph = nullptr;
+                return fail(c, DAETI_ECUDA, std::string("adjoint graph: ") + cudaGetErrorString(e));
+            }
+            std::memcpy(b->gkey, key, sizeof(key));
+            A.fwd_steps = G.fwd_steps;
+        } else {
+            A.fwd_steps = c->adj_fwd_steps;
+        }
+        CK(cudaGraphLaunch(b->graph, st));
     }
-    A.restore(0);   // the context keeps its starting state
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     double acc[2];

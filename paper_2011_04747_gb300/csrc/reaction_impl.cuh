@@ -164,7 +164,11 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
         __syncthreads();
         total = off[0];
     }
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // Item warps are dealt to blocks round-robin (item warp u = j * gridDim.x +
+    // block, j the warp within the block), so the few heavy (large k) warps at
+    // the head of the list land on different SMs instead of a handful of blocks.
+    const int u = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int t = a.lists ? u * 32 + (threadIdx.x & 31) : blockIdx.x * blockDim.x + threadIdx.x;
     if (t < total) {
         int i, k;
         if (a.lists) {

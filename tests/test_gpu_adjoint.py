@@ -143,3 +143,19 @@ def test_autograd_wrapper():
     assert abs(float(loss.detach()) - lo) <= 1e-9 * lo
     assert _rel(d_node.grad.numpy(), 2.0 * adjoint.nodal_gradient(conn, ge, wl.n_nodes)) <= 1e-8
     assert abs(float(tau.grad) - 2.0 * gt) <= 1e-8 * abs(2.0 * gt)
+
+
+def test_adjoint_graph_replay_repeats_exactly():
+    """The gradient sweep is captured once and replayed: a second call (and a call
+    after a different request) returns the same loss and gradients."""
+    wl, prob, d_elem, sensors, data, n_steps = _small(n=10, n_steps=120)
+    s = _gpu(wl, d_elem, "fp32_kahan")
+    a = s.daeti_adjoint(sensors, data, n_steps, 10, n_slots=4, n_elem=len(d_elem))
+    b = s.daeti_adjoint(sensors, data, n_steps, 10, n_slots=4, n_elem=len(d_elem))
+    c = s.daeti_adjoint(sensors, data[:6], 60, 10, n_slots=4, n_elem=len(d_elem))
+    d = s.daeti_adjoint(sensors, data, n_steps, 10, n_slots=4, n_elem=len(d_elem))
+    s.close()
+    for x in (b, d):
+        assert abs(x[0] - a[0]) <= 1e-12 * a[0] and abs(x[2] - a[2]) <= 1e-9 * abs(a[2])
+        assert np.allclose(x[1], a[1], rtol=1e-9, atol=1e-12 * np.abs(a[1]).max())
+    assert c[0] < a[0]
