@@ -207,8 +207,11 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
  * 256), or 0 for the shared-memory tiled kernel on structured grids;
  * fuse_diffusion: run the last diffusion sub-step of step I inside the
  * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
- * steps per captured CUDA graph (rounded up to even, 0 = plain launches).
- * set waits for enqueued work and drops captured graphs. */
+ * steps per captured CUDA graph (rounded up to even, 0 = plain launches);
+ * pdl: 1 = launch the per-step kernels with
+ * programmatic dependent launch, so each one's blocks are resident when its
+ * predecessor ends (default), 0 = plain launches.  set waits for enqueued
+ * work and drops captured graphs. */
 typedef struct daeti_tuning {
     int32_t struct_size;       /* sizeof(daeti_tuning) */
     int32_t react_block;
@@ -217,6 +220,7 @@ typedef struct daeti_tuning {
     int32_t fuse_diffusion;
     int32_t bucket_k;
     int32_t graph_steps;
+    int32_t pdl;
 } daeti_tuning;
 int daeti_get_tuning(daeti_ctx* ctx, daeti_tuning* tuning);
 int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);

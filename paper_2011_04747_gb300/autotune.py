@@ -3,7 +3,7 @@
 For a prepared ``Solver`` it times a short stretch of the simulation under
 each candidate tuning (reaction block size and register cap, the diffusion
 sub-step fused into the reaction launch or not, k bucketing, diffusion block
-size, steps per CUDA graph), keeps only candidates whose final state is
+size, steps per CUDA graph, programmatic dependent launch), keeps only candidates whose final state is
 bit-identical to the reference run (the shapes must not change results), and
 applies the fastest.  Choices are cached as JSON keyed by the problem's
 signature (mesh, model, precision, l, k_max, GPU name) so a later run of the
@@ -26,6 +26,7 @@ DEFAULT_SPACE = {
     "bucket_k": (1, 0),
     "diff_block": (0, 256),
     "graph_steps": (20, 100),
+    "pdl": (1, 0),
 }
 
 

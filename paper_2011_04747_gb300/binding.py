@@ -64,10 +64,12 @@ class daeti_tuning(ctypes.Structure):
         ("fuse_diffusion", ctypes.c_int32),
         ("bucket_k", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
+        ("pdl", ctypes.c_int32),
     ]
 
 
-TUNING_FIELDS = ("react_block", "react_min_blocks", "diff_block", "fuse_diffusion", "bucket_k", "graph_steps")
+TUNING_FIELDS = ("react_block", "react_min_blocks", "diff_block", "fuse_diffusion", "bucket_k", "graph_steps",
+                 "pdl")
 
 _lib = None
 

@@ -325,6 +325,7 @@ struct Adj {
     void diffuse_view(const void* in, void* out, const float* cin, float* cout, bool sync, StepRef ref,
                       uint8_t* kk_out) {
         DevState v = c->s;
+        v.vpad = 0;
         v.V[0] = const_cast<void*>(in);
         v.V[1] = out;
         v.C[0] = const_cast<float*>(cin);
@@ -411,6 +412,7 @@ struct Adj {
 
     void mu_substep() {
         DevState view = c->s;
+        view.vpad = 0;
         view.V[0] = b->mu[0];
         view.V[1] = b->mu[1];
         view.C[0] = view.C[1] = nullptr;

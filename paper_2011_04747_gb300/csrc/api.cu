@@ -121,7 +121,8 @@ void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bo
 
 void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
     Timer t(c, st, timed, 1);
-    launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st);
+    launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st,
+                     c->rtune.pdl != 0);
 }
 
 // One Strang step from a synchronisation to the next: step I (l sub-steps,
@@ -623,7 +624,15 @@ int daeti_prepare(daeti_ctx* c) {
     // ---- device state
     const size_t R = rsize(c);
     void* p = nullptr;
-    if ((rc = dalloc(c, &c->s.V[0], R * N)) || (rc = dalloc(c, &c->s.V[1], R * N))) return rc;
+    // V buffers of a structured grid carry a zeroed ghost margin of the stencil
+    // reach on both sides, so the stencil needs no per-neighbour boundary tests
+    const int64_t pad = table ? 1 + (int64_t)tab.nx + (tab.dim == 3 ? (int64_t)tab.nx * tab.ny : 0) : 0;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dalloc(c, &p, R * (N + 2 * pad)))) return rc;
+        CK(set_(c, p, 0, R * (N + 2 * pad)));
+        c->s.V[b] = (char*)p + R * pad;
+    }
+    c->s.vpad = pad;
     if (c->s.kahan) {
         if ((rc = dalloc(c, &p, 4 * N))) return rc;
         c->s.C[0] = (float*)p;
@@ -1014,6 +1023,7 @@ int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
     t->fuse_diffusion = c->fused ? 1 : 0;
     t->bucket_k = c->lists ? 1 : 0;
     t->graph_steps = c->graph_steps;
+    t->pdl = c->rtune.pdl;
     return DAETI_OK;
 }
 
@@ -1021,13 +1031,14 @@ int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
     if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block < 0 ||
         t->diff_block > 256 || t->diff_block % 32 || t->graph_steps < 0 ||
-        (t->react_min_blocks != 8 && t->react_min_blocks != 10))
+        (t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1))
         return fail(c, DAETI_EINVAL, "bad tuning values");
     int rc = daeti_synchronize(c);
     if (rc) return rc;
     drop_graphs(c);
     c->rtune.block = t->react_block;
     c->rtune.min_blocks = t->react_min_blocks;
+    c->rtune.pdl = t->pdl;
     c->diff_block = t->diff_block;
     c->fused = t->fuse_diffusion != 0;
     const bool new_lists = t->bucket_k != 0;

@@ -64,12 +64,14 @@ struct TP06State {
     R V, Cai, CaSR, CaSS, Nai, Ki, m, h, j, xr1, xr2, xs, r, s, d, f, f2, fcass, RR;
 };
 
-// Gate update toward g_inf with rate 1/tau over dt (Rush-Larsen or forward Euler).
+// Gate update toward g_inf with rate 1/tau over dt: Rush-Larsen
+// g_inf + (g - g_inf) e^{-dt rate}, the exponential taken as 2^{ndtl rate}
+// with ndtl = -dt log2(e); or forward Euler.
 template <typename R>
-__device__ __forceinline__ R gate_rate(R g, R ginf, R rate, R dt, int rl) {
+__device__ __forceinline__ R gate_rate(R g, R ginf, R rate, R dt, R ndtl, int rl) {
     typedef Fm<R> M;
-    if (rl) return ginf - (ginf - g) * M::ex(-dt * rate);
-    return g + dt * rate * (ginf - g);
+    if (rl) return fma(g - ginf, M::ex2(ndtl * rate), ginf);
+    return fma(dt * rate, ginf - g, g);
 }
 
 // x / (e^x - 1) given e = e^x, with its series near x = 0 (removable
@@ -87,73 +89,80 @@ __device__ __forceinline__ double x_over_expm1<double>(double x, double e) {
     return x / expm1(x);
 }
 
+// exp(c q^2 + b) for compile-time constants c, b.
+#define EXQ(q, c, b) M::ex2(fma((q) * (R)((c) * DAETI_LOG2E), (q), (R)((b) * DAETI_LOG2E)))
+
 // One sub-step.  The published rate expressions are regrouped so that each
 // gate and each saturating term costs a single reciprocal: time constants
 // enter as rates 1/tau, products of logistic factors are put over one
 // common denominator, and reversal potentials use ln(c_out) - ln(c_in).
+// Every exponential exp(a V + b) (and c exp(a V) as exp(a V + ln c)) is
+// written as 2^(a' V + b') with the constants scaled by log2(e) at compile
+// time, one FMA and one SFU operation each.
 template <typename R>
 __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
     typedef TP06Consts C;
     typedef Fm<R> M;
     const R one = (R)1;
-    const R RTF = (R)(C::R_ * C::T_ / C::F_);
-    const R FRT = (R)(C::F_ / (C::R_ * C::T_));
+    constexpr double RTFd = C::R_ * C::T_ / C::F_;
+    constexpr double FRTd = C::F_ / (C::R_ * C::T_);
     const R V = x.V;
+    const R ndtl = dt * (R)(-DAETI_LOG2E);
 
-    // reversal potentials
-    const R lnKi = M::lg(x.Ki);
-    const R EK = RTF * ((R)1.6863989535702288 - lnKi);   // ln(5.4)
-    const R ENa = RTF * ((R)4.941642422609304 - M::lg(x.Nai));   // ln(140)
-    const R EKs = RTF * ((R)2.2617630984737906 - M::lg(x.Ki + (R)C::pKNa * x.Nai));   // ln(5.4 + 0.03*140)
-    const R ECa = (R)0.5 * RTF * ((R)0.6931471805599453 - M::lg(x.Cai));   // ln(2)
+    // reversal potentials: E = RT/F (ln c_out - ln c_in), ln c = ln2 log2 c
+    const R EK = fma(M::lg2(x.Ki), (R)(-RTFd * DAETI_LN2), (R)(RTFd * 1.6863989535702288));   // ln(5.4)
+    const R ENa = fma(M::lg2(x.Nai), (R)(-RTFd * DAETI_LN2), (R)(RTFd * 4.941642422609304));   // ln(140)
+    const R EKs = fma(M::lg2(fma((R)C::pKNa, x.Nai, x.Ki)), (R)(-RTFd * DAETI_LN2),
+                      (R)(RTFd * 2.2617630984737906));   // ln(5.4 + 0.03*140)
+    const R ECa = fma(M::lg2(x.Cai), (R)(-0.5 * RTFd * DAETI_LN2), (R)(0.5 * RTFd * DAETI_LN2));   // ln(2)
 
     // inward rectifier: x_K1 = a/(a+b) with a = 0.1/(1+e0), b = (3 e1 + e2)/(1+e3)
     const R vek = V - EK;
-    const R e0 = M::ex((R)0.06 * (vek - (R)200));
-    const R e1 = M::ex((R)0.0002 * (vek + (R)100));
-    const R e2 = M::ex((R)0.1 * (vek - (R)10));
-    const R e3 = M::ex((R)-0.5 * vek);
-    const R ak = (R)0.1 * (one + e3);
-    const R xk1 = M::dv(ak, ak + ((R)3 * e1 + e2) * (one + e0));
+    const R e0 = EXL(vek, 0.06, -12.0);
+    const R e1 = EXL(vek, 0.0002, 0.02 + 1.0986122886681098);   // 3 e^{0.0002 (vek + 100)}
+    const R e2 = EXL(vek, 0.1, -1.0);
+    const R e3 = EXL(vek, -0.5, 0.0);
+    const R ak = fma((R)0.1, e3, (R)0.1);
+    const R xk1 = M::dv(ak, fma(e1 + e2, one + e0, ak));
 
     const R Gks = prm.celltype == 2 ? (R)0.098 : (R)0.392;
     const R Gto = prm.celltype == 0 ? (R)0.073 : (R)0.294;
 
     const R INa = (R)C::GNa * x.m * x.m * x.m * x.h * x.j * (V - ENa);
     // I_CaL = G d f f2 fCass 4 (V-15) F^2/RT (0.25 CaSS e^x - Cao)/(e^x - 1), x = 2 (V-15) F/RT
-    const R xc = (R)2 * (V - (R)15) * FRT;
-    const R exc = M::ex(xc);
-    const R ICaL = (R)C::GCaL * x.d * x.f * x.f2 * x.fcass * (R)(2.0 * C::F_) *
-                   ((R)0.25 * x.CaSS * exc - (R)C::Cao) * x_over_expm1<R>(xc, exc);
+    const R xc = fma(V, (R)(2.0 * FRTd), (R)(-30.0 * FRTd));
+    const R exc = EXL(V, 2.0 * FRTd, -30.0 * FRTd);
+    const R ICaL = (R)(C::GCaL * 2.0 * C::F_) * x.d * x.f * x.f2 * x.fcass *
+                   fma((R)0.25 * x.CaSS, exc, (R)-C::Cao) * x_over_expm1<R>(xc, exc);
     const R Ito = Gto * x.r * x.s * vek;
     const R IKr = (R)C::GKr * x.xr1 * x.xr2 * vek;   // sqrt(Ko/5.4) = 1
     const R IKs = Gks * x.xs * x.xs * (V - EKs);
     const R IK1 = (R)C::GK1 * xk1 * vek;             // sqrt(Ko/5.4) = 1
-    const R em = M::ex(-V * FRT);                    // e^{-VF/RT}
-    const R e_g = M::ex((R)C::gam * V * FRT);        // e^{gamma VF/RT}
+    const R em = EXL(V, -FRTd, 0.0);                 // e^{-VF/RT}
+    const R e_g = EXL(V, C::gam * FRTd, 0.0);        // e^{gamma VF/RT}
     const R e_g1 = e_g * em;                         // e^{(gamma-1) VF/RT}
-    const R INaCa = M::dv((R)C::knaca * (e_g * x.Nai * x.Nai * x.Nai * (R)C::Cao -
-                                         e_g1 * (R)(C::Nao * C::Nao * C::Nao) * x.Cai * (R)C::alf),
-                          (R)((C::KmNai * C::KmNai * C::KmNai + C::Nao * C::Nao * C::Nao) * (C::KmCa + C::Cao)) *
-                              (one + (R)C::ksat * e_g1));
+    const R nai3 = x.Nai * x.Nai * x.Nai;
+    const R INaCa = M::dv(fma(e_g * nai3, (R)(C::knaca * C::Cao),
+                              e_g1 * x.Cai * (R)(-C::knaca * C::Nao * C::Nao * C::Nao * C::alf)),
+                          fma((R)(C::ksat * (C::KmNai * C::KmNai * C::KmNai + C::Nao * C::Nao * C::Nao) * (C::KmCa + C::Cao)),
+                              e_g1, (R)((C::KmNai * C::KmNai * C::KmNai + C::Nao * C::Nao * C::Nao) * (C::KmCa + C::Cao))));
     const R INaK = M::dv((R)(C::knak * C::Ko / (C::Ko + C::KmK)) * x.Nai,
-                         (x.Nai + (R)C::KmNa) * (one + (R)0.1245 * M::ex((R)-0.1 * V * FRT) + (R)0.0353 * em));
+                         (x.Nai + (R)C::KmNa) * fma((R)0.0353, em, one + EXL(V, -0.1 * FRTd, -2.083449563077375)));   // ln 0.1245
     const R IpCa = M::dv((R)C::GpCa * x.Cai, (R)C::KpCa + x.Cai);
-    const R IpK = M::dv((R)C::GpK * vek, one + M::ex(((R)25 - V) * (R)(1.0 / 5.98)));
+    const R IpK = M::dv((R)C::GpK * vek, one + EXL(V, -1.0 / 5.98, 25.0 / 5.98));
     const R IbNa = (R)C::GbNa * (V - ENa);
     const R IbCa = (R)C::GbCa * (V - ECa);
 
     const R Iion = IKr + IKs + IK1 + Ito + INa + IbNa + ICaL + IbCa + INaK + INaCa + IpCa + IpK;
-    const R dV = -Iion + J;
+    const R dV = J - Iion;
 
     // calcium handling
     const R sr2 = x.CaSR * x.CaSR;
     const R kcasr = (R)C::maxsr - M::dv((R)(C::maxsr - C::minsr) * sr2, sr2 + (R)(C::EC * C::EC));
-    const R k2 = (R)C::k2p * kcasr;
-    const R dRR = -k2 * x.CaSS * x.RR + (R)C::k4 * (one - x.RR);
+    const R dRR = fma((R)-C::k2p * kcasr * x.CaSS, x.RR, (R)C::k4 * (one - x.RR));
     const R css2 = x.CaSS * x.CaSS;
     // O = k1 CaSS^2 RR / (k3 + k1 CaSS^2) with k1 = k1' / kcasr
-    const R O = M::dv((R)C::k1p * css2 * x.RR, (R)C::k3 * kcasr + (R)C::k1p * css2);
+    const R O = M::dv((R)C::k1p * css2 * x.RR, fma((R)C::k3, kcasr, (R)C::k1p * css2));
     const R Irel = (R)C::Vrel * O * (x.CaSR - x.CaSS);
     const R ci2 = x.Cai * x.Cai;
     const R Iup = M::dv((R)C::Vmaxup * ci2, ci2 + (R)(C::Kup * C::Kup));
@@ -162,9 +171,9 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const R ci = x.Cai + (R)C::Kbufc;
     const R csr = x.CaSR + (R)C::Kbufsr;
     const R css = x.CaSS + (R)C::Kbufss;
-    const R bi = M::dv(ci * ci, ci * ci + (R)(C::Bufc * C::Kbufc));
-    const R bsr = M::dv(csr * csr, csr * csr + (R)(C::Bufsr * C::Kbufsr));
-    const R bss = M::dv(css * css, css * css + (R)(C::Bufss * C::Kbufss));
+    const R bi = M::dv(ci * ci, fma(ci, ci, (R)(C::Bufc * C::Kbufc)));
+    const R bsr = M::dv(csr * csr, fma(csr, csr, (R)(C::Bufsr * C::Kbufsr)));
+    const R bss = M::dv(css * css, fma(css, css, (R)(C::Bufss * C::Kbufss)));
     const R dCai = bi * ((Ileak - Iup) * (R)(C::Vsr / C::Vc) + Ixfer -
                          (IbCa + IpCa - (R)2 * INaCa) * (R)(C::Cm / (2.0 * C::Vc * C::F_)));
     const R dCaSR = bsr * (Iup - Irel - Ileak);
@@ -177,115 +186,116 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const int rl = prm.gate_rl;
     {
         // m: tau = a b, a = 1/(1+ea), b = 0.1/(1+eb) + 0.1/(1+ec)
-        const R e_inf = one + M::ex(((R)-56.86 - V) * (R)(1.0 / 9.03));
+        const R e_inf = one + EXL(V, -1.0 / 9.03, -56.86 / 9.03);
         const R minf = M::dv(one, e_inf * e_inf);
-        const R ea = one + M::ex(((R)-60 - V) * (R)0.2);
-        const R eb = one + M::ex((V + (R)35) * (R)0.2);
-        const R ec = one + M::ex((V - (R)50) * (R)0.005);
+        const R ea = one + EXL(V, -0.2, -12.0);
+        const R eb = one + EXL(V, 0.2, 7.0);
+        const R ec = one + EXL(V, 0.005, -0.25);
         const R rate = M::dv(ea * eb * ec, (R)0.1 * (eb + ec));
-        x.m = gate_rate(x.m, minf, rate, dt, rl);
+        x.m = gate_rate(x.m, minf, rate, dt, ndtl, rl);
     }
     {
-        const R eh = one + M::ex((V + (R)71.55) * (R)(1.0 / 7.43));
+        const R eh = one + EXL(V, 1.0 / 7.43, 71.55 / 7.43);
         const R hinf = M::dv(one, eh * eh);
         R rh, rj;
         if (V >= (R)-40) {
             // a_h = a_j = 0
-            rh = M::dv((R)(0.77 / 0.13), one + M::ex(-(V + (R)10.66) * (R)(1.0 / 11.1)));
-            rj = M::dv((R)0.6 * M::ex((R)0.057 * V), one + M::ex((R)-0.1 * (V + (R)32)));
+            rh = M::dv((R)(0.77 / 0.13), one + EXL(V, -1.0 / 11.1, -10.66 / 11.1));
+            rj = M::dv(EXL(V, 0.057, -0.5108256237659907), one + EXL(V, -0.1, -3.2));   // ln 0.6
         } else {
-            rh = (R)0.057 * M::ex(-(V + (R)80) * (R)(1.0 / 6.8)) + (R)2.7 * M::ex((R)0.079 * V) +
-                 (R)3.1e5 * M::ex((R)0.3485 * V);
-            const R da = one + M::ex((R)0.311 * (V + (R)79.23));
-            const R db = one + M::ex((R)-0.1378 * (V + (R)40.14));
-            const R na = ((R)-2.5428e4 * M::ex((R)0.2444 * V) - (R)6.948e-6 * M::ex((R)-0.04391 * V)) * (V + (R)37.78);
-            const R nb = (R)0.02424 * M::ex((R)-0.01052 * V);
-            rj = M::dv(na * db + nb * da, da * db);
+            rh = EXL(V, -1.0 / 6.8, -80.0 / 6.8 - 2.864704011147587) +   // ln 0.057
+                 EXL(V, 0.079, 0.9932517730102834) +                  // ln 2.7
+                 EXL(V, 0.3485, 12.644327576461329);                  // ln 3.1e5
+            const R da = one + EXL(V, 0.311, 0.311 * 79.23);
+            const R db = one + EXL(V, -0.1378, -0.1378 * 40.14);
+            const R na = -(EXL(V, 0.2444, 10.1436062080563) + EXL(V, -0.04391, -11.877056709585416)) *
+                         (V + (R)37.78);   // ln 2.5428e4, ln 6.948e-6
+            const R nb = EXL(V, -0.01052, -3.719751117781023);   // ln 0.02424
+            rj = M::dv(fma(na, db, nb * da), da * db);
         }
-        x.h = gate_rate(x.h, hinf, rh, dt, rl);
-        x.j = gate_rate(x.j, hinf, rj, dt, rl);
+        x.h = gate_rate(x.h, hinf, rh, dt, ndtl, rl);
+        x.j = gate_rate(x.j, hinf, rj, dt, ndtl, rl);
     }
     {
         // xr1: tau = 450/(1+e1) * 6/(1+e2)
-        const R inf = M::dv(one, one + M::ex(((R)-26 - V) * (R)(1.0 / 7.0)));
-        const R rate = (one + M::ex(((R)-45 - V) * (R)0.1)) * (one + M::ex((V + (R)30) * (R)(1.0 / 11.5))) *
-                       (R)(1.0 / 2700.0);
-        x.xr1 = gate_rate(x.xr1, inf, rate, dt, rl);
+        const R inf = M::dv(one, one + EXL(V, -1.0 / 7.0, -26.0 / 7.0));
+        const R rate = (one + EXL(V, -0.1, -4.5)) * fma(EXL(V, 1.0 / 11.5, 30.0 / 11.5), (R)(1.0 / 2700.0), (R)(1.0 / 2700.0));
+        x.xr1 = gate_rate(x.xr1, inf, rate, dt, ndtl, rl);
     }
     {
         // xr2: tau = 3/(1+e1) * 1.12/(1+e2)
-        const R inf = M::dv(one, one + M::ex((V + (R)88) * (R)(1.0 / 24.0)));
-        const R rate = (one + M::ex(((R)-60 - V) * (R)0.05)) * (one + M::ex((V - (R)60) * (R)0.05)) *
-                       (R)(1.0 / 3.36);
-        x.xr2 = gate_rate(x.xr2, inf, rate, dt, rl);
+        const R inf = M::dv(one, one + EXL(V, 1.0 / 24.0, 88.0 / 24.0));
+        const R rate = (one + EXL(V, -0.05, -3.0)) * fma(EXL(V, 0.05, -3.0), (R)(1.0 / 3.36), (R)(1.0 / 3.36));
+        x.xr2 = gate_rate(x.xr2, inf, rate, dt, ndtl, rl);
     }
     {
         // xs: tau = 1400/sqrt(1+e1) / (1+e2) + 80
-        const R inf = M::dv(one, one + M::ex(((R)-5 - V) * (R)(1.0 / 14.0)));
-        const R d2 = one + M::ex((V - (R)35) * (R)(1.0 / 15.0));
-        const R rate = M::dv(d2, (R)1400 * M::rsq(one + M::ex(((R)5 - V) * (R)(1.0 / 6.0))) + (R)80 * d2);
-        x.xs = gate_rate(x.xs, inf, rate, dt, rl);
+        const R inf = M::dv(one, one + EXL(V, -1.0 / 14.0, -5.0 / 14.0));
+        const R d2 = one + EXL(V, 1.0 / 15.0, -35.0 / 15.0);
+        const R rate = M::dv(d2, fma((R)1400, M::rsq(one + EXL(V, -1.0 / 6.0, 5.0 / 6.0)), (R)80 * d2));
+        x.xs = gate_rate(x.xs, inf, rate, dt, ndtl, rl);
     }
     {
-        const R inf = M::dv(one, one + M::ex(((R)20 - V) * (R)(1.0 / 6.0)));
+        const R inf = M::dv(one, one + EXL(V, -1.0 / 6.0, 20.0 / 6.0));
         const R v40 = V + (R)40;
-        const R rate = M::dv(one, (R)9.5 * M::ex(-v40 * v40 * (R)(1.0 / 1800.0)) + (R)0.8);
-        x.r = gate_rate(x.r, inf, rate, dt, rl);
+        const R rate = M::dv(one, EXQ(v40, -1.0 / 1800.0, 2.2512917986064953) + (R)0.8);   // ln 9.5
+        x.r = gate_rate(x.r, inf, rate, dt, ndtl, rl);
     }
     {
         R inf, rate;
         if (prm.celltype == 0) {
-            inf = M::dv(one, one + M::ex((V + (R)28) * (R)0.2));
+            inf = M::dv(one, one + EXL(V, 0.2, 5.6));
             const R v67 = V + (R)67;
-            rate = M::dv(one, (R)1000 * M::ex(-v67 * v67 * (R)0.001) + (R)8);
+            rate = M::dv(one, EXQ(v67, -0.001, 6.907755278982137) + (R)8);   // ln 1000
         } else {
-            inf = M::dv(one, one + M::ex((V + (R)20) * (R)0.2));
+            inf = M::dv(one, one + EXL(V, 0.2, 4.0));
             const R v45 = V + (R)45;
-            const R dd = one + M::ex((V - (R)20) * (R)0.2);
+            const R dd = one + EXL(V, 0.2, -4.0);
             // tau = 85 e + 5/dd + 3
-            rate = M::dv(dd, ((R)85 * M::ex(-v45 * v45 * (R)(1.0 / 320.0)) + (R)3) * dd + (R)5);
+            rate = M::dv(dd, fma(EXQ(v45, -1.0 / 320.0, 4.442651256490317) + (R)3, dd, (R)5));   // ln 85
         }
-        x.s = gate_rate(x.s, inf, rate, dt, rl);
+        x.s = gate_rate(x.s, inf, rate, dt, ndtl, rl);
     }
     {
         // d: tau = (1.4/d1 + 0.25) (1.4/d2) + 1/d3
-        const R inf = M::dv(one, one + M::ex(((R)-8 - V) * (R)(1.0 / 7.5)));
-        const R d1 = one + M::ex(((R)-35 - V) * (R)(1.0 / 13.0));
-        const R d2 = one + M::ex((V + (R)5) * (R)0.2);
-        const R d3 = one + M::ex(((R)50 - V) * (R)0.05);
-        const R rate = M::dv(d1 * d2 * d3, ((R)1.4 + (R)0.25 * d1) * (R)1.4 * d3 + d1 * d2);
-        x.d = gate_rate(x.d, inf, rate, dt, rl);
+        const R inf = M::dv(one, one + EXL(V, -1.0 / 7.5, -8.0 / 7.5));
+        const R d1 = one + EXL(V, -1.0 / 13.0, -35.0 / 13.0);
+        const R d2 = one + EXL(V, 0.2, 1.0);
+        const R d3 = one + EXL(V, -0.05, 2.5);
+        const R rate = M::dv(d1 * d2 * d3, fma(fma((R)0.35, d1, (R)1.96), d3, d1 * d2));
+        x.d = gate_rate(x.d, inf, rate, dt, ndtl, rl);
     }
     {
         // f: tau = 1102.5 e + 200/f1 + 180/f2 + 20 ; f2: tau = 562 e' + 31/f1' + 80/f2
-        const R inf = M::dv(one, one + M::ex((V + (R)20) * (R)(1.0 / 7.0)));
+        const R inf = M::dv(one, one + EXL(V, 1.0 / 7.0, 20.0 / 7.0));
         const R v27 = V + (R)27;
-        const R f1 = one + M::ex(((R)13 - V) * (R)0.1);
-        const R f2 = one + M::ex((V + (R)30) * (R)0.1);
-        const R tnum = ((R)1102.5 * M::ex(-v27 * v27 * (R)(1.0 / 225.0)) + (R)20) * f1 * f2 + (R)200 * f2 +
-                       (R)180 * f1;
-        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, rl);
-        const R inf2 = M::dv((R)0.67, one + M::ex((V + (R)35) * (R)(1.0 / 7.0))) + (R)0.33;
-        const R g1 = one + M::ex(((R)25 - V) * (R)0.1);
-        const R tnum2 = (R)562 * M::ex(-v27 * v27 * (R)(1.0 / 240.0)) * g1 * f2 + (R)31 * f2 + (R)80 * g1;
-        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, rl);
+        const R f1 = one + EXL(V, -0.1, 1.3);
+        const R f2 = one + EXL(V, 0.1, 3.0);
+        const R tnum = fma((EXQ(v27, -1.0 / 225.0, 7.005335607321001) + (R)20) * f1, f2,   // ln 1102.5
+                           fma((R)200, f2, (R)180 * f1));
+        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, ndtl, rl);
+        const R inf2 = M::dv((R)0.67, one + EXL(V, 1.0 / 7.0, 5.0)) + (R)0.33;
+        const R g1 = one + EXL(V, -0.1, 2.5);
+        const R tnum2 = fma(EXQ(v27, -1.0 / 240.0, 6.331501849893691) * g1, f2,   // ln 562
+                            fma((R)31, f2, (R)80 * g1));
+        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, ndtl, rl);
     }
     {
         // fCass: inf = 0.6/den + 0.4, tau = 80/den + 2, den = 1 + (CaSS/0.05)^2
         const R q = x.CaSS * (R)20;
-        const R den = one + q * q;
+        const R den = fma(q, q, one);
         const R inv = M::dv(one, den);
-        x.fcass = gate_rate(x.fcass, (R)0.6 * inv + (R)0.4, M::dv(den, (R)80 + (R)2 * den), dt, rl);
+        x.fcass = gate_rate(x.fcass, fma((R)0.6, inv, (R)0.4), M::dv(den, fma((R)2, den, (R)80)), dt, ndtl, rl);
     }
 
     // forward Euler for V, concentrations and RR
     add_comp(x.V, cv, dt * dV);
-    x.Cai += dt * dCai;
-    x.CaSR += dt * dCaSR;
-    x.CaSS += dt * dCaSS;
-    x.Nai += dt * dNai;
-    x.Ki += dt * dKi;
-    x.RR += dt * dRR;
+    x.Cai = fma(dt, dCai, x.Cai);
+    x.CaSR = fma(dt, dCaSR, x.CaSR);
+    x.CaSS = fma(dt, dCaSS, x.CaSS);
+    x.Nai = fma(dt, dNai, x.Nai);
+    x.Ki = fma(dt, dKi, x.Ki);
+    x.RR = fma(dt, dRR, x.RR);
 }
 
 }  // namespace daeti

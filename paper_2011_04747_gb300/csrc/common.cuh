@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #define DAETI_MAX_STIM 32
@@ -48,6 +49,33 @@ __device__ __forceinline__ bool stim_overlaps(const StimDev& s, double t0, doubl
     return false;
 }
 
+// ------------------------------------------------- dependent launch overlap
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while its predecessor in
+// the stream drains, so its blocks are resident when the predecessor ends.
+// pdl_wait() blocks until the predecessor grid has completed and its writes
+// are visible (a no-op after a normal launch); every kernel that can be
+// launched that way calls it before its first global memory access.
+// pdl_trigger() allows the successor to be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, bool pdl,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------- precision
 template <typename R> struct Fm;
 template <> struct Fm<float> {
@@ -56,6 +84,19 @@ template <> struct Fm<float> {
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
     static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
+    // 2^x and log2(x) by the SFU instructions of the PTX ISA (ex2.approx,
+    // lg2.approx; relative error ~2^-22), so that exp(a v + b) = 2^(a' v + b')
+    // costs one FFMA with a' = a log2(e), b' = b log2(e) folded at compile time.
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float lg2(float x) {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
 };
 template <> struct Fm<double> {
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
@@ -63,7 +104,14 @@ template <> struct Fm<double> {
     static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double em1(double x) { return expm1(x); }
+    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
+    static __device__ __forceinline__ double lg2(double x) { return log2(x); }
 };
+
+#define DAETI_LOG2E 1.4426950408889634
+#define DAETI_LN2 0.6931471805599453
+// exp(a v + b) for compile-time constants a, b (R and M in scope).
+#define EXL(v, a, b) M::ex2(fma((v), (R)((a) * DAETI_LOG2E), (R)((b) * DAETI_LOG2E)))
 
 // v += d with optional Kahan compensation c (true value ~= v - c).
 template <typename R>

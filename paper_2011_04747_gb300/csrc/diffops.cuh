@@ -13,8 +13,11 @@ __device__ __forceinline__ int bclass(int x, int n) { return x == 0 ? 0 : (x == 
 
 // One explicit sub-step at a node whose neighbour at offset (dx,dy,dz) is
 // fetch(dx,dy,dz).  Shared by the plain and the fused kernels so both give
-// bit-identical results.
-template <typename R, int DIM, bool KAHAN, class Fetch>
+// the same results.  Offsets outside the grid have coefficient 0 in the
+// table; PAD (V buffers with a finite ghost margin wider than the stencil
+// reach) reads them anyway and adds 0 * (finite), which leaves the sum
+// unchanged, instead of testing the boundary class per neighbour.
+template <typename R, int DIM, bool KAHAN, bool PAD = false, class Fetch>
 __device__ __forceinline__ void stencil_update(const R* __restrict__ crow, int cx, int cy, int z, int nz, R vi,
                                                float ci, const Fetch& fetch, R& vout, float& cout) {
     R acc = (R)0;
@@ -25,8 +28,9 @@ __device__ __forceinline__ void stencil_update(const R* __restrict__ crow, int c
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 if (dx == 0 && dy == 0 && dz == 0) continue;
-                const bool ok = (dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
-                                (dy <= 0 || cy < 2) && (DIM == 2 || ((dz >= 0 || z > 0) && (dz <= 0 || z < nz - 1)));
+                const bool ok = PAD || ((dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
+                                        (dy <= 0 || cy < 2) &&
+                                        (DIM == 2 || ((dz >= 0 || z > 0) && (dz <= 0 || z < nz - 1))));
                 if (ok) {
                     const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
                     acc = fma(__ldg(crow + j), fetch(dx, dy, dz) - vi, acc);
@@ -75,8 +79,8 @@ struct OpView {
     const R* val;
 };
 
-// One sub-step at node i from vin (and cin), any layout.
-template <typename R, int DIM, bool KAHAN>
+// One sub-step at node i from vin (and cin), any layout (PAD: see stencil_update).
+template <typename R, int DIM, bool KAHAN, bool PAD = false>
 __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __restrict__ vin, const float* cin, int i,
                                              R& vout, float& cout) {
     const R vi = vin[i];
@@ -93,7 +97,7 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
         const int nxy = op.nx * op.ny;
         const int nx = op.nx;
         auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
-        stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
+        stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
     }
 }
 

@@ -18,16 +18,18 @@
 
 namespace daeti {
 
-template <typename R, int DIM, bool KAHAN, bool SYNC>
+template <typename R, int DIM, bool KAHAN, bool SYNC, bool PAD>
 __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const R* __restrict__ vin, R* vout,
                                                      const float* cin, float* cout, SyncParams<R> sp) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     int k = 1;
     if (valid) {
         R v;
         float cc;
-        diffuse_node<R, DIM, KAHAN>(op, vin, cin, i, v, cc);
+        diffuse_node<R, DIM, KAHAN, PAD>(op, vin, cin, i, v, cc);
         vout[i] = v;
         if (KAHAN) cout[i] = cc;
         if (SYNC) k = sync_node(sp, i, v);
@@ -45,6 +47,8 @@ template <typename R, int DIM, bool KAHAN, bool SYNC>
 __global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, int n, int zrun,
                                                                const R* __restrict__ vin, R* vout,
                                                                const float* cin, float* cout, SyncParams<R> sp) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;
     constexpr int NP = DIM == 3 ? 3 : 1;
     __shared__ R buf[NP][PLANE];
@@ -120,16 +124,18 @@ static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef st
     return sp;
 }
 
-template <typename R, int DIM, bool KAHAN>
-static void sub_launch(bool sync, int grid, int block, cudaStream_t st, const OpView<R>& op, int n, const R* vin,
-                       R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
-    if (sync) substep_kernel<R, DIM, KAHAN, true><<<grid, block, 0, st>>>(op, n, vin, vout, cin, cout, sp);
-    else substep_kernel<R, DIM, KAHAN, false><<<grid, block, 0, st>>>(op, n, vin, vout, cin, cout, sp);
+template <typename R, int DIM, bool KAHAN, bool PAD>
+static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl, const OpView<R>& op, int n,
+                       const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
+    if (sync)
+        launch_ex(substep_kernel<R, DIM, KAHAN, true, PAD>, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else
+        launch_ex(substep_kernel<R, DIM, KAHAN, false, PAD>, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
 }
 
 template <typename R, int DIM, bool KAHAN>
-static void tiled_launch(bool sync, cudaStream_t st, const OpView<R>& op, const DiffOp& dop, int n, const R* vin,
-                         R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
+static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
+                         const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
     const int gx = (dop.nx + TX - 1) / TX, gy = (dop.ny + TY - 1) / TY;
     int zrun = 1, gz = 1;
     if (DIM == 3) {
@@ -139,13 +145,17 @@ static void tiled_launch(bool sync, cudaStream_t st, const OpView<R>& op, const 
         gz = (dop.nz + zrun - 1) / zrun;
     }
     const dim3 grid(gx, gy, gz);
-    if (sync) tiled_substep_kernel<R, DIM, KAHAN, true><<<grid, TX * TY, 0, st>>>(op, n, zrun, vin, vout, cin, cout, sp);
-    else tiled_substep_kernel<R, DIM, KAHAN, false><<<grid, TX * TY, 0, st>>>(op, n, zrun, vin, vout, cin, cout, sp);
+    if (sync)
+        launch_ex(tiled_substep_kernel<R, DIM, KAHAN, true>, grid, TX * TY, st, pdl, op, n, zrun, vin, vout, cin, cout,
+                  sp);
+    else
+        launch_ex(tiled_substep_kernel<R, DIM, KAHAN, false>, grid, TX * TY, st, pdl, op, n, zrun, vin, vout, cin,
+                  cout, sp);
 }
 
 template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
-                       StepRef step, bool lists, int block, cudaStream_t st) {
+                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
     if (dop.kind == 0 && block == 0) {
         // structured grid, shared-memory tiles
@@ -154,8 +164,8 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        if (dop.dim == 2) tiled_launch<R, 2, KAHAN>(sync, st, op, dop, (int)s.n, vin, vout, cin, cout, sp);
-        else tiled_launch<R, 3, KAHAN>(sync, st, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        if (dop.dim == 2) tiled_launch<R, 2, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        else tiled_launch<R, 3, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
         return;
     }
     if (block <= 0) block = 256;
@@ -167,19 +177,22 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
     const float* cin = KAHAN ? s.C[src] : nullptr;
     float* cout = KAHAN ? s.C[1 - src] : nullptr;
     const int n = (int)s.n;
-    if (dop.kind == 1) sub_launch<R, 0, KAHAN>(sync, grid, block, st, op, n, vin, vout, cin, cout, sp);
-    else if (dop.dim == 2) sub_launch<R, 2, KAHAN>(sync, grid, block, st, op, n, vin, vout, cin, cout, sp);
-    else sub_launch<R, 3, KAHAN>(sync, grid, block, st, op, n, vin, vout, cin, cout, sp);
+    const bool pad = s.vpad >= stencil_reach(dop);
+    if (dop.kind == 1) sub_launch<R, 0, KAHAN, false>(sync, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else if (dop.dim == 2 && pad) sub_launch<R, 2, KAHAN, true>(sync, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else if (dop.dim == 2) sub_launch<R, 2, KAHAN, false>(sync, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else if (pad) sub_launch<R, 3, KAHAN, true>(sync, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else sub_launch<R, 3, KAHAN, false>(sync, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
 }
 
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st) {
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     if (s.prec == P_F64)
-        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st);
+        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
     else if (s.kahan)
-        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st);
+        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
     else
-        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st);
+        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
 }
 
 // ---------------------------------------------------------- per-k node lists
@@ -196,8 +209,14 @@ void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st) {
     if (grid) rebuild_lists_kernel<<<grid, 256, 0, st>>>((int)s.n, s.kk, s.counts + par * DAETI_MAX_K, s.lists);
 }
 
-__global__ void tick_kernel(long long* ctr, long long inc) { *ctr += inc; }
-__global__ void set_counter_kernel(long long* ctr, long long v) { *ctr = v; }
+__global__ void tick_kernel(long long* ctr, long long inc) {
+    pdl_wait();
+    *ctr += inc;
+}
+__global__ void set_counter_kernel(long long* ctr, long long v) {
+    pdl_wait();
+    *ctr = v;
+}
 
 void launch_tick(long long* ctr, long long inc, cudaStream_t st) { tick_kernel<<<1, 1, 0, st>>>(ctr, inc); }
 void launch_set_counter(long long* ctr, long long value, cudaStream_t st) {

@@ -19,6 +19,7 @@ struct DevState {
     int64_t n = 0;           // nodes
     int n_states = 0;        // including V
     void* V[2] = {nullptr, nullptr};      // ping-pong V
+    int64_t vpad = 0;                     // finite ghost elements before and after each V buffer (stencil reach)
     float* C[2] = {nullptr, nullptr};     // Kahan compensation (nullable)
     void* S = nullptr;                    // other states, state-major, row stride n
     void* vsync = nullptr;                // V at the last synchronisation
@@ -56,6 +57,12 @@ struct DiffOp {
     int64_t nnz_padded = 0;
 };
 
+// Largest |index offset| of a stencil neighbour on a structured grid (0 for SELL-32).
+inline int64_t stencil_reach(const DiffOp& op) {
+    if (op.kind != 0) return 0;
+    return 1 + (int64_t)op.nx + (op.dim == 3 ? (int64_t)op.nx * op.ny : 0);
+}
+
 struct SyncArgs {
     double dt = 0.1;
     double vscale = 1.0;
@@ -69,6 +76,7 @@ struct ReactTuning {
     int block = 128;        // threads per block (<= 128)
     int min_blocks = 8;     // float TP06: resident 128-thread blocks per SM the registers must allow (8 or 10)
     int kmax = 10;
+    int pdl = 1;            // launch the per-step kernels with programmatic dependent launch
 };
 
 // Launchers.  `step` identifies the step whose work is launched.
@@ -80,8 +88,10 @@ void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef s
                      bool fused, const DiffOp& op, const ReactTuning& tune, cudaStream_t st);
 // One diffusion sub-step from V[src] to V[1-src]; with `sync`, the
 // synchronisation epilogue runs on the result (lists of parity `par`).
+// pdl: launch with programmatic dependent launch (the kernels wait for their
+// predecessor before touching memory either way).
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st);
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false);
 void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st);
 void launch_tick(long long* ctr, long long inc, cudaStream_t st);
 void launch_set_counter(long long* ctr, long long value, cudaStream_t st);

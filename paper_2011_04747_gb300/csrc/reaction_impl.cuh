@@ -25,7 +25,7 @@ struct ReactArgs {
     size_t ld;
     const uint8_t* kk;
     const int* lists;    // per-k node lists (list k at lists + k*n), null: node = item
-    const int* counts;   // list lengths of this step A
+    const int* counts;   // list lengths of this step A (counts[k], k >= 1)
     int* counts_next;    // list lengths of the next step A, cleared here
     unsigned long long* substeps;
     int kmax;
@@ -121,74 +121,104 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
     if (KAHAN) a.C[i] = c;
 }
 
-// One item per thread.  Items are taken largest k first (list kmax, ...,
-// list 1), so that every warp but those at the list boundaries runs one
-// uniform sub-step count.  MINB caps registers (minimum resident blocks of
-// 128 threads) to trade spills against occupancy.  DIM >= 0 fuses one
-// diffusion sub-step before the reaction (0: SELL-32, 2/3: stencil).
-template <typename R, int MODEL, bool KAHAN, int MINB, int DIM>
+// Node of item t.  Buckets are laid out largest k first: bucket k holds the
+// items off[k] <= t < off[k-1], with off[k] = sum of the lengths of buckets
+// j > k non-increasing in k and off[j] = 0 for j >= kmax, so k is the
+// smallest j >= 1 with off[j] <= t (branch-free binary search over 1..15).
+__device__ __forceinline__ int item_node(const int* __restrict__ lists, int n, const int* off, int t, int& k) {
+    int lo = 0;   // off[lo] > t holds for lo = 0 (t < total = off[0])
+#pragma unroll
+    for (int step = 8; step >= 1; step >>= 1)
+        if (off[lo + step] > t) lo += step;
+    k = lo + 1;
+    return lists[(size_t)k * n + (t - off[k])];
+}
+
+// One item: the optional fused diffusion sub-step, then step A of node i.
+template <typename R, int MODEL, bool KAHAN, int DIM, bool PAD>
+__device__ __forceinline__ void react_item(const ReactArgs<R>& a, const OpView<R>& op, int i, int k, double tn,
+                                           bool any_stim) {
+    R v0;
+    float c0 = 0.f;
+    if (DIM >= 0) {
+        diffuse_node<R, (DIM < 0 ? 0 : DIM), KAHAN, PAD>(op, a.vsrc, a.csrc, i, v0, c0);
+    } else {
+        v0 = a.V[i];
+        if (KAHAN) c0 = a.C[i];
+    }
+    react_node<R, MODEL, KAHAN>(a, i, k, tn, any_stim, v0, c0);
+}
+
+// Items are the entries of the per-k lists taken largest k first (list
+// kmax, ..., list 1), one per thread, so that every warp but those at list
+// boundaries runs one uniform sub-step count.  Item-warp u goes to warp
+// u / gridDim.x of block u % gridDim.x, so the few heavy (large k) warps at
+// the head of the list land on different SMs instead of a handful of
+// blocks.  MINB caps registers (minimum resident blocks of 128 threads) to
+// trade spills against occupancy.  DIM >= 0 fuses one diffusion sub-step
+// before the reaction (0: SELL-32, 2/3: stencil; PAD: V buffers with a ghost
+// margin, no per-neighbour boundary tests).
+template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD>
 __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpView<R> op) {
     __shared__ int off[DAETI_MAX_K];
-    __shared__ int cnt[DAETI_MAX_K];
     __shared__ double sh_tn;
     __shared__ int sh_stim;
-    // step time and stimulus window once per block (FP64 is slow on this part)
-    if (threadIdx.x == 0) {
+    __shared__ int sh_uni;
+    pdl_wait();
+    pdl_trigger();
+    // Warp 0: step time, stimulus window and list offsets, with the loads of
+    // the step counter, the stimuli and the list lengths in flight together.
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         const double t0 = (double)step_index(a.step) * a.dt;
-        int on = 0;
-        for (int s = 0; s < a.n_stims; ++s) on |= stim_overlaps(a.stims[s], t0, t0 + a.dt) ? 1 : 0;
-        sh_tn = t0;
-        sh_stim = on;
+        const bool on = lane < a.n_stims && stim_overlaps(a.stims[lane], t0, t0 + a.dt);
+        const unsigned any = __ballot_sync(0xffffffffu, on);
+        const int c = (a.lists && lane >= 1 && lane <= a.kmax) ? a.counts[lane] : 0;
+        // inclusive suffix sum of the bucket lengths c over lanes 0..15:
+        // off[k] = sum of c_j, j > k; off[0] = total number of items
+        int sfx = c;
+#pragma unroll
+        for (int d = 1; d < DAETI_MAX_K; d <<= 1) {
+            const int y = __shfl_down_sync(0xffffffffu, sfx, d);
+            if (lane + d < DAETI_MAX_K) sfx += y;
+        }
+        if (lane < DAETI_MAX_K) off[lane] = sfx - c;
+        // the k of a bucket that holds all n nodes, else 0
+        const unsigned full = __ballot_sync(0xffffffffu, c == a.n && c > 0);
+        if (lane == 0) {
+            sh_tn = t0;
+            sh_stim = any != 0u;
+            sh_uni = full ? __ffs(full) - 1 : 0;
+        }
+        if (a.lists && blockIdx.x == 0) {
+            if (lane < DAETI_MAX_K) a.counts_next[lane] = 0;
+            if (a.substeps) {
+                unsigned long long tot = (unsigned long long)lane * (unsigned long long)c;
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+                if (lane == 0) atomicAdd(a.substeps, tot);
+            }
+        }
     }
-    if (threadIdx.x < DAETI_MAX_K)
-        cnt[threadIdx.x] = (a.lists && threadIdx.x >= 1 && threadIdx.x <= a.kmax) ? a.counts[threadIdx.x] : 0;
     __syncthreads();
     const double tn = sh_tn;
     const bool any_stim = sh_stim != 0;
-    int total = a.n;
-    if (a.lists) {
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int k = DAETI_MAX_K - 1; k >= 1; --k) {
-                off[k] = acc;
-                acc += cnt[k];
-            }
-            off[0] = acc;
-        }
-        if (blockIdx.x == 0 && threadIdx.x < DAETI_MAX_K) a.counts_next[threadIdx.x] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 32 && a.substeps) {
-            unsigned long long tot = 0;
-            for (int k = 1; k < DAETI_MAX_K; ++k) tot += (unsigned long long)k * cnt[k];
-            atomicAdd(a.substeps, tot);
-        }
-        __syncthreads();
-        total = off[0];
+    if (!a.lists) {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, a.kk[t], tn, any_stim);
+        return;
     }
-    // Item warps are dealt to blocks round-robin (item warp u = j * gridDim.x +
-    // block, j the warp within the block), so the few heavy (large k) warps at
-    // the head of the list land on different SMs instead of a handful of blocks.
-    const int u = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int t = a.lists ? u * 32 + (threadIdx.x & 31) : blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < total) {
-        int i, k;
-        if (a.lists) {
-            // buckets are laid out largest k first: walk down to the one holding t
-            k = a.kmax;
-            while (k > 1 && t >= off[k] + cnt[k]) --k;
-            i = a.lists[(size_t)k * a.n + (t - off[k])];
-        } else {
-            i = t;
-            k = a.kk[i];
-        }
-        R v0;
-        float c0 = 0.f;
-        if (DIM >= 0) {
-            diffuse_node<R, (DIM < 0 ? 0 : DIM), KAHAN>(op, a.vsrc, a.csrc, i, v0, c0);
-        } else {
-            v0 = a.V[i];
-            if (KAHAN) c0 = a.C[i];
-        }
-        react_node<R, MODEL, KAHAN>(a, i, k, tn, any_stim, v0, c0);
+    const int total = off[0];
+    const int t = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+    if (t >= total) return;
+    if (sh_uni) {
+        // one bucket holds every node (common away from wavefronts): item t is
+        // node t, no list indirection
+        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, sh_uni, tn, any_stim);
+    } else {
+        int k;
+        const int i = item_node(a.lists, a.n, off, t, k);
+        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, i, k, tn, any_stim);
     }
 }
 
@@ -229,14 +259,24 @@ ReactArgs<R> react_args(const DevState& s, const ModelArgs& m, double dt, StepRe
     return a;
 }
 
+template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD = false>
+void launch_react_one(const ReactArgs<R>& a, const OpView<R>& op, int grid, int block, bool pdl, cudaStream_t st) {
+    launch_ex(reaction_kernel<R, MODEL, KAHAN, MINB, DIM, PAD>, grid, block, st, pdl, a, op);
+}
+
 // Launch of one (model, precision, register cap) over the four operator cases.
 template <typename R, int MODEL, bool KAHAN, int MINB>
-void launch_react_dims(const ReactArgs<R>& a, const DiffOp& dop, bool fused, int grid, int block, cudaStream_t st) {
+void launch_react_dims(const ReactArgs<R>& a, const DevState& s, const DiffOp& dop, bool fused, int grid, int block,
+                       const ReactTuning& tune, cudaStream_t st) {
     const OpView<R> op = op_view<R>(dop);
-    if (!fused) reaction_kernel<R, MODEL, KAHAN, MINB, -1><<<grid, block, 0, st>>>(a, op);
-    else if (dop.kind == 1) reaction_kernel<R, MODEL, KAHAN, MINB, 0><<<grid, block, 0, st>>>(a, op);
-    else if (dop.dim == 2) reaction_kernel<R, MODEL, KAHAN, MINB, 2><<<grid, block, 0, st>>>(a, op);
-    else reaction_kernel<R, MODEL, KAHAN, MINB, 3><<<grid, block, 0, st>>>(a, op);
+    const bool pdl = tune.pdl != 0;
+    const bool pad = s.vpad >= stencil_reach(dop);
+    if (!fused) launch_react_one<R, MODEL, KAHAN, MINB, -1>(a, op, grid, block, pdl, st);
+    else if (dop.kind == 1) launch_react_one<R, MODEL, KAHAN, MINB, 0>(a, op, grid, block, pdl, st);
+    else if (dop.dim == 2 && pad) launch_react_one<R, MODEL, KAHAN, MINB, 2, true>(a, op, grid, block, pdl, st);
+    else if (dop.dim == 2) launch_react_one<R, MODEL, KAHAN, MINB, 2>(a, op, grid, block, pdl, st);
+    else if (pad) launch_react_one<R, MODEL, KAHAN, MINB, 3, true>(a, op, grid, block, pdl, st);
+    else launch_react_one<R, MODEL, KAHAN, MINB, 3>(a, op, grid, block, pdl, st);
 }
 
 // Per-TU entry points (explicitly instantiated in reaction_*.cu).

@@ -11,7 +11,7 @@ namespace daeti {
         const int block = react_block(tune);                                                                   \
         const int grid = (int)((s.n + block - 1) / block);                                                     \
         if (grid == 0) return;                                                                                 \
-        launch_react_dims<R, M_MS, K, 1>(a, op, fused, grid, block, st);                                       \
+        launch_react_dims<R, M_MS, K, 1>(a, s, op, fused, grid, block, tune, st);                                       \
     }
 
 DAETI_MS_LAUNCH(float, true)

@@ -10,8 +10,8 @@ void launch_tp06<float, false>(const DevState& s, const ModelArgs& m, double dt,
     const int block = react_block(tune);
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
-    if (tune.min_blocks >= 10) launch_react_dims<float, M_TP06, false, 10>(a, op, fused, grid, block, st);
-    else launch_react_dims<float, M_TP06, false, 8>(a, op, fused, grid, block, st);
+    if (tune.min_blocks >= 10) launch_react_dims<float, M_TP06, false, 10>(a, s, op, fused, grid, block, tune, st);
+    else launch_react_dims<float, M_TP06, false, 8>(a, s, op, fused, grid, block, tune, st);
 }
 
 }  // namespace daeti

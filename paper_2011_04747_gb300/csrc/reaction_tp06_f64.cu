@@ -10,7 +10,7 @@ void launch_tp06<double, false>(const DevState& s, const ModelArgs& m, double dt
     const int block = react_block(tune);
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
-    launch_react_dims<double, M_TP06, false, 1>(a, op, fused, grid, block, st);
+    launch_react_dims<double, M_TP06, false, 1>(a, s, op, fused, grid, block, tune, st);
 }
 
 }  // namespace daeti

@@ -11,8 +11,8 @@ from parity_util import ensure_lib, gpu_available
 
 def test_candidate_grid():
     c = autotune.candidates()
-    assert len(c) == 64
-    assert len({json.dumps(x, sort_keys=True) for x in c}) == 64
+    assert len(c) == 128
+    assert len({json.dumps(x, sort_keys=True) for x in c}) == 128
     assert autotune.candidates({"react_block": (32,), "bucket_k": (0, 1)}) == [
         {"bucket_k": 0, "react_block": 32}, {"bucket_k": 1, "react_block": 32}]
 
@@ -36,9 +36,9 @@ def test_autotune_preserves_results_and_caches(tmp_path):
     binding = ensure_lib()
     wl = I.tp06_slab_3d(31, 29, 9)
     s = binding.solver_from_workload(wl)
-    space = {"react_block": (64, 128), "fuse_diffusion": (1, 0), "bucket_k": (1, 0)}
+    space = {"react_block": (64, 128), "fuse_diffusion": (1, 0), "bucket_k": (1, 0), "pdl": (1, 0)}
     rep = autotune.autotune(s, sim_ms=5.0, space=space, cache_path=str(tmp_path / "t.json"))
-    assert not rep["cached"] and rep["rejected"] == 0 and rep["candidates"] == 8
+    assert not rep["cached"] and rep["rejected"] == 0 and rep["candidates"] == 16
     s.daeti_advance(10.0)
     v = s.daeti_read_v()
     s.close()

@@ -178,8 +178,9 @@ def test_full_slab_bench_config_first_steps(precision):
 
 @pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3"])
 def test_launch_shapes_do_not_change_results(wl_name):
-    """Fused or separate diffusion sub-step, register caps, block sizes, k lists and graphs
-    give bit-identical states."""
+    """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
+    programmatic dependent launch or plain launches, and graphs give
+    bit-identical states."""
     from parity_util import ensure_lib
 
     binding = ensure_lib()
@@ -189,6 +190,8 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 dict(fuse_diffusion=0),
                 dict(react_min_blocks=10),
                 dict(react_min_blocks=10, react_block=64, fuse_diffusion=0),
+                dict(pdl=0),
+                dict(pdl=0, react_block=64, graph_steps=0),
                 dict(bucket_k=0, graph_steps=0),
                 dict(graph_steps=6, diff_block=128)]
     ref = None
