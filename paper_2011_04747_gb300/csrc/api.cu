@@ -639,7 +639,7 @@ int daeti_prepare(daeti_ctx* c) {
         if ((rc = dalloc(c, &p, 4 * N))) return rc;
         c->s.C[1] = (float*)p;
     }
-    if ((rc = dalloc(c, &c->s.S, R * N * (c->s.n_states - 1)))) return rc;
+    if ((rc = dalloc(c, &c->s.S, R * state_elems(N, c->s.n_states - 1)))) return rc;
     if ((rc = dalloc(c, &c->s.vsync, R * N)) || (rc = dalloc(c, &c->s.act, R * N))) return rc;
     if ((rc = dalloc(c, &p, N))) return rc;
     c->s.kk = (uint8_t*)p;
@@ -761,7 +761,14 @@ int daeti_init_state(daeti_ctx* c, const double* state) {
     int rc;
     if ((rc = upload_real(c, c->s.V[0], state, N))) return rc;
     if ((rc = upload_real(c, c->s.vsync, state, N))) return rc;
-    if ((rc = upload_real(c, c->s.S, state + N, (int64_t)(ns - 1) * N))) return rc;
+    {
+        // cell states in chunks of 32 nodes (state_index); lanes past N hold 0
+        const int nsx = ns - 1;
+        std::vector<double> chunked(state_elems(N, nsx), 0.0);
+        for (int k = 0; k < nsx; ++k)
+            for (int64_t i = 0; i < N; ++i) chunked[state_index(i, k, nsx)] = state[(size_t)(k + 1) * N + i];
+        if ((rc = upload_real(c, c->s.S, chunked.data(), (int64_t)chunked.size()))) return rc;
+    }
     if (c->s.kahan) {
         CK(set_(c, c->s.C[0], 0, 4 * N));
         CK(set_(c, c->s.C[1], 0, 4 * N));
@@ -863,8 +870,7 @@ int daeti_read_state(daeti_ctx* c, double* out) {
     int rc = daeti_read_v(c, out, DAETI_DTYPE_F64, 0);
     if (rc) return rc;
     for (int k = 1; k < c->s.n_states; ++k) {
-        const char* src = (const char*)c->s.S + (size_t)(k - 1) * N * rsize(c);
-        launch_convert(src, c->s.prec, nullptr, c->scratch, 0, N, c->stream);
+        launch_gather_state(c->s.S, c->s.prec, c->s.n_states - 1, k - 1, (double*)c->scratch, N, c->stream);
         CK(cudaMemcpyAsync(out + (size_t)k * N, c->scratch, 8 * N, cudaMemcpyDeviceToHost, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -877,7 +883,7 @@ static int64_t ckpt_bytes(const daeti_ctx* c) {
     const int64_t R = (int64_t)rsize(c);
     int64_t b = 64 + R * N;
     if (c->s.kahan) b += 4 * N;
-    b += R * N * (c->s.n_states - 1) + 2 * R * N + N + 4 * 2 * DAETI_MAX_K;
+    b += R * state_elems(N, c->s.n_states - 1) + 2 * R * N + N + 4 * 2 * DAETI_MAX_K;
     return b;
 }
 
@@ -904,8 +910,8 @@ int daeti_save_state(daeti_ctx* c, void* buf, int64_t buf_bytes) {
         CK(cpy_(c, p, c->s.C[c->cur], 4 * N, cudaMemcpyDeviceToHost));
         p += 4 * N;
     }
-    CK(cpy_(c, p, c->s.S, R * N * (c->s.n_states - 1), cudaMemcpyDeviceToHost));
-    p += R * N * (c->s.n_states - 1);
+    CK(cpy_(c, p, c->s.S, R * state_elems(N, c->s.n_states - 1), cudaMemcpyDeviceToHost));
+    p += R * state_elems(N, c->s.n_states - 1);
     CK(cpy_(c, p, c->s.vsync, R * N, cudaMemcpyDeviceToHost));
     p += R * N;
     CK(cpy_(c, p, c->s.act, R * N, cudaMemcpyDeviceToHost));
@@ -936,8 +942,8 @@ int daeti_load_state(daeti_ctx* c, const void* buf, int64_t buf_bytes) {
         CK(cpy_(c, c->s.C[0], p, 4 * N, cudaMemcpyHostToDevice));
         p += 4 * N;
     }
-    CK(cpy_(c, c->s.S, p, R * N * (c->s.n_states - 1), cudaMemcpyHostToDevice));
-    p += R * N * (c->s.n_states - 1);
+    CK(cpy_(c, c->s.S, p, R * state_elems(N, c->s.n_states - 1), cudaMemcpyHostToDevice));
+    p += R * state_elems(N, c->s.n_states - 1);
     CK(cpy_(c, c->s.vsync, p, R * N, cudaMemcpyHostToDevice));
     p += R * N;
     CK(cpy_(c, c->s.act, p, R * N, cudaMemcpyHostToDevice));

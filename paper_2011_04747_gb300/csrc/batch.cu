@@ -416,7 +416,7 @@ int daeti_batch_prepare(daeti_batch* b) {
     if ((rc = balloc(b, &p, 8))) return rc;
     s.step_ctr = (long long*)p;
     if ((rc = balloc(b, &b->S_ms, R * std::max<int64_t>(1, b->n_ms)))) return rc;
-    if ((rc = balloc(b, &b->S_tp, R * 18 * std::max<int64_t>(1, b->n_tp)))) return rc;
+    if ((rc = balloc(b, &b->S_tp, R * state_elems(std::max<int64_t>(1, b->n_tp), 18)))) return rc;
     if (!sd.empty()) {
         if ((rc = balloc(b, &p, 4 * N))) return rc;
         s.stim_mask = (unsigned*)p;
@@ -454,13 +454,14 @@ int daeti_batch_prepare(daeti_batch* b) {
     b->rtune.kmax = b->kmax;
     b->prepared = true;
     // initial state: published defaults
-    std::vector<double> v(N), h_ms(std::max<int64_t>(1, b->n_ms), 1.0), tp(18 * std::max<int64_t>(1, b->n_tp));
+    std::vector<double> v(N), h_ms(std::max<int64_t>(1, b->n_ms), 1.0),
+        tp(state_elems(std::max<int64_t>(1, b->n_tp), 18));
     for (int64_t i = 0; i < N; ++i) v[i] = i < b->n_ms ? 0.0 : TP06_INIT[0];
-    for (int k = 0; k < 18; ++k)
-        std::fill(tp.begin() + (size_t)k * b->n_tp, tp.begin() + (size_t)(k + 1) * b->n_tp, TP06_INIT[k + 1]);
+    // TP06 cell states in chunks of 32 pool nodes (state_index)
+    for (size_t q = 0; q < tp.size(); ++q) tp[q] = TP06_INIT[1 + (q / 32) % 18];
     if ((rc = bupload(b, s.V[0], v.data(), N)) || (rc = bupload(b, s.vsync, v.data(), N))) return rc;
     if (b->n_ms && (rc = bupload(b, b->S_ms, h_ms.data(), b->n_ms))) return rc;
-    if (b->n_tp && (rc = bupload(b, b->S_tp, tp.data(), 18 * b->n_tp))) return rc;
+    if (b->n_tp && (rc = bupload(b, b->S_tp, tp.data(), (int64_t)tp.size()))) return rc;
     std::vector<double> neg(N, -1.0);
     if ((rc = bupload(b, s.act, neg.data(), N))) return rc;
     if (s.kahan) {

@@ -203,4 +203,19 @@ void launch_convert(const void* src, int src_prec, const float* comp, void* dst,
     }
 }
 
+// dst[i] = state s of node i from the chunked state array (state_index), as double.
+template <typename S>
+__global__ void gather_state_kernel(const S* __restrict__ src, int ns, int s, double* __restrict__ dst, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dst[i] = (double)src[((i >> 5) * ns + s) * 32 + (i & 31)];
+}
+
+void launch_gather_state(const void* src, int src_prec, int ns, int s, double* dst, int64_t n, cudaStream_t st) {
+    const int grid = (int)((n + 255) / 256);
+    if (!grid) return;
+    if (src_prec == P_F64) gather_state_kernel<double><<<grid, 256, 0, st>>>((const double*)src, ns, s, dst, n);
+    else gather_state_kernel<float><<<grid, 256, 0, st>>>((const float*)src, ns, s, dst, n);
+}
+
 }  // namespace daeti

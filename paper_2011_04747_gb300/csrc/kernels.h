@@ -21,7 +21,7 @@ struct DevState {
     void* V[2] = {nullptr, nullptr};      // ping-pong V
     int64_t vpad = 0;                     // finite ghost elements before and after each V buffer (stencil reach)
     float* C[2] = {nullptr, nullptr};     // Kahan compensation (nullable)
-    void* S = nullptr;                    // other states, state-major, row stride n
+    void* S = nullptr;                    // other states, in chunks of 32 nodes (state_index)
     void* vsync = nullptr;                // V at the last synchronisation
     uint8_t* kk = nullptr;                // sub-step count of the next step A
     void* act = nullptr;                  // activation times
@@ -56,6 +56,14 @@ struct DiffOp {
     void* val = nullptr;            // off-diagonal dt_ad K_ij / m_i
     int64_t nnz_padded = 0;
 };
+
+// Cell states other than V are stored in chunks of 32 nodes: state s (of ns)
+// of node i sits at ((i / 32) * ns + s) * 32 + i % 32.  A thread's states are
+// then fixed offsets from one base address, and a warp of consecutive nodes
+// reads 128 contiguous bytes per state.  With ns = 1 this is the plain array.
+inline int64_t state_chunks(int64_t n) { return (n + 31) / 32; }
+inline int64_t state_elems(int64_t n, int ns) { return state_chunks(n) * 32 * ns; }
+inline int64_t state_index(int64_t i, int s, int ns) { return ((i >> 5) * ns + s) * 32 + (i & 31); }
 
 // Largest |index offset| of a stencil neighbour on a structured grid (0 for SELL-32).
 inline int64_t stencil_reach(const DiffOp& op) {
@@ -121,4 +129,6 @@ void launch_node_mass(const EstOp& op, double* m_out, cudaStream_t st);
 // Conversions between the state precision and the caller's dtype.
 void launch_convert(const void* src, int src_prec, const float* comp, void* dst, int dst_f32,
                     int64_t n, cudaStream_t st);
+// State s of every node from the chunked state array, as double.
+void launch_gather_state(const void* src, int src_prec, int ns, int s, double* dst, int64_t n, cudaStream_t st);
 }  // namespace daeti

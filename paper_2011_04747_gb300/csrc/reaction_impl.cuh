@@ -21,8 +21,7 @@ struct ReactArgs {
     float* C;            // Kahan compensation or null
     const R* vsrc;       // fused diffusion: V before the sub-step (other buffer)
     const float* csrc;
-    R* S;                // states 1.. (state-major, stride ld)
-    size_t ld;
+    R* S;                // states 1.. in chunks of 32 nodes: state s of node i at ((i/32)*ns + s)*32 + i%32
     const uint8_t* kk;
     const int* lists;    // per-k node lists (list k at lists + k*n), null: node = item
     const int* counts;   // list lengths of this step A (counts[k], k >= 1)
@@ -61,7 +60,6 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
     const R h = a.dtkr[k];
     float c = c0;
     float* cp = KAHAN ? &c : nullptr;
-    const size_t ld = a.ld;
     if (MODEL == M_MS) {
         R v = v0;
         R g = a.S[i];
@@ -72,51 +70,51 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
         a.V[i] = v;
         a.S[i] = g;
     } else {
+        // the node's 18 cell states in its chunk of 32 nodes: base + 32 s
         TP06State<R> x;
-        const R* S = a.S;
+        R* const S = a.S + (size_t)(i >> 5) * (18 * 32) + (i & 31);
         x.V = v0;
-        x.Cai = S[0 * ld + i];
-        x.CaSR = S[1 * ld + i];
-        x.CaSS = S[2 * ld + i];
-        x.Nai = S[3 * ld + i];
-        x.Ki = S[4 * ld + i];
-        x.m = S[5 * ld + i];
-        x.h = S[6 * ld + i];
-        x.j = S[7 * ld + i];
-        x.xr1 = S[8 * ld + i];
-        x.xr2 = S[9 * ld + i];
-        x.xs = S[10 * ld + i];
-        x.r = S[11 * ld + i];
-        x.s = S[12 * ld + i];
-        x.d = S[13 * ld + i];
-        x.f = S[14 * ld + i];
-        x.f2 = S[15 * ld + i];
-        x.fcass = S[16 * ld + i];
-        x.RR = S[17 * ld + i];
+        x.Cai = S[0 * 32];
+        x.CaSR = S[1 * 32];
+        x.CaSS = S[2 * 32];
+        x.Nai = S[3 * 32];
+        x.Ki = S[4 * 32];
+        x.m = S[5 * 32];
+        x.h = S[6 * 32];
+        x.j = S[7 * 32];
+        x.xr1 = S[8 * 32];
+        x.xr2 = S[9 * 32];
+        x.xs = S[10 * 32];
+        x.r = S[11 * 32];
+        x.s = S[12 * 32];
+        x.d = S[13 * 32];
+        x.f = S[14 * 32];
+        x.f2 = S[15 * 32];
+        x.fcass = S[16 * 32];
+        x.RR = S[17 * 32];
         for (int s = 0; s < k; ++s) {
             R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
             tp06_substep(x, cp, h, J, a.tp);
         }
-        R* W = a.S;
         a.V[i] = x.V;
-        W[0 * ld + i] = x.Cai;
-        W[1 * ld + i] = x.CaSR;
-        W[2 * ld + i] = x.CaSS;
-        W[3 * ld + i] = x.Nai;
-        W[4 * ld + i] = x.Ki;
-        W[5 * ld + i] = x.m;
-        W[6 * ld + i] = x.h;
-        W[7 * ld + i] = x.j;
-        W[8 * ld + i] = x.xr1;
-        W[9 * ld + i] = x.xr2;
-        W[10 * ld + i] = x.xs;
-        W[11 * ld + i] = x.r;
-        W[12 * ld + i] = x.s;
-        W[13 * ld + i] = x.d;
-        W[14 * ld + i] = x.f;
-        W[15 * ld + i] = x.f2;
-        W[16 * ld + i] = x.fcass;
-        W[17 * ld + i] = x.RR;
+        S[0 * 32] = x.Cai;
+        S[1 * 32] = x.CaSR;
+        S[2 * 32] = x.CaSS;
+        S[3 * 32] = x.Nai;
+        S[4 * 32] = x.Ki;
+        S[5 * 32] = x.m;
+        S[6 * 32] = x.h;
+        S[7 * 32] = x.j;
+        S[8 * 32] = x.xr1;
+        S[9 * 32] = x.xr2;
+        S[10 * 32] = x.xs;
+        S[11 * 32] = x.r;
+        S[12 * 32] = x.s;
+        S[13 * 32] = x.d;
+        S[14 * 32] = x.f;
+        S[15 * 32] = x.f2;
+        S[16 * 32] = x.fcass;
+        S[17 * 32] = x.RR;
     }
     if (KAHAN) a.C[i] = c;
 }
@@ -233,7 +231,6 @@ ReactArgs<R> react_args(const DevState& s, const ModelArgs& m, double dt, StepRe
     a.vsrc = (const R*)s.V[src];
     a.csrc = KAHAN ? s.C[src] : nullptr;
     a.S = (R*)s.S;
-    a.ld = (size_t)s.n;
     a.kk = s.kk;
     a.lists = lists ? s.lists : nullptr;
     a.counts = s.counts + par * DAETI_MAX_K;
