@@ -182,18 +182,12 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     const R dNai = -(INa + IbNa + (R)3 * INaK + (R)3 * INaCa) * (R)(C::Cm / (C::Vc * C::F_));
     const R dKi = -(IK1 + Ito + IKr + IKs - (R)2 * INaK + IpK - J) * (R)(C::Cm / (C::Vc * C::F_));
 
-    // gates at the start-of-sub-step V
+    // Gates at the start-of-sub-step V.  Exponentials with a common slope,
+    // exp(s V + b) = e^b exp(s V), share one SFU evaluation of exp(s V): the
+    // slopes 0.1, -0.1, 0.2, 0.05, -0.05, 1/7 and -1/6 per mV (gates ordered
+    // so that few of these are live at once).
     const int rl = prm.gate_rl;
-    {
-        // m: tau = a b, a = 1/(1+ea), b = 0.1/(1+eb) + 0.1/(1+ec)
-        const R e_inf = one + EXL(V, -1.0 / 9.03, -56.86 / 9.03);
-        const R minf = M::dv(one, e_inf * e_inf);
-        const R ea = one + EXL(V, -0.2, -12.0);
-        const R eb = one + EXL(V, 0.2, 7.0);
-        const R ec = one + EXL(V, 0.005, -0.25);
-        const R rate = M::dv(ea * eb * ec, (R)0.1 * (eb + ec));
-        x.m = gate_rate(x.m, minf, rate, dt, ndtl, rl);
-    }
+    const R iE1 = EXL(V, -0.1, 0.0);   // e^{-0.1 V}
     {
         const R eh = one + EXL(V, 1.0 / 7.43, 71.55 / 7.43);
         const R hinf = M::dv(one, eh * eh);
@@ -201,7 +195,7 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         if (V >= (R)-40) {
             // a_h = a_j = 0
             rh = M::dv((R)(0.77 / 0.13), one + EXL(V, -1.0 / 11.1, -10.66 / 11.1));
-            rj = M::dv(EXL(V, 0.057, -0.5108256237659907), one + EXL(V, -0.1, -3.2));   // ln 0.6
+            rj = M::dv(EXL(V, 0.057, -0.5108256237659907), fma((R)0.04076220397836621, iE1, one));   // ln 0.6; e^{-3.2}
         } else {
             rh = EXL(V, -1.0 / 6.8, -80.0 / 6.8 - 2.864704011147587) +   // ln 0.057
                  EXL(V, 0.079, 0.9932517730102834) +                  // ln 2.7
@@ -216,69 +210,86 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         x.h = gate_rate(x.h, hinf, rh, dt, ndtl, rl);
         x.j = gate_rate(x.j, hinf, rj, dt, ndtl, rl);
     }
+    const R E7 = EXL(V, 1.0 / 7.0, 0.0);   // e^{V/7}
     {
-        // xr1: tau = 450/(1+e1) * 6/(1+e2)
-        const R inf = M::dv(one, one + EXL(V, -1.0 / 7.0, -26.0 / 7.0));
-        const R rate = (one + EXL(V, -0.1, -4.5)) * fma(EXL(V, 1.0 / 11.5, 30.0 / 11.5), (R)(1.0 / 2700.0), (R)(1.0 / 2700.0));
+        // xr1: g_inf = 1/(1 + e^{-26/7} / E7) = E7 / (E7 + e^{-26/7}); tau = 450/(1+e1) * 6/(1+e2)
+        const R inf = M::dv(E7, E7 + (R)0.0243728440732796);
+        const R rate = fma((R)0.011108996538242306, iE1, one) *                       // e^{-4.5}
+                       fma(EXL(V, 1.0 / 11.5, 30.0 / 11.5), (R)(1.0 / 2700.0), (R)(1.0 / 2700.0));
         x.xr1 = gate_rate(x.xr1, inf, rate, dt, ndtl, rl);
     }
     {
-        // xr2: tau = 3/(1+e1) * 1.12/(1+e2)
-        const R inf = M::dv(one, one + EXL(V, 1.0 / 24.0, 88.0 / 24.0));
-        const R rate = (one + EXL(V, -0.05, -3.0)) * fma(EXL(V, 0.05, -3.0), (R)(1.0 / 3.36), (R)(1.0 / 3.36));
-        x.xr2 = gate_rate(x.xr2, inf, rate, dt, ndtl, rl);
+        // f: tau = 1102.5 e + 200/f1 + 180/f2 + 20 ; f2: tau = 562 e' + 31/f1' + 80/f2
+        const R E1 = EXL(V, 0.1, 0.0);   // e^{0.1 V}
+        const R inf = M::dv(one, fma((R)17.41170806332765, E7, one));                 // e^{20/7}
+        const R v27 = V + (R)27;
+        const R f1 = fma((R)3.6692966676192444, iE1, one);                            // e^{1.3}
+        const R f2 = fma((R)20.085536923187668, E1, one);                             // e^{3}
+        const R tnum = fma((EXQ(v27, -1.0 / 225.0, 7.005335607321001) + (R)20) * f1, f2,   // ln 1102.5
+                           fma((R)200, f2, (R)180 * f1));
+        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, ndtl, rl);
+        const R inf2 = M::dv((R)0.67, fma((R)148.4131591025766, E7, one)) + (R)0.33;   // e^{5}
+        const R g1 = fma((R)12.182493960703473, iE1, one);                            // e^{2.5}
+        const R tnum2 = fma(EXQ(v27, -1.0 / 240.0, 6.331501849893691) * g1, f2,   // ln 562
+                            fma((R)31, f2, (R)80 * g1));
+        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, ndtl, rl);
     }
+    const R E2 = EXL(V, 0.2, 0.0);   // e^{0.2 V}
     {
-        // xs: tau = 1400/sqrt(1+e1) / (1+e2) + 80
-        const R inf = M::dv(one, one + EXL(V, -1.0 / 14.0, -5.0 / 14.0));
-        const R d2 = one + EXL(V, 1.0 / 15.0, -35.0 / 15.0);
-        const R rate = M::dv(d2, fma((R)1400, M::rsq(one + EXL(V, -1.0 / 6.0, 5.0 / 6.0)), (R)80 * d2));
-        x.xs = gate_rate(x.xs, inf, rate, dt, ndtl, rl);
-    }
-    {
-        const R inf = M::dv(one, one + EXL(V, -1.0 / 6.0, 20.0 / 6.0));
-        const R v40 = V + (R)40;
-        const R rate = M::dv(one, EXQ(v40, -1.0 / 1800.0, 2.2512917986064953) + (R)0.8);   // ln 9.5
-        x.r = gate_rate(x.r, inf, rate, dt, ndtl, rl);
+        // m: tau = a b, a = 1/(1+ea), b = 0.1/(1+eb) + 0.1/(1+ec)
+        const R e_inf = one + EXL(V, -1.0 / 9.03, -56.86 / 9.03);
+        const R minf = M::dv(one, e_inf * e_inf);
+        const R ea = one + EXL(V, -0.2, -12.0);
+        const R eb = fma((R)1096.6331584284585, E2, one);                             // e^{7}
+        const R ec = one + EXL(V, 0.005, -0.25);
+        const R rate = M::dv(ea * eb * ec, (R)0.1 * (eb + ec));
+        x.m = gate_rate(x.m, minf, rate, dt, ndtl, rl);
     }
     {
         R inf, rate;
         if (prm.celltype == 0) {
-            inf = M::dv(one, one + EXL(V, 0.2, 5.6));
+            inf = M::dv(one, fma((R)270.42640742615254, E2, one));                    // e^{5.6}
             const R v67 = V + (R)67;
             rate = M::dv(one, EXQ(v67, -0.001, 6.907755278982137) + (R)8);   // ln 1000
         } else {
-            inf = M::dv(one, one + EXL(V, 0.2, 4.0));
+            inf = M::dv(one, fma((R)54.598150033144236, E2, one));                    // e^{4}
             const R v45 = V + (R)45;
-            const R dd = one + EXL(V, 0.2, -4.0);
+            const R dd = fma((R)0.01831563888873418, E2, one);                        // e^{-4}
             // tau = 85 e + 5/dd + 3
             rate = M::dv(dd, fma(EXQ(v45, -1.0 / 320.0, 4.442651256490317) + (R)3, dd, (R)5));   // ln 85
         }
         x.s = gate_rate(x.s, inf, rate, dt, ndtl, rl);
     }
+    const R iE05 = EXL(V, -0.05, 0.0);   // e^{-0.05 V}
     {
         // d: tau = (1.4/d1 + 0.25) (1.4/d2) + 1/d3
         const R inf = M::dv(one, one + EXL(V, -1.0 / 7.5, -8.0 / 7.5));
         const R d1 = one + EXL(V, -1.0 / 13.0, -35.0 / 13.0);
-        const R d2 = one + EXL(V, 0.2, 1.0);
-        const R d3 = one + EXL(V, -0.05, 2.5);
+        const R d2 = fma((R)2.718281828459045, E2, one);                              // e^{1}
+        const R d3 = fma((R)12.182493960703473, iE05, one);                           // e^{2.5}
         const R rate = M::dv(d1 * d2 * d3, fma(fma((R)0.35, d1, (R)1.96), d3, d1 * d2));
         x.d = gate_rate(x.d, inf, rate, dt, ndtl, rl);
     }
     {
-        // f: tau = 1102.5 e + 200/f1 + 180/f2 + 20 ; f2: tau = 562 e' + 31/f1' + 80/f2
-        const R inf = M::dv(one, one + EXL(V, 1.0 / 7.0, 20.0 / 7.0));
-        const R v27 = V + (R)27;
-        const R f1 = one + EXL(V, -0.1, 1.3);
-        const R f2 = one + EXL(V, 0.1, 3.0);
-        const R tnum = fma((EXQ(v27, -1.0 / 225.0, 7.005335607321001) + (R)20) * f1, f2,   // ln 1102.5
-                           fma((R)200, f2, (R)180 * f1));
-        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, ndtl, rl);
-        const R inf2 = M::dv((R)0.67, one + EXL(V, 1.0 / 7.0, 5.0)) + (R)0.33;
-        const R g1 = one + EXL(V, -0.1, 2.5);
-        const R tnum2 = fma(EXQ(v27, -1.0 / 240.0, 6.331501849893691) * g1, f2,   // ln 562
-                            fma((R)31, f2, (R)80 * g1));
-        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, ndtl, rl);
+        // xr2: tau = 3/(1+e1) * 1.12/(1+e2)
+        const R inf = M::dv(one, one + EXL(V, 1.0 / 24.0, 88.0 / 24.0));
+        const R rate = fma((R)0.049787068367863944, iE05, one) *                      // e^{-3}
+                       fma(EXL(V, 0.05, -3.0), (R)(1.0 / 3.36), (R)(1.0 / 3.36));
+        x.xr2 = gate_rate(x.xr2, inf, rate, dt, ndtl, rl);
+    }
+    const R iE6 = EXL(V, -1.0 / 6.0, 0.0);   // e^{-V/6}
+    {
+        // xs: tau = 1400/sqrt(1+e1) / (1+e2) + 80
+        const R inf = M::dv(one, one + EXL(V, -1.0 / 14.0, -5.0 / 14.0));
+        const R d2 = one + EXL(V, 1.0 / 15.0, -35.0 / 15.0);
+        const R rate = M::dv(d2, fma((R)1400, M::rsq(fma((R)2.300975890892825, iE6, one)), (R)80 * d2));   // e^{5/6}
+        x.xs = gate_rate(x.xs, inf, rate, dt, ndtl, rl);
+    }
+    {
+        const R inf = M::dv(one, fma((R)28.03162489452614, iE6, one));                // e^{20/6}
+        const R v40 = V + (R)40;
+        const R rate = M::dv(one, EXQ(v40, -1.0 / 1800.0, 2.2512917986064953) + (R)0.8);   // ln 9.5
+        x.r = gate_rate(x.r, inf, rate, dt, ndtl, rl);
     }
     {
         // fCass: inf = 0.6/den + 0.4, tau = 80/den + 2, den = 1 + (CaSS/0.05)^2
