@@ -201,7 +201,7 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
 
 /* Launch shapes (set by the caller or an autotuner; results do not depend on
  * them).  react_block: threads per reaction block (32..128, multiple of 32);
- * react_min_blocks: 8 or 10 resident reaction blocks per SM the register
+ * react_min_blocks: 6, 8 or 10 resident reaction blocks per SM the register
  * budget must allow (TP06 in float); diff_block: threads per block of the
  * one-thread-per-node diffusion kernel (32..256, multiple of 32; default
  * 256), or 0 for the shared-memory tiled kernel on structured grids;

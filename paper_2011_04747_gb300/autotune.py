@@ -21,7 +21,7 @@ import numpy as np
 
 DEFAULT_SPACE = {
     "react_block": (64, 128),
-    "react_min_blocks": (8, 10),
+    "react_min_blocks": (6, 8, 10),
     "fuse_diffusion": (1, 0),
     "bucket_k": (1, 0),
     "diff_block": (0, 256),

@@ -56,7 +56,7 @@ struct TP06Consts {
 
 struct TP06Params {
     int celltype;  // 0 endo, 1 epi, 2 mid
-    int gate_rl;   // 1 Rush-Larsen, 0 forward Euler gates
+    int gate_rl;   // 1 Rush-Larsen, 0 forward Euler gates (selects the RL instance of tp06_substep)
 };
 
 template <typename R>
@@ -67,10 +67,10 @@ struct TP06State {
 // Gate update toward g_inf with rate 1/tau over dt: Rush-Larsen
 // g_inf + (g - g_inf) e^{-dt rate}, the exponential taken as 2^{ndtl rate}
 // with ndtl = -dt log2(e); or forward Euler.
-template <typename R>
-__device__ __forceinline__ R gate_rate(R g, R ginf, R rate, R dt, R ndtl, int rl) {
+template <bool RL, typename R>
+__device__ __forceinline__ R gate_rate(R g, R ginf, R rate, R dt, R ndtl) {
     typedef Fm<R> M;
-    if (rl) return fma(g - ginf, M::ex2(ndtl * rate), ginf);
+    if (RL) return fma(g - ginf, M::ex2(ndtl * rate), ginf);
     return fma(dt * rate, ginf - g, g);
 }
 
@@ -99,7 +99,7 @@ __device__ __forceinline__ double x_over_expm1<double>(double x, double e) {
 // Every exponential exp(a V + b) (and c exp(a V) as exp(a V + ln c)) is
 // written as 2^(a' V + b') with the constants scaled by log2(e) at compile
 // time, one FMA and one SFU operation each.
-template <typename R>
+template <typename R, bool RL = true>
 __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
     typedef TP06Consts C;
     typedef Fm<R> M;
@@ -186,7 +186,6 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     // exp(s V + b) = e^b exp(s V), share one SFU evaluation of exp(s V): the
     // slopes 0.1, -0.1, 0.2, 0.05, -0.05, 1/7 and -1/6 per mV (gates ordered
     // so that few of these are live at once).
-    const int rl = prm.gate_rl;
     const R iE1 = EXL(V, -0.1, 0.0);   // e^{-0.1 V}
     {
         const R eh = one + EXL(V, 1.0 / 7.43, 71.55 / 7.43);
@@ -207,8 +206,8 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
             const R nb = EXL(V, -0.01052, -3.719751117781023);   // ln 0.02424
             rj = M::dv(fma(na, db, nb * da), da * db);
         }
-        x.h = gate_rate(x.h, hinf, rh, dt, ndtl, rl);
-        x.j = gate_rate(x.j, hinf, rj, dt, ndtl, rl);
+        x.h = gate_rate<RL>(x.h, hinf, rh, dt, ndtl);
+        x.j = gate_rate<RL>(x.j, hinf, rj, dt, ndtl);
     }
     const R E7 = EXL(V, 1.0 / 7.0, 0.0);   // e^{V/7}
     {
@@ -216,7 +215,7 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         const R inf = M::dv(E7, E7 + (R)0.0243728440732796);
         const R rate = fma((R)0.011108996538242306, iE1, one) *                       // e^{-4.5}
                        fma(EXL(V, 1.0 / 11.5, 30.0 / 11.5), (R)(1.0 / 2700.0), (R)(1.0 / 2700.0));
-        x.xr1 = gate_rate(x.xr1, inf, rate, dt, ndtl, rl);
+        x.xr1 = gate_rate<RL>(x.xr1, inf, rate, dt, ndtl);
     }
     {
         // f: tau = 1102.5 e + 200/f1 + 180/f2 + 20 ; f2: tau = 562 e' + 31/f1' + 80/f2
@@ -227,12 +226,12 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         const R f2 = fma((R)20.085536923187668, E1, one);                             // e^{3}
         const R tnum = fma((EXQ(v27, -1.0 / 225.0, 7.005335607321001) + (R)20) * f1, f2,   // ln 1102.5
                            fma((R)200, f2, (R)180 * f1));
-        x.f = gate_rate(x.f, inf, M::dv(f1 * f2, tnum), dt, ndtl, rl);
+        x.f = gate_rate<RL>(x.f, inf, M::dv(f1 * f2, tnum), dt, ndtl);
         const R inf2 = M::dv((R)0.67, fma((R)148.4131591025766, E7, one)) + (R)0.33;   // e^{5}
         const R g1 = fma((R)12.182493960703473, iE1, one);                            // e^{2.5}
         const R tnum2 = fma(EXQ(v27, -1.0 / 240.0, 6.331501849893691) * g1, f2,   // ln 562
                             fma((R)31, f2, (R)80 * g1));
-        x.f2 = gate_rate(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, ndtl, rl);
+        x.f2 = gate_rate<RL>(x.f2, inf2, M::dv(g1 * f2, tnum2), dt, ndtl);
     }
     const R E2 = EXL(V, 0.2, 0.0);   // e^{0.2 V}
     {
@@ -243,7 +242,7 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         const R eb = fma((R)1096.6331584284585, E2, one);                             // e^{7}
         const R ec = one + EXL(V, 0.005, -0.25);
         const R rate = M::dv(ea * eb * ec, (R)0.1 * (eb + ec));
-        x.m = gate_rate(x.m, minf, rate, dt, ndtl, rl);
+        x.m = gate_rate<RL>(x.m, minf, rate, dt, ndtl);
     }
     {
         R inf, rate;
@@ -258,7 +257,7 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
             // tau = 85 e + 5/dd + 3
             rate = M::dv(dd, fma(EXQ(v45, -1.0 / 320.0, 4.442651256490317) + (R)3, dd, (R)5));   // ln 85
         }
-        x.s = gate_rate(x.s, inf, rate, dt, ndtl, rl);
+        x.s = gate_rate<RL>(x.s, inf, rate, dt, ndtl);
     }
     const R iE05 = EXL(V, -0.05, 0.0);   // e^{-0.05 V}
     {
@@ -268,14 +267,14 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         const R d2 = fma((R)2.718281828459045, E2, one);                              // e^{1}
         const R d3 = fma((R)12.182493960703473, iE05, one);                           // e^{2.5}
         const R rate = M::dv(d1 * d2 * d3, fma(fma((R)0.35, d1, (R)1.96), d3, d1 * d2));
-        x.d = gate_rate(x.d, inf, rate, dt, ndtl, rl);
+        x.d = gate_rate<RL>(x.d, inf, rate, dt, ndtl);
     }
     {
         // xr2: tau = 3/(1+e1) * 1.12/(1+e2)
         const R inf = M::dv(one, one + EXL(V, 1.0 / 24.0, 88.0 / 24.0));
         const R rate = fma((R)0.049787068367863944, iE05, one) *                      // e^{-3}
                        fma(EXL(V, 0.05, -3.0), (R)(1.0 / 3.36), (R)(1.0 / 3.36));
-        x.xr2 = gate_rate(x.xr2, inf, rate, dt, ndtl, rl);
+        x.xr2 = gate_rate<RL>(x.xr2, inf, rate, dt, ndtl);
     }
     const R iE6 = EXL(V, -1.0 / 6.0, 0.0);   // e^{-V/6}
     {
@@ -283,20 +282,20 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
         const R inf = M::dv(one, one + EXL(V, -1.0 / 14.0, -5.0 / 14.0));
         const R d2 = one + EXL(V, 1.0 / 15.0, -35.0 / 15.0);
         const R rate = M::dv(d2, fma((R)1400, M::rsq(fma((R)2.300975890892825, iE6, one)), (R)80 * d2));   // e^{5/6}
-        x.xs = gate_rate(x.xs, inf, rate, dt, ndtl, rl);
+        x.xs = gate_rate<RL>(x.xs, inf, rate, dt, ndtl);
     }
     {
         const R inf = M::dv(one, fma((R)28.03162489452614, iE6, one));                // e^{20/6}
         const R v40 = V + (R)40;
         const R rate = M::dv(one, EXQ(v40, -1.0 / 1800.0, 2.2512917986064953) + (R)0.8);   // ln 9.5
-        x.r = gate_rate(x.r, inf, rate, dt, ndtl, rl);
+        x.r = gate_rate<RL>(x.r, inf, rate, dt, ndtl);
     }
     {
         // fCass: inf = 0.6/den + 0.4, tau = 80/den + 2, den = 1 + (CaSS/0.05)^2
         const R q = x.CaSS * (R)20;
         const R den = fma(q, q, one);
         const R inv = M::dv(one, den);
-        x.fcass = gate_rate(x.fcass, fma((R)0.6, inv, (R)0.4), M::dv(den, fma((R)2, den, (R)80)), dt, ndtl, rl);
+        x.fcass = gate_rate<RL>(x.fcass, fma((R)0.6, inv, (R)0.4), M::dv(den, fma((R)2, den, (R)80)), dt, ndtl);
     }
 
     // forward Euler for V, concentrations and RR

@@ -81,8 +81,18 @@ template <typename R> struct Fm;
 template <> struct Fm<float> {
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
     static __device__ __forceinline__ float lg(float x) { return __logf(x); }
-    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    // a / b as a times the SFU reciprocal (rcp.approx.ftz of the PTX ISA,
+    // relative error ~2^-23; 0 for |b| beyond the normal range)
+    static __device__ __forceinline__ float dv(float a, float b) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+        return a * r;
+    }
+    static __device__ __forceinline__ float rsq(float x) {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
     static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
     // 2^x and log2(x) by the SFU instructions of the PTX ISA (ex2.approx,
     // lg2.approx; relative error ~2^-22), so that exp(a v + b) = 2^(a' v + b')

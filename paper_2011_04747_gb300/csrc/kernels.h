@@ -82,7 +82,7 @@ struct SyncArgs {
 // Launch shape of the reaction kernel.
 struct ReactTuning {
     int block = 128;        // threads per block (<= 128)
-    int min_blocks = 8;     // float TP06: resident 128-thread blocks per SM the registers must allow (8 or 10)
+    int min_blocks = 8;     // float TP06: resident 128-thread blocks per SM the registers must allow (6, 8 or 10)
     int kmax = 10;
     int pdl = 1;            // launch the per-step kernels with programmatic dependent launch
 };

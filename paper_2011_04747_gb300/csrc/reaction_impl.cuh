@@ -92,9 +92,16 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
         x.f2 = S[15 * 32];
         x.fcass = S[16 * 32];
         x.RR = S[17 * 32];
-        for (int s = 0; s < k; ++s) {
-            R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-            tp06_substep(x, cp, h, J, a.tp);
+        if (a.tp.gate_rl) {
+            for (int s = 0; s < k; ++s) {
+                R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
+                tp06_substep<R, true>(x, cp, h, J, a.tp);
+            }
+        } else {
+            for (int s = 0; s < k; ++s) {
+                R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
+                tp06_substep<R, false>(x, cp, h, J, a.tp);
+            }
         }
         a.V[i] = x.V;
         S[0 * 32] = x.Cai;

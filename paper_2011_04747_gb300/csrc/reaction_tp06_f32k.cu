@@ -11,6 +11,7 @@ void launch_tp06<float, true>(const DevState& s, const ModelArgs& m, double dt, 
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
     if (tune.min_blocks >= 10) launch_react_dims<float, M_TP06, true, 10>(a, s, op, fused, grid, block, tune, st);
+    else if (tune.min_blocks <= 6) launch_react_dims<float, M_TP06, true, 6>(a, s, op, fused, grid, block, tune, st);
     else launch_react_dims<float, M_TP06, true, 8>(a, s, op, fused, grid, block, tune, st);
 }
 

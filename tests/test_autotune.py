@@ -11,8 +11,8 @@ from parity_util import ensure_lib, gpu_available
 
 def test_candidate_grid():
     c = autotune.candidates()
-    assert len(c) == 128
-    assert len({json.dumps(x, sort_keys=True) for x in c}) == 128
+    assert len(c) == 192
+    assert len({json.dumps(x, sort_keys=True) for x in c}) == 192
     assert autotune.candidates({"react_block": (32,), "bucket_k": (0, 1)}) == [
         {"bucket_k": 0, "react_block": 32}, {"bucket_k": 1, "react_block": 32}]
 
