@@ -546,6 +546,20 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
                 if (j != self) A[cls * 27 + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
         if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
+        // per-node table row (z * 3 + y class) * 3 + x class, when it fits 16 bits
+        if (fresh && (int64_t)tab.nz * 9 <= 65535) {
+            std::vector<uint16_t> cls(N);
+            const int64_t nx = tab.nx, ny = tab.ny;
+            for (int64_t i = 0; i < N; ++i) {
+                const int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+                const int cx = x == 0 ? 0 : (x == nx - 1 ? 2 : 1);
+                const int cy = y == 0 ? 0 : (y == ny - 1 ? 2 : 1);
+                cls[i] = (uint16_t)((z * 3 + cy) * 3 + cx);
+            }
+            if ((rc = dalloc(c, &p, 2 * (size_t)N))) return rc;
+            c->op.cls = (uint16_t*)p;
+            CK(cpy_(c, p, cls.data(), 2 * (size_t)N, cudaMemcpyHostToDevice));
+        }
     } else {
         if (!fresh && c->op.kind != 1) return fail(c, DAETI_EINVAL, "operator layout changed");
         std::vector<double> scale(N);

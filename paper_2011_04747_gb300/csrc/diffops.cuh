@@ -73,6 +73,7 @@ struct OpView {
     int kind;             // 0 stencil table, 1 SELL-32
     int nx, ny, nz;
     const R* coef;
+    const uint16_t* cls;  // table row of each node (nullable)
     const int64_t* chunk_ptr;
     const int* chunk_w;
     const int* col;
@@ -88,16 +89,22 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
     if (DIM == 0) {
         sell_update<R, KAHAN>(op.chunk_ptr, op.chunk_w, op.col, op.val, vin, i, vi, ci, vout, cout);
     } else {
-        const int x = i % op.nx;
-        const int yz = i / op.nx;
-        const int y = yz % op.ny;
-        const int z = yz / op.ny;
-        const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
-        const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
         const int nxy = op.nx * op.ny;
         const int nx = op.nx;
         auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
-        stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
+        if (PAD && op.cls) {
+            // no boundary tests: the table row is all the stencil needs
+            const R* crow = op.coef + (size_t)op.cls[i] * 27;
+            stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, 1, 1, 1, 3, vi, ci, fetch, vout, cout);
+        } else {
+            const int x = i % op.nx;
+            const int yz = i / op.nx;
+            const int y = yz % op.ny;
+            const int z = yz / op.ny;
+            const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
+            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
+            stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
+        }
     }
 }
 
@@ -109,6 +116,7 @@ inline OpView<R> op_view(const DiffOp& op) {
     v.ny = op.ny;
     v.nz = op.nz;
     v.coef = (const R*)op.coef;
+    v.cls = op.cls;
     v.chunk_ptr = op.chunk_ptr;
     v.chunk_w = op.chunk_w;
     v.col = op.col;

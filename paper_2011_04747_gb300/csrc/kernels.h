@@ -48,6 +48,7 @@ struct DiffOp {
     int dim = 3;
     int nx = 1, ny = 1, nz = 1;
     void* coef = nullptr;    // table: [nz*9][27] off-diagonal dt_ad K_ij / m_i (self entry 0)
+    uint16_t* cls = nullptr; // table row of each node (nullable)
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
     int64_t* chunk_ptr = nullptr;   // start of chunk c in val/col
