@@ -37,7 +37,10 @@ ORACLE_SAMPLE_STEPS = 20
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 XU_LANES_PER_SM = 16
-TP06_XU_PER_SUBSTEP = 94.0     # exp/log/reciprocal/rsqrt per TP06 sub-step, counted from cells.cuh
+TP06_XU_PER_SUBSTEP = 82.0     # SFU (MUFU) instructions per TP06 sub-step, ncu opcode count (profiles/)
+# DRAM bytes (read + write) per reaction launch from the resting-phase ncu
+# capture in profiles/reaction_tp06_fp32_slab.md (the state stays in L2)
+REACTION_DRAM_BYTES_PER_LAUNCH = 146944.0
 
 
 def _dist():
@@ -205,7 +208,7 @@ def _reaction_roofline(solver, clocks, sub_per_step):
     fused = solver.daeti_get_tuning()["fuse_diffusion"]
     label = "reaction (TP06, FP32" + (", with the fused diffusion sub-step)" if fused else ")")
     return {"bound": "alu", "kernel": label, "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": REACTION_DRAM_BYTES_PER_LAUNCH,
             "avg_launch_us": avg_s * 1e6, "ops_per_node_substep": ops_per_sub,
             "substeps_per_launch": sub_per_step,
             "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled), 1 op/lane/cycle",
@@ -457,10 +460,12 @@ def profile_run(args):
     wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
     s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=args.graph_steps,
                                      bucket_k=bool(args.bucket))
-    s.daeti_advance(args.profile_run)
+    if args.profile_from > 0:
+        s.daeti_advance(args.profile_from)
+    s.daeti_advance(args.profile_from + args.profile_run)
     s.daeti_synchronize()
     s.close()
-    print(f"profile run: {args.profile_run} ms simulated")
+    print(f"profile run: {args.profile_run} ms simulated after {args.profile_from} ms")
 
 
 def main():
@@ -478,6 +483,9 @@ def main():
     ap.add_argument("--bucket", type=int, default=1, help="group nodes by k before step A (1) or not (0)")
     ap.add_argument("--profile-run", type=float, default=0.0,
                     help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
+    ap.add_argument("--profile-from", type=float, default=0.0,
+                    help="with --profile-run: first advance to this time (ms), e.g. into the plateau "
+                         "(60) or the resting phase (150)")
     args = ap.parse_args()
     if args.profile_run > 0:
         profile_run(args)
