@@ -181,10 +181,15 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
     return k;
 }
 
-// Block-cooperative append of node i (valid lanes) to the list of its k:
-// warp ranks by __match_any_sync, one shared atomic per (warp, k), one global
-// atomic per (block, k).  Every thread of the block must call it.
-__device__ __forceinline__ void block_append(int* counts, int* lists, int n, int i, int k, bool valid) {
+// Block-cooperative bucketing of node i (valid lanes) by its k: warp ranks
+// by __match_any_sync and one shared atomic per (warp, k), then one global
+// atomic per (block, k) on counts[k].  With `lists` the global atomics return
+// the block's positions and the nodes are written to their lists (list k at
+// lists + k*n); without, the counts are added without waiting for a result
+// and no list is written.  Every thread of the block must call it with the
+// same `lists`.
+__device__ __forceinline__ void block_append(int* counts, int* lists, int n, int i, int k, bool valid,
+                                             bool with_lists = true) {
     __shared__ int blk[DAETI_MAX_K];
     __shared__ int base[DAETI_MAX_K];
     if (threadIdx.x < DAETI_MAX_K) blk[threadIdx.x] = 0;
@@ -200,6 +205,10 @@ __device__ __forceinline__ void block_append(int* counts, int* lists, int n, int
         wbase = __shfl_sync(peers, wbase, leader);
     }
     __syncthreads();
+    if (!with_lists) {
+        if (threadIdx.x < DAETI_MAX_K && blk[threadIdx.x]) atomicAdd(&counts[threadIdx.x], blk[threadIdx.x]);
+        return;
+    }
     if (threadIdx.x < DAETI_MAX_K) {
         const int c = blk[threadIdx.x];
         base[threadIdx.x] = c ? atomicAdd(&counts[threadIdx.x], c) : 0;

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const
         if (KAHAN) cout[i] = cc;
         if (SYNC) k = sync_node(sp, i, v);
     }
-    if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, valid);
+    // counts[0] of this parity: 1 if the step A that follows wants its per-k
+    // lists built (set by the previous step A), else only the counts
+    if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, valid, sp.counts[0] != 0);
 }
 
 // Structured grids: a block owns a TX x TY tile in x-y and marches through a
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, in
             if (KAHAN) cout[i] = cc;
             if (SYNC) k = sync_node(sp, i, v);
         }
-        if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, col_in);
+        if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, col_in, sp.counts[0] != 0);
         __syncthreads();   // the plane z - 1 buffer is refilled next
     }
 }
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(256) rebuild_lists_kernel(int n, const uint8_t
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     block_append(counts, lists, n, i, valid ? (int)kk[i] : 1, valid);
+    if (i == 0) counts[0] = 1;   // the lists of this parity are built
 }
 
 void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st) {

@@ -26,7 +26,8 @@ struct DevState {
     uint8_t* kk = nullptr;                // sub-step count of the next step A
     void* act = nullptr;                  // activation times
     int* lists = nullptr;                 // per-k node lists of the next step A: list k at lists + k*n
-    int* counts = nullptr;                // [2][DAETI_MAX_K] list lengths (double-buffered by step parity)
+    int* counts = nullptr;                // [2][DAETI_MAX_K] bucket lengths (k >= 1) by step parity; [par][0]
+                                          // = 1 if the lists of that parity are (to be) built, 0 counts only
     unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
     StimDev* stims = nullptr;             // stimulus table
     int n_stims = 0;
@@ -92,7 +93,8 @@ struct ReactTuning {
 // Step A.  fused = false: on V[src] in place.  fused = true: first one
 // diffusion sub-step V[src] -> node value, then step A, result in V[1-src].
 // With `lists`, nodes come from the per-k lists of parity `par` (lengths
-// counts[par]); counts[1-par] is cleared for the next synchronisation.
+// counts[par]); counts[1-par] is cleared for the next synchronisation, which
+// builds lists only if this step's k was not uniform (counts[1-par][0]).
 void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef step, bool lists, int par, int src,
                      bool fused, const DiffOp& op, const ReactTuning& tune, cudaStream_t st);
 // One diffusion sub-step from V[src] to V[1-src]; with `sync`, the

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     __shared__ double sh_tn;
     __shared__ int sh_stim;
     __shared__ int sh_uni;
+    __shared__ int sh_listed;
     pdl_wait();
     pdl_trigger();
     // Warp 0: step time, stimulus window and list offsets, with the loads of
@@ -194,9 +195,12 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
             sh_tn = t0;
             sh_stim = any != 0u;
             sh_uni = full ? __ffs(full) - 1 : 0;
+            sh_listed = a.lists ? a.counts[0] : 0;
         }
         if (a.lists && blockIdx.x == 0) {
-            if (lane < DAETI_MAX_K) a.counts_next[lane] = 0;
+            // clear the next lengths; counts_next[0] asks the next
+            // synchronisation for lists unless one bucket holds every node now
+            if (lane < DAETI_MAX_K) a.counts_next[lane] = lane == 0 ? (full ? 0 : 1) : 0;
             if (a.substeps) {
                 unsigned long long tot = (unsigned long long)lane * (unsigned long long)c;
 #pragma unroll
@@ -220,6 +224,10 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
         // one bucket holds every node (common away from wavefronts): item t is
         // node t, no list indirection
         react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, sh_uni, tn, any_stim);
+    } else if (!sh_listed) {
+        // k became mixed after a step in which one bucket held every node, so
+        // the lists were not built: item t is node t with its own k
+        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, a.kk[t], tn, any_stim);
     } else {
         int k;
         const int i = item_node(a.lists, a.n, off, t, k);
