@@ -420,6 +420,36 @@ def bench_adjoint(args, env):
             "forward_ms": t_fwd * 1e3, "plain_advance_ms": t_plain * 1e3}
 
 
+def bench_accuracy(args, env):
+    """Section 3.1's comparison on the 2D sheet 501 x 501 (TP06 standing in for
+    O'Hara-Rudy), FP32 + Kahan: OST (dt 0.01 ms), OSTAR (dt_s-limited step) and
+    DAETI (dt 0.1 ms), 500 ms each; errors against OST as in Section 3.3."""
+    import inputs
+
+    wl = inputs.aniso_sheet_2d()
+    k, w = max(1, args.steps // 2), max(1, args.warmup // 2)
+
+    def timer(s):
+        return env.timed(lambda: s.daeti_advance(wl.t_end), k, w, reset=lambda: s.daeti_init_state(None))
+
+    common = dict(precision="fp32_kahan", graph_steps=args.graph_steps)
+    runs = [("ost", dict(scheme="ost", dt=0.01, **common)), ("ostar", dict(scheme="ostar", **common)),
+            ("daeti", dict(scheme="daeti", **common))]
+    from paper_2011_04747_gb300.compare import scheme_comparison
+
+    per = scheme_comparison(env.binding, wl, runs, stream=env.stream, timer=timer)
+    per["daeti"]["speedup_vs_ostar"] = per["ostar"]["wall_s"] / per["daeti"]["wall_s"]
+    return {
+        "metric": "DAETI speed-up over OST, 2D sheet 501x501 TP06 500 ms (Section 3.1 comparison)",
+        "value": per["daeti"]["speedup_vs_ost"], "unit": "x", "n_gpus": env.world, "steps": k, "warmup": w,
+        "ms_per_step": per["daeti"]["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32_kahan", "data": "synthetic",
+        "config": {"workload": "tp06_sheet_501x501_h0.01_500ms_ost_ostar_daeti", "nodes": wl.n_nodes,
+                   "probes": "centre + 11x11 grid, V every 0.1 ms", "cv_line": "centre row, x in [1, 4] cm"},
+        "schemes": per,
+    }
+
+
 def run_ours(args):
     import inputs
 
@@ -441,6 +471,8 @@ def run_ours(args):
                             t_end=50.0, steps_sample=2)
     elif wk == "batch":
         line = bench_batch(args, env)
+    elif wk == "accuracy":
+        line = bench_accuracy(args, env)
     else:
         line = bench_adjoint(args, env)
     if env.rank == 0:
@@ -475,7 +507,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slab",
-                    choices=["slab", "slab_l", "square", "sheet", "tets", "batch", "adjoint"])
+                    choices=["slab", "slab_l", "square", "sheet", "tets", "batch", "adjoint", "accuracy"])
     ap.add_argument("--graph-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")

@@ -181,6 +181,12 @@ int daeti_get_time(daeti_ctx* ctx, double* t, int64_t* n_steps);
  * means out is device memory (enqueued on the stream), 0 host (waits). */
 int daeti_read_v(daeti_ctx* ctx, void* out, int dtype, int on_device);
 
+/* V at n_probe given nodes (probe traces, e.g. every step at a few sites):
+ * out[j] = V(nodes[j]) as double, into host memory (waits).  nodes is
+ * caller-owned host memory of node indices in [0, n_nodes); EINVAL for an
+ * index out of range or n_probe < 0. */
+int daeti_read_v_nodes(daeti_ctx* ctx, const int64_t* nodes, int64_t n_probe, double* out);
+
 /* Activation times (ms, first upward crossing of v_threshold, -1 if none). */
 int daeti_read_activation(daeti_ctx* ctx, void* out, int dtype, int on_device);
 

@@ -155,15 +155,20 @@ def tp06_slab_3d(nx: int = 101, ny: int = 101, nz: int = 26, h: float = 0.02,
     )
 
 
+SHEET_COLUMN_THRESHOLD = 257.4   # TP06, 1 ms pulse on the X = 0 column, h = 100 um (bisection, oracle)
+
+
 def aniso_sheet_2d(n: int = 501, length: float = 5.0, d0: float = 0.0017, rho: float = 0.25,
-                   model: str = "tp06", t_end: float = 500.0, amp: float = 60.0,
+                   model: str = "tp06", t_end: float = 500.0, amp: float = 2.0 * SHEET_COLUMN_THRESHOLD,
                    dt: float = 0.1) -> Workload:
     """2D sheet shaped like the paper's Section 3.1 example.
 
     5 x 5 cm, h = 100 um (n = 501 nodes per side, 251 001 nodes), fibres along
     X, d0 = 0.0017 cm^2/ms longitudinal and rho * d0 transverse, 1 ms stimulus
-    on the X = 0 column.  The cell model is a stand-in (the paper's O'Hara-Rudy
-    model is not available).
+    on the X = 0 column at twice its capture threshold (Section 3.1; the
+    threshold of a single column at h = 100 um is 257 mV/ms, found by bisection
+    with the oracle on a 0.2 cm sheet).  The cell model is a stand-in (the
+    paper's O'Hara-Rudy model is not available).
     """
     h = length / (n - 1)
     ne = (n - 1) * (n - 1)

@@ -99,6 +99,7 @@ _SIGNATURES = {
     "daeti_get_time": (ctypes.c_int, [_VP, _DP, _I64P]),
     "daeti_read_v": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int]),
     "daeti_read_activation": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int]),
+    "daeti_read_v_nodes": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, _DP]),
     "daeti_read_state": (ctypes.c_int, [_VP, _DP]),
     "daeti_state_bytes": (ctypes.c_int, [_VP, _I64P]),
     "daeti_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
@@ -302,6 +303,14 @@ class Solver:
 
     def daeti_read_activation(self, out=None, dtype=np.float64):
         return self._read(self.lib.daeti_read_activation, out, dtype)
+
+    def daeti_read_v_nodes(self, nodes):
+        """V (double) at the given node indices."""
+        idx = np.ascontiguousarray(nodes, dtype=np.int64)
+        out = np.empty(idx.size, dtype=np.float64)
+        self._check(self.lib.daeti_read_v_nodes(self.ctx, _ptr(idx, ctypes.c_int64), idx.size,
+                                                _ptr(out, ctypes.c_double)))
+        return out
 
     def daeti_read_state(self):
         out = np.empty(self.n_states * self.n_nodes, dtype=np.float64)

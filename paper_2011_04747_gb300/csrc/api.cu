@@ -84,6 +84,8 @@ void free_device(daeti_ctx* c) {
     c->s = DevState();
     c->op = DiffOp();
     c->scratch = nullptr;
+    c->probe = nullptr;
+    c->probe_cap = 0;
     c->prepared = false;
 }
 
@@ -861,6 +863,29 @@ static int read_array(daeti_ctx* c, const void* src, const float* comp, void* ou
     }
     launch_convert(src, c->s.prec, comp, c->scratch, dtype == DAETI_DTYPE_F32, N, c->stream);
     CK(cudaMemcpyAsync(out, c->scratch, ob * N, cudaMemcpyDeviceToHost, c->stream));
+    return daeti_synchronize(c);
+}
+
+int daeti_read_v_nodes(daeti_ctx* c, const int64_t* nodes, int64_t n_probe, double* out) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (n_probe < 0 || (n_probe > 0 && (!nodes || !out))) return fail(c, DAETI_EINVAL, "bad probe arguments");
+    if (n_probe == 0) return DAETI_OK;
+    for (int64_t j = 0; j < n_probe; ++j)
+        if (nodes[j] < 0 || nodes[j] >= c->n_nodes) return fail(c, DAETI_EINVAL, "probe node out of range");
+    if (n_probe > c->probe_cap) {
+        void* p = nullptr;
+        int rc = dalloc(c, &p, 16 * (size_t)n_probe);
+        if (rc) return rc;
+        c->probe = p;
+        c->probe_cap = n_probe;
+    }
+    int64_t* dn = (int64_t*)c->probe;
+    double* dv = (double*)((char*)c->probe + 8 * (size_t)c->probe_cap);
+    CK(cudaMemcpyAsync(dn, nodes, 8 * (size_t)n_probe, cudaMemcpyHostToDevice, c->stream));
+    launch_gather_v(c->s.V[c->cur], c->s.prec, c->s.kahan ? c->s.C[c->cur] : nullptr, dn, dv, n_probe, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dv, 8 * (size_t)n_probe, cudaMemcpyDeviceToHost, c->stream));
     return daeti_synchronize(c);
 }
 

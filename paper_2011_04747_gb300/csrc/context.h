@@ -49,6 +49,8 @@ struct daeti_ctx {
     int cur = 0;
     int par = 0;
     void* scratch = nullptr;   // n doubles for conversions
+    void* probe = nullptr;     // probe node indices then values (daeti_read_v_nodes)
+    int64_t probe_cap = 0;     // probes the buffer holds
     std::vector<double> mass;  // lumped mass per node (host, FP64)
     double kref[64];           // unit-D element stiffness of a grid element (adjoint)
     struct AdjointBuffers* adj = nullptr;   // adjoint work buffers (adjoint.cu)

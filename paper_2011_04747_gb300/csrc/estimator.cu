@@ -203,6 +203,26 @@ void launch_convert(const void* src, int src_prec, const float* comp, void* dst,
     }
 }
 
+// dst[j] = V(nodes[j]) (- comp), as double.
+template <typename S>
+__global__ void gather_v_kernel(const S* __restrict__ src, const float* __restrict__ comp,
+                                const int64_t* __restrict__ nodes, double* __restrict__ dst, int64_t m) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t i = nodes[j];
+    double v = (double)src[i];
+    if (comp) v -= (double)comp[i];
+    dst[j] = v;
+}
+
+void launch_gather_v(const void* src, int src_prec, const float* comp, const int64_t* nodes, double* dst, int64_t m,
+                     cudaStream_t st) {
+    const int grid = (int)((m + 127) / 128);
+    if (!grid) return;
+    if (src_prec == P_F64) gather_v_kernel<double><<<grid, 128, 0, st>>>((const double*)src, comp, nodes, dst, m);
+    else gather_v_kernel<float><<<grid, 128, 0, st>>>((const float*)src, comp, nodes, dst, m);
+}
+
 // dst[i] = state s of node i from the chunked state array (state_index), as double.
 template <typename S>
 __global__ void gather_state_kernel(const S* __restrict__ src, int ns, int s, double* __restrict__ dst, int64_t n) {

@@ -132,6 +132,9 @@ void launch_node_mass(const EstOp& op, double* m_out, cudaStream_t st);
 // Conversions between the state precision and the caller's dtype.
 void launch_convert(const void* src, int src_prec, const float* comp, void* dst, int dst_f32,
                     int64_t n, cudaStream_t st);
+// V at the given nodes (minus the Kahan term), as double.
+void launch_gather_v(const void* src, int src_prec, const float* comp, const int64_t* nodes, double* dst, int64_t m,
+                     cudaStream_t st);
 // State s of every node from the chunked state array, as double.
 void launch_gather_state(const void* src, int src_prec, int ns, int s, double* dst, int64_t n, cudaStream_t st);
 }  // namespace daeti
