@@ -541,11 +541,12 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
         c->op.nx = tab.nx;
         c->op.ny = tab.ny;
         c->op.nz = tab.nz;
-        std::vector<double> A(tab.K.size(), 0.0);
-        const int self = c->dim == 3 ? 13 : 4;
+        // rows of DAETI_ROW entries (27 offsets, zero pad) for 16-byte loads
+        std::vector<double> A(tab.m.size() * DAETI_ROW, 0.0);
+        const int self = 13;   // the centre entry (2D rows use entries 9..17)
         for (size_t cls = 0; cls < tab.m.size(); ++cls)
             for (int j = 0; j < 27; ++j)
-                if (j != self) A[cls * 27 + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
+                if (j != self) A[cls * DAETI_ROW + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
         if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
         // per-node table row (z * 3 + y class) * 3 + x class, when it fits 16 bits

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev*
     const int z = yz / t.ny;
     const int cx = x == 0 ? 0 : (x == t.nx - 1 ? 2 : 1);
     const int cy = y == 0 ? 0 : (y == t.ny - 1 ? 2 : 1);
-    const R* crow = coef + ((size_t)t.coef_off + (size_t)(z * 3 + cy) * 3 + cx) * 27;
+    const R* crow = coef + ((size_t)t.coef_off + (size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
     const int nx = t.nx, nxy = t.nx * t.ny;
     auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
     R v;
@@ -331,7 +331,7 @@ int daeti_batch_prepare(daeti_batch* b) {
             return bfail(b, DAETI_EUNSUPPORTED, "batch tissues need conductivity constant on each z layer");
         const GridTable& g = tabs[t];
         double mn = 1e300;
-        const int self = bt.dim == 3 ? 13 : 4;
+        const int self = 13;   // the centre entry (2D rows use entries 9..17)
         for (size_t cls = 0; cls < g.m.size(); ++cls) {
             double s = g.K[cls * 27 + self];
             for (int j = 0; j < 27; ++j)
@@ -357,15 +357,15 @@ int daeti_batch_prepare(daeti_batch* b) {
         info[t].ny = (int)bt.n[1];
         info[t].nz = bt.dim == 3 ? (int)bt.n[2] : 1;
         info[t].dim = bt.dim;
-        info[t].coef_off = (int)(A.size() / 27);
+        info[t].coef_off = (int)(A.size() / DAETI_ROW);
         info[t].vscale = bt.model == DAETI_MODEL_MS ? 100.0 : 1.0;
         info[t].vth = std::isnan(b->opt.v_threshold) ? (bt.model == DAETI_MODEL_MS ? 0.5 : -40.0) : b->opt.v_threshold;
-        const int self = bt.dim == 3 ? 13 : 4;
+        const int self = 13;
         const size_t base = A.size();
-        A.resize(base + g.K.size(), 0.0);
+        A.resize(base + g.m.size() * DAETI_ROW, 0.0);
         for (size_t cls = 0; cls < g.m.size(); ++cls)
             for (int j = 0; j < 27; ++j)
-                if (j != self) A[base + cls * 27 + j] = b->dt_ad * g.K[cls * 27 + j] / g.m[cls];
+                if (j != self) A[base + cls * DAETI_ROW + j] = b->dt_ad * g.K[cls * 27 + j] / g.m[cls];
     }
     // stimuli: identical (t0, duration, amplitude, period, count) share one slot
     // (identical stimuli within one tissue keep separate slots: they add up)

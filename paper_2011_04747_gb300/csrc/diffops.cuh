@@ -11,31 +11,50 @@ namespace daeti {
 // Boundary class of a coordinate: 0 low face, 1 interior, 2 high face.
 __device__ __forceinline__ int bclass(int x, int n) { return x == 0 ? 0 : (x == n - 1 ? 2 : 1); }
 
+template <typename R>
+__device__ __forceinline__ void ld16(const R* p, R* out);
+template <>
+__device__ __forceinline__ void ld16<float>(const float* p, float* out) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ld16<double>(const double* p, double* out) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    out[0] = v.x;
+    out[1] = v.y;
+}
+
 // One explicit sub-step at a node whose neighbour at offset (dx,dy,dz) is
 // fetch(dx,dy,dz).  Shared by the plain and the fused kernels so both give
-// the same results.  Offsets outside the grid have coefficient 0 in the
-// table; PAD (V buffers with a finite ghost margin wider than the stencil
-// reach) reads them anyway and adds 0 * (finite), which leaves the sum
-// unchanged, instead of testing the boundary class per neighbour.
+// the same results: the terms are added in the order of the table entries.
+// Offsets outside the grid have coefficient 0 in the table; PAD (V buffers
+// with a finite ghost margin wider than the stencil reach) reads them anyway
+// and adds 0 * (finite), which leaves the sum unchanged, instead of testing
+// the boundary class per neighbour.
 template <typename R, int DIM, bool KAHAN, bool PAD = false, class Fetch>
 __device__ __forceinline__ void stencil_update(const R* __restrict__ crow, int cx, int cy, int z, int nz, R vi,
                                                float ci, const Fetch& fetch, R& vout, float& cout) {
+    constexpr int NV = 16 / (int)sizeof(R);           // entries per 16-byte load
+    constexpr int J0 = DIM == 3 ? 0 : 9;              // entries used: [J0, J1)
+    constexpr int J1 = DIM == 3 ? 27 : 18;
     R acc = (R)0;
 #pragma unroll
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    for (int q = J0 / NV; q * NV < J1; ++q) {
+        R cs[NV];
+        ld16<R>(crow + q * NV, cs);
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (dx == 0 && dy == 0 && dz == 0) continue;
-                const bool ok = PAD || ((dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
-                                        (dy <= 0 || cy < 2) &&
-                                        (DIM == 2 || ((dz >= 0 || z > 0) && (dz <= 0 || z < nz - 1))));
-                if (ok) {
-                    const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                    acc = fma(__ldg(crow + j), fetch(dx, dy, dz) - vi, acc);
-                }
-            }
+        for (int r = 0; r < NV; ++r) {
+            const int j = q * NV + r;
+            if (j < J0 || j >= J1 || j == 13) continue;
+            const int dz = j / 9 - 1, dy = (j / 3) % 3 - 1, dx = j % 3 - 1;
+            const bool ok = PAD || ((dx >= 0 || cx > 0) && (dx <= 0 || cx < 2) && (dy >= 0 || cy > 0) &&
+                                    (dy <= 0 || cy < 2) &&
+                                    (DIM == 2 || ((dz >= 0 || z > 0) && (dz <= 0 || z < nz - 1))));
+            if (ok) acc = fma(cs[r], fetch(dx, dy, dz) - vi, acc);
         }
     }
     R v = vi;
@@ -94,7 +113,7 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
         auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
         if (PAD && op.cls) {
             // no boundary tests: the table row is all the stencil needs
-            const R* crow = op.coef + (size_t)op.cls[i] * 27;
+            const R* crow = op.coef + (size_t)op.cls[i] * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, 1, 1, 1, 3, vi, ci, fetch, vout, cout);
         } else {
             const int x = i % op.nx;
@@ -102,7 +121,7 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
             const int y = yz % op.ny;
             const int z = yz / op.ny;
             const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
-            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
+            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
         }
     }

@@ -6,7 +6,8 @@
 // neighbouring nodes.  Layouts:
 //   * structured grids: a 9-point (2D) / 27-point (3D) stencil whose
 //     coefficients depend only on the node's z layer and its x/y boundary
-//     class (table [nz][3][3][27]); used when D varies at most with z;
+//     class (table [nz][3][3][28], the 27 offsets and a pad); used when D
+//     varies at most with z;
 //   * any mesh: SELL-32 sparse rows (chunks of 32 rows, column-major).
 // The launch that ends a diffusion half at t_n also runs the synchronisation
 // epilogue (activation time, k of the next step A, per-k node lists).  The
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, in
         int i = 0;
         if (col_in) {
             i = gx + nx * gy + nxy * z;
-            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * 27;
+            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             auto fetch = [&](int dx, int dy, int dz) {
                 return buf[DIM == 3 ? ((z + dz + 3) % 3) : 0][li + dx + dy * PX];
             };

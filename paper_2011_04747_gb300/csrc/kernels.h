@@ -43,12 +43,17 @@ struct ModelArgs {
     int gate_rl = 1;
 };
 
+// Stencil table rows are DAETI_ROW entries: the 27 offsets (dz+1)*9 +
+// (dy+1)*3 + (dx+1) (2D uses 9..17), the centre 13 being 0, and one zero pad,
+// so that a row is read with 16-byte loads.
+#define DAETI_ROW 28
+
 // Diffusion operator in one of two layouts.
 struct DiffOp {
     int kind = 0;            // 0 structured stencil table, 1 SELL-32
     int dim = 3;
     int nx = 1, ny = 1, nz = 1;
-    void* coef = nullptr;    // table: [nz*9][27] off-diagonal dt_ad K_ij / m_i (self entry 0)
+    void* coef = nullptr;    // table: [nz*9][28] off-diagonal dt_ad K_ij / m_i (centre entry and pad 0)
     uint16_t* cls = nullptr; // table row of each node (nullable)
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
