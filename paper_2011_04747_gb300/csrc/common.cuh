@@ -148,6 +148,7 @@ struct SyncParams {
     int* lists;        // list of k starts at lists + k * n (k = 1..kmax)
     int n;
     int* flags;        // flags[0] |= 1 on non-finite V
+    int* uflag;        // set when a node's k differs from the expected uniform k (mode -K)
     double dt;
     R vscale;          // model units -> mV for the k rule
     R vth;             // activation threshold
@@ -181,15 +182,11 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
     return k;
 }
 
-// Block-cooperative bucketing of node i (valid lanes) by its k: warp ranks
-// by __match_any_sync and one shared atomic per (warp, k), then one global
-// atomic per (block, k) on counts[k].  With `lists` the global atomics return
-// the block's positions and the nodes are written to their lists (list k at
-// lists + k*n); without, the counts are added without waiting for a result
-// and no list is written.  Every thread of the block must call it with the
-// same `lists`.
-__device__ __forceinline__ void block_append(int* counts, int* lists, int n, int i, int k, bool valid,
-                                             bool with_lists = true) {
+// Block-cooperative append of node i (valid lanes) to the list of its k
+// (list k at lists + k*n): warp ranks by __match_any_sync and one shared
+// atomic per (warp, k), then one global atomic per (block, k) on counts[k]
+// that returns the block's positions.  Every thread of the block must call it.
+__device__ __forceinline__ void block_append(int* counts, int* lists, int n, int i, int k, bool valid) {
     __shared__ int blk[DAETI_MAX_K];
     __shared__ int base[DAETI_MAX_K];
     if (threadIdx.x < DAETI_MAX_K) blk[threadIdx.x] = 0;
@@ -205,10 +202,6 @@ __device__ __forceinline__ void block_append(int* counts, int* lists, int n, int
         wbase = __shfl_sync(peers, wbase, leader);
     }
     __syncthreads();
-    if (!with_lists) {
-        if (threadIdx.x < DAETI_MAX_K && blk[threadIdx.x]) atomicAdd(&counts[threadIdx.x], blk[threadIdx.x]);
-        return;
-    }
     if (threadIdx.x < DAETI_MAX_K) {
         const int c = blk[threadIdx.x];
         base[threadIdx.x] = c ? atomicAdd(&counts[threadIdx.x], c) : 0;
@@ -218,6 +211,21 @@ __device__ __forceinline__ void block_append(int* counts, int* lists, int n, int
         const int pos = base[k] + wbase + rank;
         if (pos < n) lists[(size_t)k * n + pos] = i;
     }
+}
+
+// Bucketing at a synchronisation.  counts[0] holds the mode the previous
+// step A chose: 1 = append every node to the list of its k (block_append);
+// -K = that step had k = K at every node, so only check that this one does
+// too (one block vote; *uflag is set if some node's k differs).  Every
+// thread of the block must call it.
+__device__ __forceinline__ void bucket_nodes(int* counts, int* lists, int* uflag, int n, int i, int k, bool valid) {
+    const int mode = counts[0];
+    if (mode < 0) {
+        const int differs = __syncthreads_or(valid && k != -mode);
+        if (differs && threadIdx.x == 0) atomicOr(uflag, 1);
+        return;
+    }
+    block_append(counts, lists, n, i, k, valid);
 }
 
 }  // namespace daeti

@@ -35,9 +35,7 @@ __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const
         if (KAHAN) cout[i] = cc;
         if (SYNC) k = sync_node(sp, i, v);
     }
-    // counts[0] of this parity: 1 if the step A that follows wants its per-k
-    // lists built (set by the previous step A), else only the counts
-    if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, valid, sp.counts[0] != 0);
+    if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, valid);
 }
 
 // Structured grids: a block owns a TX x TY tile in x-y and marches through a
@@ -103,7 +101,7 @@ __global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, in
             if (KAHAN) cout[i] = cc;
             if (SYNC) k = sync_node(sp, i, v);
         }
-        if (SYNC && sp.counts) block_append(sp.counts, sp.lists, sp.n, i, k, col_in, sp.counts[0] != 0);
+        if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
         __syncthreads();   // the plane z - 1 buffer is refilled next
     }
 }
@@ -118,6 +116,7 @@ static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef st
     sp.lists = s.lists;
     sp.n = (int)s.n;
     sp.flags = s.flags;
+    sp.uflag = s.flags + 2 + par;
     sp.dt = sa.dt;
     sp.vscale = (R)sa.vscale;
     sp.vth = (R)sa.vth;

@@ -27,13 +27,13 @@ struct DevState {
     void* act = nullptr;                  // activation times
     int* lists = nullptr;                 // per-k node lists of the next step A: list k at lists + k*n
     int* counts = nullptr;                // [2][DAETI_MAX_K] bucket lengths (k >= 1) by step parity; [par][0]
-                                          // = 1 if the lists of that parity are (to be) built, 0 counts only
+                                          // = bucketing mode: 1 lists, -K every node expected at k = K
     unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
     StimDev* stims = nullptr;             // stimulus table
     int n_stims = 0;
     long long* step_ctr = nullptr;        // device step counter used by graph replays
     unsigned long long* substeps = nullptr;   // running total of node reaction sub-steps (bucketing)
-    int* flags = nullptr;                 // [0] non-finite, [1] timeout
+    int* flags = nullptr;                 // [0] non-finite, [1] timeout, [2 + par] k not uniform (mode -K)
 };
 
 struct ModelArgs {
@@ -99,7 +99,8 @@ struct ReactTuning {
 // diffusion sub-step V[src] -> node value, then step A, result in V[1-src].
 // With `lists`, nodes come from the per-k lists of parity `par` (lengths
 // counts[par]); counts[1-par] is cleared for the next synchronisation, which
-// builds lists only if this step's k was not uniform (counts[1-par][0]).
+// builds lists unless this step had one k at every node (then it only checks
+// that the next step has it too: counts[1-par][0] = -k).
 void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef step, bool lists, int par, int src,
                      bool fused, const DiffOp& op, const ReactTuning& tune, cudaStream_t st);
 // One diffusion sub-step from V[src] to V[1-src]; with `sync`, the

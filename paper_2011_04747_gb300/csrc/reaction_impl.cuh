@@ -25,7 +25,9 @@ struct ReactArgs {
     const uint8_t* kk;
     const int* lists;    // per-k node lists (list k at lists + k*n), null: node = item
     const int* counts;   // list lengths of this step A (counts[k], k >= 1)
-    int* counts_next;    // list lengths of the next step A, cleared here
+    int* counts_next;    // list lengths of the next step A, cleared here; [0] = its bucketing mode
+    const int* uflag;    // with mode -K: set if some node's k is not K
+    int* uflag_next;     // the same for the next step A, cleared here
     unsigned long long* substeps;
     int kmax;
     const unsigned* stim_mask;
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     __shared__ int sh_stim;
     __shared__ int sh_uni;
     __shared__ int sh_listed;
+    __shared__ int sh_total;
     pdl_wait();
     pdl_trigger();
     // Warp 0: step time, stimulus window and list offsets, with the loads of
@@ -189,22 +192,31 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
             if (lane + d < DAETI_MAX_K) sfx += y;
         }
         if (lane < DAETI_MAX_K) off[lane] = sfx - c;
-        // the k of a bucket that holds all n nodes, else 0
+        // Bucketing mode of this step (counts[0], chosen by the previous step
+        // A): 1 = lists built, counts valid; -K = k expected to be K at every
+        // node, confirmed unless *uflag is set.  uni = the k every node has,
+        // else 0.
+        const int mode = a.lists ? a.counts[0] : 1;
+        const int broken = mode < 0 ? *a.uflag : 0;
         const unsigned full = __ballot_sync(0xffffffffu, c == a.n && c > 0);
+        const int uni = mode < 0 ? (broken ? 0 : -mode) : (full ? __ffs(full) - 1 : 0);
+        const int listed_total = __shfl_sync(0xffffffffu, sfx, 0);
         if (lane == 0) {
             sh_tn = t0;
             sh_stim = any != 0u;
-            sh_uni = full ? __ffs(full) - 1 : 0;
-            sh_listed = a.lists ? a.counts[0] : 0;
+            sh_uni = uni;
+            sh_listed = mode > 0;
+            sh_total = mode < 0 ? a.n : listed_total;
         }
         if (a.lists && blockIdx.x == 0) {
-            // clear the next lengths; counts_next[0] asks the next
-            // synchronisation for lists unless one bucket holds every node now
-            if (lane < DAETI_MAX_K) a.counts_next[lane] = lane == 0 ? (full ? 0 : 1) : 0;
-            if (a.substeps) {
-                unsigned long long tot = (unsigned long long)lane * (unsigned long long)c;
+            // next step's mode: expect this step's uniform k again, else lists
+            if (lane < DAETI_MAX_K) a.counts_next[lane] = lane == 0 ? (uni ? -uni : 1) : 0;
+            if (lane == 0) *a.uflag_next = 0;
+            if (a.substeps && (mode > 0 || uni)) {
+                unsigned long long tot = mode > 0 ? (unsigned long long)lane * (unsigned long long)c : 0ull;
 #pragma unroll
                 for (int d = 16; d >= 1; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+                if (mode < 0) tot = (unsigned long long)a.n * (unsigned long long)uni;
                 if (lane == 0) atomicAdd(a.substeps, tot);
             }
         }
@@ -217,18 +229,25 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
         if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, a.kk[t], tn, any_stim);
         return;
     }
-    const int total = off[0];
+    const int total = sh_total;
     const int t = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
-    if (t >= total) return;
     if (sh_uni) {
-        // one bucket holds every node (common away from wavefronts): item t is
+        // every node has the same k (common away from wavefronts): item t is
         // node t, no list indirection
-        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, sh_uni, tn, any_stim);
+        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, sh_uni, tn, any_stim);
     } else if (!sh_listed) {
-        // k became mixed after a step in which one bucket held every node, so
-        // the lists were not built: item t is node t with its own k
-        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, a.kk[t], tn, any_stim);
-    } else {
+        // k became mixed after a step with the same k everywhere, so no lists
+        // were built: item t is node t with its own k (and the sub-step count
+        // is summed here)
+        const int kt = t < total ? (int)a.kk[t] : 0;
+        if (a.substeps) {
+            unsigned long long w = (unsigned long long)kt;
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+            if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.substeps, w);
+        }
+        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, kt, tn, any_stim);
+    } else if (t < total) {
         int k;
         const int i = item_node(a.lists, a.n, off, t, k);
         react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, i, k, tn, any_stim);
@@ -250,6 +269,8 @@ ReactArgs<R> react_args(const DevState& s, const ModelArgs& m, double dt, StepRe
     a.lists = lists ? s.lists : nullptr;
     a.counts = s.counts + par * DAETI_MAX_K;
     a.counts_next = s.counts + (1 - par) * DAETI_MAX_K;
+    a.uflag = s.flags + 2 + par;
+    a.uflag_next = s.flags + 2 + (1 - par);
     a.substeps = s.substeps;
     a.kmax = tune.kmax;
     a.stim_mask = s.stim_mask;

@@ -229,3 +229,26 @@ def test_cell_models_fp64_tight(model, params):
     assert float(np.max(np.abs(g - o))) * scale <= 1e-6
     np.testing.assert_allclose(gs, sim.S, rtol=1e-9, atol=1e-12)
     assert np.all(ga >= 0) and float(np.max(np.abs(ga - oa))) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp32_kahan", "fp64"])
+def test_probe_reads_match_the_full_field(precision):
+    """daeti_read_v_nodes returns V (Kahan term applied) at the given nodes,
+    repeated and unordered indices included; bad indices are EINVAL."""
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = I.tp06_slab_3d(13, 11, 5, t_end=10)
+    s = binding.solver_from_workload(wl, precision=precision)
+    s.daeti_advance(3.0)
+    full = s.daeti_read_v()
+    nodes = np.array([0, wl.n_nodes - 1, 17, 17, 5, 300], dtype=np.int64)
+    assert np.array_equal(s.daeti_read_v_nodes(nodes), full[nodes])
+    big = np.arange(wl.n_nodes, dtype=np.int64)[::-1]
+    assert np.array_equal(s.daeti_read_v_nodes(big), full[big])
+    assert s.daeti_read_v_nodes(np.zeros(0, dtype=np.int64)).size == 0
+    for bad in ([-1], [wl.n_nodes]):
+        with pytest.raises(binding.DaetiError) as e:
+            s.daeti_read_v_nodes(np.array(bad, dtype=np.int64))
+        assert e.value.code == binding.EINVAL
+    s.close()
