@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
         // node, confirmed unless *uflag is set.  uni = the k every node has,
         // else 0.
         const int mode = a.lists ? a.counts[0] : 1;
-        const int broken = mode < 0 ? *a.uflag : 0;
+        const int uflag = a.lists ? *a.uflag : 0;   // loaded with the mode, not after it
+        const int broken = mode < 0 ? uflag : 0;
         const unsigned full = __ballot_sync(0xffffffffu, c == a.n && c > 0);
         const int uni = mode < 0 ? (broken ? 0 : -mode) : (full ? __ffs(full) - 1 : 0);
         const int listed_total = __shfl_sync(0xffffffffu, sfx, 0);
