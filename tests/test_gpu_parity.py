@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import inputs as I
+from oracle import scheme
 from parity_util import act_error, gpu_available, run_gpu, run_oracle
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
@@ -252,3 +253,27 @@ def test_probe_reads_match_the_full_field(precision):
             s.daeti_read_v_nodes(np.array(bad, dtype=np.int64))
         assert e.value.code == binding.EINVAL
     s.close()
+
+
+@pytest.mark.parametrize("graph_steps", [0, 20])
+def test_substep_count_equals_the_oracle_sum_of_k(graph_steps):
+    """The sub-step counter (sum over steps and nodes of the k step A used),
+    kept from the per-k list lengths, from n * k when every node has one k,
+    and summed per node on the step after that stops holding, equals the
+    oracle's sum of k in FP64 through the stimulus and the first wavefront."""
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = I.tp06_slab_3d(15, 13, 5, t_end=40)
+    n_steps = 300
+    sim = scheme.simulation_from_workload(wl)
+    total = 0
+    for _ in range(n_steps):
+        total += int(np.sum(sim.k))
+        sim.step()
+    s = binding.solver_from_workload(wl, precision="fp64", graph_steps=graph_steps)
+    s.daeti_advance(n_steps * wl.dt)
+    got = s.daeti_get_substeps()
+    s.close()
+    assert total > n_steps * wl.n_nodes          # k > 1 somewhere
+    assert got == total
