@@ -10,7 +10,9 @@
 //     varies at most with z;
 //   * any mesh: SELL-32 sparse rows (chunks of 32 rows, column-major).
 // The launch that ends a diffusion half at t_n also runs the synchronisation
-// epilogue (activation time, k of the next step A, per-k node lists).  The
+// epilogue (activation time, k of the next step A, and either the per-k node
+// lists or, after a step with one k at every node, the check that k is still
+// uniform).  The
 // last sub-step of each step I is fused into the reaction launch
 // (reaction.cu).
 #include <algorithm>
