@@ -69,7 +69,7 @@ const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.
 namespace {
 
 void drop_graphs(daeti_ctx* c) {
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
         if (c->graphs[i]) {
             cudaGraphExecDestroy(c->graphs[i]);
             c->graphs[i] = nullptr;
@@ -116,9 +116,39 @@ struct Timer {
 
 bool lists_mode(const daeti_ctx* c) { return c->lists && c->sargs.adaptive; }
 
-void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bool timed) {
+// quiet: no stimulus window overlaps the step, so the launch is told there are
+// no stimuli (it then skips the step time and the window test; J = 0 either way)
+void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bool timed, bool quiet) {
     Timer t(c, st, timed, 0);
-    launch_reaction(c->s, c->margs, c->dt_eff, ref, lists_mode(c), c->par, buf, fused, c->op, c->rtune, st);
+    if (quiet && c->s.n_stims) {
+        DevState sv = c->s;
+        sv.n_stims = 0;
+        launch_reaction(sv, c->margs, c->dt_eff, ref, lists_mode(c), c->par, buf, fused, c->op, c->rtune, st);
+    } else {
+        launch_reaction(c->s, c->margs, c->dt_eff, ref, lists_mode(c), c->par, buf, fused, c->op, c->rtune, st);
+    }
+}
+
+// True if some stimulus window [t0 + p T, t0 + p T + dur) (with the 1e-9 ms
+// guard of the kernels, widened by 1e-6 ms here) meets the sub-step times
+// of steps n0 .. n0 + G - 1, i.e. [n0 dt, (n0 + G) dt).
+bool stimulus_in_steps(const daeti_ctx* c, int64_t n0, int64_t G) {
+    const double a = (double)n0 * c->dt_eff - 1e-6, b = (double)(n0 + G) * c->dt_eff + 1e-6;
+    for (const StimHost& s : c->stims) {
+        if (s.count <= 0) continue;
+        if (s.count == 1 || s.period <= 0.0) {
+            for (int p = 0; p < (s.period > 0.0 ? s.count : 1); ++p)
+                if (s.t0 + p * s.period < b && s.t0 + p * s.period + s.dur > a) return true;
+            continue;
+        }
+        // repetitions p with t0 + p T < b and t0 + p T + dur > a
+        const double lo = std::ceil((a - s.t0 - s.dur) / s.period - 1e-12);
+        const double hi = std::floor((b - s.t0) / s.period + 1e-12);
+        const double p0 = std::max(0.0, lo), p1 = std::min((double)(s.count - 1), hi);
+        for (double p = p0; p <= p1 && p <= p0 + 2.0; p += 1.0)
+            if (s.t0 + p * s.period < b && s.t0 + p * s.period + s.dur > a) return true;
+    }
+    return false;
 }
 
 void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
@@ -131,14 +161,14 @@ void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool
 // the last one fused into the reaction launch unless disabled), step II,
 // step III (l sub-steps, synchronisation after the last).  V returns to
 // buffer c->cur (2l buffer flips).
-void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed) {
+void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed, bool quiet = false) {
     int buf = c->cur;
     const int first = c->fused ? c->l - 1 : c->l;
     for (int i = 0; i < first; ++i) {
         L_diff(c, ref, buf, false, st, timed);
         buf ^= 1;
     }
-    L_react(c, ref, buf, c->fused, st, timed);
+    L_react(c, ref, buf, c->fused, st, timed, quiet);
     if (c->fused) buf ^= 1;
     for (int i = 0; i < c->l; ++i) {
         L_diff(c, ref, buf, i == c->l - 1, st, timed);
@@ -147,13 +177,15 @@ void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed) {
     if (lists_mode(c)) c->par ^= 1;
 }
 
-// Capture graph_steps steps from the current list parity.
-int capture_graph(daeti_ctx* c, cudaGraphExec_t* out) {
+// Capture graph_steps steps from the current list parity (quiet: for
+// segments in which no stimulus window is open).
+int capture_graph(daeti_ctx* c, cudaGraphExec_t* out, bool quiet) {
     const int G = c->graph_steps;
     const int par0 = c->par;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int j = 0; j < G; ++j) enqueue_step(c, StepRef{c->s.step_ctr, (long long)j}, c->cap_stream, false);
+    for (int j = 0; j < G; ++j)
+        enqueue_step(c, StepRef{c->s.step_ctr, (long long)j}, c->cap_stream, false, quiet);
     launch_tick(c->s.step_ctr, G, c->cap_stream);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->par = par0;   // capture only recorded the launches
@@ -171,13 +203,14 @@ int capture_graph(daeti_ctx* c, cudaGraphExec_t* out) {
 int replay_graphs(daeti_ctx* c, int64_t& remaining, int64_t reserve, cudaStream_t st) {
     const int G = c->graph_steps;
     if (c->prof || G <= 0 || remaining - reserve < G) return DAETI_OK;
-    const int key = c->cur * 2 + c->par;
-    if (!c->graphs[key]) {
-        int rc = capture_graph(c, &c->graphs[key]);
-        if (rc) return rc;
-    }
     launch_set_counter(c->s.step_ctr, c->nstep, st);
     while (remaining - reserve >= G) {
+        const bool quiet = !stimulus_in_steps(c, c->nstep, G);
+        const int key = (c->cur * 2 + c->par) * 2 + (quiet ? 1 : 0);
+        if (!c->graphs[key]) {
+            int rc = capture_graph(c, &c->graphs[key], quiet);
+            if (rc) return rc;
+        }
         CK(cudaGraphLaunch(c->graphs[key], st));
         c->nstep += G;
         remaining -= G;

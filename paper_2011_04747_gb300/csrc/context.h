@@ -62,8 +62,9 @@ struct daeti_ctx {
     bool fused = true;          // last sub-step of step I inside the reaction launch
     bool lists = true;
     int graph_steps = 20;
-    // graphs of graph_steps steps, keyed by (start V buffer, list parity)
-    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    // graphs of graph_steps steps, keyed by (start V buffer, list parity,
+    // stimulus-free segment)
+    cudaGraphExec_t graphs[8] = {};
     // profiling
     bool prof = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     // the step counter, the stimuli and the list lengths in flight together.
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        const double t0 = (double)step_index(a.step) * a.dt;
+        const double t0 = a.n_stims ? (double)step_index(a.step) * a.dt : 0.0;   // only stimuli need it
         const bool on = lane < a.n_stims && stim_overlaps(a.stims[lane], t0, t0 + a.dt);
         const unsigned any = __ballot_sync(0xffffffffu, on);
         const int c = (a.lists && lane >= 1 && lane <= a.kmax) ? a.counts[lane] : 0;
