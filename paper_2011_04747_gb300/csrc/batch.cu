@@ -36,7 +36,7 @@ struct TissueInfoDev {
     long long off;
     int nx, ny, nz, dim;
     int coef_off;     // first class row of this tissue in the coefficient table
-    double vscale, vth;
+    double rate_scale, vth;   // (model units -> mV) / dt, activation threshold
 };
 
 struct daeti_batch {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev*
     if (KAHAN) cout[i] = cc;
     if (SYNC) {
         SyncParams<R> p = sp;
-        p.vscale = (R)t.vscale;
+        p.rate_scale = (R)t.rate_scale;
         p.vth = (R)t.vth;
         sync_node(p, i, v);
     }
@@ -126,7 +126,7 @@ void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t
     sp.n = (int)b->n_total;
     sp.flags = b->s_all.flags;
     sp.dt = b->dt;
-    sp.vscale = (R)1;
+    sp.rate_scale = (R)(1.0 / b->dt);
     sp.vth = (R)0;
     sp.kmax = b->kmax;
     sp.adaptive = b->sargs.adaptive;
@@ -358,7 +358,7 @@ int daeti_batch_prepare(daeti_batch* b) {
         info[t].nz = bt.dim == 3 ? (int)bt.n[2] : 1;
         info[t].dim = bt.dim;
         info[t].coef_off = (int)(A.size() / DAETI_ROW);
-        info[t].vscale = bt.model == DAETI_MODEL_MS ? 100.0 : 1.0;
+        info[t].rate_scale = (bt.model == DAETI_MODEL_MS ? 100.0 : 1.0) / b->dt;
         info[t].vth = std::isnan(b->opt.v_threshold) ? (bt.model == DAETI_MODEL_MS ? 0.5 : -40.0) : b->opt.v_threshold;
         const int self = 13;
         const size_t base = A.size();

@@ -150,7 +150,7 @@ struct SyncParams {
     int* flags;        // flags[0] |= 1 on non-finite V
     int* uflag;        // set when a node's k differs from the expected uniform k (mode -K)
     double dt;
-    R vscale;          // model units -> mV for the k rule
+    R rate_scale;      // (model units -> mV) / dt: dV/dt of the k rule in mV/ms per unit difference
     R vth;             // activation threshold
     int kmax;
     int adaptive;      // 0: k = 1 (OST)
@@ -164,7 +164,7 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
     R vold = p.vsync[i];
     int k = 1;
     if (p.adaptive) {
-        R rate = ((vnew - vold) / (R)p.dt) * p.vscale;
+        R rate = (vnew - vold) * p.rate_scale;
         int k0 = rate > (R)0 ? 5 : 1;
         R a = fabs(rate);
         a = a < (R)1e6 ? a : (R)1e6;          // also maps NaN to 1e6

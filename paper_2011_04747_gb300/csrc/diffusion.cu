@@ -120,7 +120,7 @@ static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef st
     sp.flags = s.flags;
     sp.uflag = s.flags + 2 + par;
     sp.dt = sa.dt;
-    sp.vscale = (R)sa.vscale;
+    sp.rate_scale = (R)(sa.vscale / sa.dt);
     sp.vth = (R)sa.vth;
     sp.kmax = sa.kmax;
     sp.adaptive = sa.adaptive;
