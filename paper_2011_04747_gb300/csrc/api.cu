@@ -129,28 +129,6 @@ void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bo
     }
 }
 
-// True if some stimulus window [t0 + p T, t0 + p T + dur) (with the 1e-9 ms
-// guard of the kernels, widened by 1e-6 ms here) meets the sub-step times
-// of steps n0 .. n0 + G - 1, i.e. [n0 dt, (n0 + G) dt).
-bool stimulus_in_steps(const daeti_ctx* c, int64_t n0, int64_t G) {
-    const double a = (double)n0 * c->dt_eff - 1e-6, b = (double)(n0 + G) * c->dt_eff + 1e-6;
-    for (const StimHost& s : c->stims) {
-        if (s.count <= 0) continue;
-        if (s.count == 1 || s.period <= 0.0) {
-            for (int p = 0; p < (s.period > 0.0 ? s.count : 1); ++p)
-                if (s.t0 + p * s.period < b && s.t0 + p * s.period + s.dur > a) return true;
-            continue;
-        }
-        // repetitions p with t0 + p T < b and t0 + p T + dur > a
-        const double lo = std::ceil((a - s.t0 - s.dur) / s.period - 1e-12);
-        const double hi = std::floor((b - s.t0) / s.period + 1e-12);
-        const double p0 = std::max(0.0, lo), p1 = std::min((double)(s.count - 1), hi);
-        for (double p = p0; p <= p1 && p <= p0 + 2.0; p += 1.0)
-            if (s.t0 + p * s.period < b && s.t0 + p * s.period + s.dur > a) return true;
-    }
-    return false;
-}
-
 void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
     Timer t(c, st, timed, 1);
     launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st,
@@ -205,7 +183,7 @@ int replay_graphs(daeti_ctx* c, int64_t& remaining, int64_t reserve, cudaStream_
     if (c->prof || G <= 0 || remaining - reserve < G) return DAETI_OK;
     launch_set_counter(c->s.step_ctr, c->nstep, st);
     while (remaining - reserve >= G) {
-        const bool quiet = !stimulus_in_steps(c, c->nstep, G);
+        const bool quiet = !stimulus_in_steps(c->stim_dev.data(), (int)c->stim_dev.size(), c->dt_eff, c->nstep, G);
         const int key = (c->cur * 2 + c->par) * 2 + (quiet ? 1 : 0);
         if (!c->graphs[key]) {
             int rc = capture_graph(c, &c->graphs[key], quiet);
@@ -721,6 +699,7 @@ int daeti_prepare(daeti_ctx* c) {
         CK(cpy_(c, p, mask.data(), 4 * N, cudaMemcpyHostToDevice));
         if ((rc = dalloc(c, &p, sizeof(StimDev) * sd.size()))) return rc;
         c->s.stims = (StimDev*)p;
+        c->stim_dev = sd;
         CK(cpy_(c, p, sd.data(), sizeof(StimDev) * sd.size(), cudaMemcpyHostToDevice));
         c->s.n_stims = (int)sd.size();
     }

@@ -61,7 +61,8 @@ struct daeti_batch {
     ReactTuning rtune;
     int64_t nstep = 0;
     int cur = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // steps with / without an open stimulus window
+    std::vector<StimDev> stim_dev;                     // host copy of the stimulus slots
     int graph_steps = 20;
     std::vector<void*> allocs;
 };
@@ -171,15 +172,19 @@ DevState pool_view(daeti_batch* b, bool ms) {
     return v;
 }
 
-void batch_step(daeti_batch* b, StepRef ref, cudaStream_t st) {
+// One step of every tissue (quiet: no stimulus window is open during it, so
+// the reaction launches are told there are no stimuli).
+void batch_step(daeti_batch* b, StepRef ref, cudaStream_t st, bool quiet = false) {
     int buf = b->cur;
     for (int i = 0; i < b->l; ++i) {
         batch_diffuse_any(b, buf, false, ref, st);
         buf ^= 1;
     }
     DiffOp none;
-    if (b->n_ms) launch_reaction(pool_view(b, true), b->ms_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
-    if (b->n_tp) launch_reaction(pool_view(b, false), b->tp_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
+    DevState ms = pool_view(b, true), tp = pool_view(b, false);
+    if (quiet) ms.n_stims = tp.n_stims = 0;
+    if (b->n_ms) launch_reaction(ms, b->ms_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
+    if (b->n_tp) launch_reaction(tp, b->tp_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
     for (int i = 0; i < b->l; ++i) {
         batch_diffuse_any(b, buf, i == b->l - 1, ref, st);
         buf ^= 1;
@@ -244,7 +249,8 @@ int daeti_batch_create(daeti_batch** out, const daeti_options* opt) {
 int daeti_batch_destroy(daeti_batch* b) {
     if (!b) return DAETI_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int q = 0; q < 2; ++q)
+        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
     for (void* p : b->allocs) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -425,6 +431,7 @@ int daeti_batch_prepare(daeti_batch* b) {
         s.stims = (StimDev*)p;
         BCK(cudaMemcpyAsync(p, sd.data(), sizeof(StimDev) * sd.size(), cudaMemcpyHostToDevice, b->stream));
         s.n_stims = (int)sd.size();
+        b->stim_dev = sd;
     }
     if ((rc = balloc(b, &b->coef, R * A.size()))) return rc;
     if ((rc = bupload(b, b->coef, A.data(), (int64_t)A.size()))) return rc;
@@ -486,22 +493,25 @@ int daeti_batch_advance(daeti_batch* b, double t_end) {
     int64_t remaining = target - b->nstep;
     const int G = b->graph_steps;
     if (G > 0 && remaining >= G) {
-        if (!b->graph) {
-            cudaGraph_t g = nullptr;
-            BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-            for (int j = 0; j < G; ++j) batch_step(b, StepRef{b->s_all.step_ctr, (long long)j}, b->cap_stream);
-            launch_tick(b->s_all.step_ctr, G, b->cap_stream);
-            BCK(cudaStreamEndCapture(b->cap_stream, &g));
-            cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                b->graph = nullptr;
-                return bfail(b, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-            }
-        }
         launch_set_counter(b->s_all.step_ctr, b->nstep, b->stream);
         while (remaining >= G) {
-            BCK(cudaGraphLaunch(b->graph, b->stream));
+            const int quiet =
+                !stimulus_in_steps(b->stim_dev.data(), (int)b->stim_dev.size(), b->dt, b->nstep, G) ? 1 : 0;
+            if (!b->graph[quiet]) {
+                cudaGraph_t g = nullptr;
+                BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+                for (int j = 0; j < G; ++j)
+                    batch_step(b, StepRef{b->s_all.step_ctr, (long long)j}, b->cap_stream, quiet != 0);
+                launch_tick(b->s_all.step_ctr, G, b->cap_stream);
+                BCK(cudaStreamEndCapture(b->cap_stream, &g));
+                cudaError_t e = cudaGraphInstantiate(&b->graph[quiet], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    b->graph[quiet] = nullptr;
+                    return bfail(b, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+                }
+            }
+            BCK(cudaGraphLaunch(b->graph[quiet], b->stream));
             b->nstep += G;
             remaining -= G;
         }

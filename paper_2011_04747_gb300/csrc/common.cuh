@@ -178,7 +178,7 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
         p.act[i] = (R)(tprev + p.dt * (double)((p.vth - vold) / (vnew - vold)));
     }
     p.vsync[i] = vnew;
-    if (!isfinite((double)vnew)) atomicOr(p.flags, 1);
+    if (!isfinite(vnew)) atomicOr(p.flags, 1);
     return k;
 }
 

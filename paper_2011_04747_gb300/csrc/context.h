@@ -62,6 +62,7 @@ struct daeti_ctx {
     bool fused = true;          // last sub-step of step I inside the reaction launch
     bool lists = true;
     int graph_steps = 20;
+    std::vector<StimDev> stim_dev;   // host copy of the device stimulus table
     // graphs of graph_steps steps, keyed by (start V buffer, list parity,
     // stimulus-free segment)
     cudaGraphExec_t graphs[8] = {};

@@ -1,6 +1,8 @@
 // Host-visible launch interface of the libdaeti kernels (no device code).
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -63,6 +65,28 @@ struct DiffOp {
     void* val = nullptr;            // off-diagonal dt_ad K_ij / m_i
     int64_t nnz_padded = 0;
 };
+
+// True if some stimulus window [t0 + p T, t0 + p T + dur) (the kernels test
+// sub-step start times with a 1e-9 ms guard; widened by 1e-6 ms here) meets
+// the sub-step times of steps n0 .. n0 + G - 1, i.e. [n0 dt, (n0 + G) dt).
+// A launch for steps where this is false may be told there are no stimuli.
+inline bool stimulus_in_steps(const StimDev* st, int n, double dt, int64_t n0, int64_t G) {
+    const double a = (double)n0 * dt - 1e-6, b = (double)(n0 + G) * dt + 1e-6;
+    for (int q = 0; q < n; ++q) {
+        const StimDev& s = st[q];
+        if (s.reps <= 0) continue;
+        const int reps = s.period > 0.0 ? s.reps : 1;
+        // repetitions p with t0 + p T < b and t0 + p T + dur > a
+        double p0 = 0.0, p1 = (double)(reps - 1);
+        if (reps > 1) {
+            p0 = std::max(p0, std::ceil((a - s.t0 - s.dur) / s.period) - 1.0);
+            p1 = std::min(p1, std::floor((b - s.t0) / s.period) + 1.0);
+        }
+        for (double p = p0; p <= p1; p += 1.0)
+            if (s.t0 + p * s.period < b && s.t0 + p * s.period + s.dur > a) return true;
+    }
+    return false;
+}
 
 // Cell states other than V are stored in chunks of 32 nodes: state s (of ns)
 // of node i sits at ((i / 32) * ns + s) * 32 + i % 32.  A thread's states are

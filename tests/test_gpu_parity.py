@@ -277,3 +277,27 @@ def test_substep_count_equals_the_oracle_sum_of_k(graph_steps):
     s.close()
     assert total > n_steps * wl.n_nodes          # k > 1 somewhere
     assert got == total
+
+
+@pytest.mark.parametrize("precision", ["fp32_kahan", "fp64"])
+def test_graph_segments_without_stimulus_keep_every_pulse(precision):
+    """Graph segments in which no stimulus window is open launch the reaction
+    without stimuli; a pacing train whose pulses start inside, across and
+    between 20-step segments gives the same state as plain launches, which
+    test every window."""
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = I.ms_square_2d(n=21)
+    st = wl.stimuli[0]
+    # pulses of 0.35 ms every 3.7 ms from 0.55 ms: start and end at every
+    # offset against the 2 ms (20-step) segments
+    st.t_start, st.duration, st.period, st.count, st.amplitude = 0.55, 0.35, 3.7, 12, 3.0
+    out = []
+    for graph_steps in (20, 0):
+        s = binding.solver_from_workload(wl, precision=precision, graph_steps=graph_steps)
+        s.daeti_advance(50.0)
+        out.append((s.daeti_read_state(), s.daeti_read_activation()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert (out[0][1] >= 0).any()
