@@ -835,7 +835,8 @@ int daeti_advance(daeti_ctx* c, double t_end) {
     while (remaining > 0) {
         if ((rc = replay_graphs(c, remaining, 0, st))) return rc;
         if (remaining > 0) {
-            enqueue_step(c, plain_ref(c->nstep), st, timed);
+            const bool quiet = !stimulus_in_steps(c->stim_dev.data(), (int)c->stim_dev.size(), c->dt_eff, c->nstep, 1);
+            enqueue_step(c, plain_ref(c->nstep), st, timed, quiet);
             c->nstep++;
             remaining--;
         }
