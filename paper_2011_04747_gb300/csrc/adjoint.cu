@@ -164,19 +164,24 @@ __global__ void adj_react_bwd(AdjReactArgs<R> a, const R* __restrict__ rv, const
         }
         R lv = mu[i] * m[i];
         R lh = lamh[i];
+        // this node's share of dL/dtau_close in the state precision (at most
+        // k_max terms), added to the double block sum once
+        const R tau_fac = dt * a.r_close * a.r_close;
+        R gn = (R)0;
 #pragma unroll 1
         for (int s = k - 1; s >= 0; --s) {
             const R vi = vs[s], hi = hs[s];
             const R fv = hi * ((R)2 * vi - (R)3 * vi * vi) * a.r_in - a.r_out;
             const R fh = vi * vi * ((R)1 - vi) * a.r_in;
             const R gh = lows[s] ? -a.r_open : -a.r_close;
-            if (!lows[s]) gt += (double)lh * (double)dt * (double)hi * (double)a.r_close * (double)a.r_close;
+            if (!lows[s]) gn += lh * hi * tau_fac;
             const R nlv = ((R)1 + dt * fv) * lv;
             lh = dt * fh * lv + ((R)1 + dt * gh) * lh;
             lv = nlv;
         }
         mu[i] = lv / m[i];
         lamh[i] = lh;
+        gt = (double)gn;
     }
     for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gt;
@@ -188,14 +193,16 @@ __global__ void adj_react_bwd(AdjReactArgs<R> a, const R* __restrict__ rv, const
     }
 }
 
-struct Kref {
-    double k[64];
+template <typename R>
+struct KrefR {
+    R k[64];
 };
 
-// dL/dD_e += -dt_ad mu_out^T K_e v_in on element e of a structured grid.
+// dL/dD_e += -dt_ad mu_out^T K_e v_in on element e of a structured grid (the
+// element product in the state precision, the sum over steps in double).
 template <typename R>
 __global__ void adj_dgrad(int64_t n_elem, int dim, int nx, int ny, const R* __restrict__ mu,
-                          const R* __restrict__ vin, double dt_ad, Kref kr, double* g) {
+                          const R* __restrict__ vin, double dt_ad, KrefR<R> kr, double* g) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n_elem) return;
     const int ex = (int)(e % (nx - 1));
@@ -206,13 +213,13 @@ __global__ void adj_dgrad(int64_t n_elem, int dim, int nx, int ny, const R* __re
     int node[8];
     for (int a = 0; a < nl; ++a)
         node[a] = (ex + (a & 1)) + nx * ((ey + ((a >> 1) & 1)) + ny * (ez + ((a >> 2) & 1)));
-    double s = 0.0;
+    R s = (R)0;
     for (int a = 0; a < nl; ++a) {
-        double r = 0.0;
-        for (int b = 0; b < nl; ++b) r += kr.k[a * nl + b] * (double)vin[node[b]];
-        s += (double)mu[node[a]] * r;
+        R r = (R)0;
+        for (int b = 0; b < nl; ++b) r = fma(kr.k[a * nl + b], vin[node[b]], r);
+        s = fma(mu[node[a]], r, s);
     }
-    g[e] += -dt_ad * s;
+    g[e] += -dt_ad * (double)s;
 }
 
 template <typename R>
@@ -402,8 +409,8 @@ struct Adj {
 
     template <typename T>
     void dgrad(const void* vin) {
-        Kref kr;
-        std::memcpy(kr.k, c->kref, sizeof(kr.k));
+        KrefR<T> kr;
+        for (int q = 0; q < 64; ++q) kr.k[q] = (T)c->kref[q];
         const int64_t ne = c->n_elem;
         adj_dgrad<T><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, c->dim, (int)c->n[0], (int)c->n[1],
                                                                    (const T*)b->mu[mu_cur], (const T*)vin,
