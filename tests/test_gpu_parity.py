@@ -293,6 +293,11 @@ def test_graph_segments_without_stimulus_keep_every_pulse(precision):
     # pulses of 0.35 ms every 3.7 ms from 0.55 ms: start and end at every
     # offset against the 2 ms (20-step) segments
     st.t_start, st.duration, st.period, st.count, st.amplitude = 0.55, 0.35, 3.7, 12, 3.0
+    # windows that start and end exactly on segment boundaries, one that fills
+    # a whole segment, and one ending on a boundary
+    edge = wl.stimuli[0].nodes[:3]
+    wl.stimuli = wl.stimuli + [I.Stimulus(edge, 4.0, 2.0, 3.0), I.Stimulus(edge, 9.6, 0.4, 3.0),
+                               I.Stimulus(edge, 20.0, 0.1, 3.0, period=2.0, count=5)]
     out = []
     for graph_steps in (20, 0):
         s = binding.solver_from_workload(wl, precision=precision, graph_steps=graph_steps)
