@@ -55,6 +55,7 @@ struct daeti_batch {
     void* S_tp = nullptr;
     void* coef = nullptr;
     int* tid = nullptr;
+    uint32_t* rows = nullptr;        // stencil table row of each node (tissue offset included)
     TissueInfoDev* info = nullptr;
     ModelArgs ms_args, tp_args;
     SyncArgs sargs;
@@ -82,30 +83,29 @@ int bfail(daeti_batch* b, int code, const std::string& msg) {
                          std::string(#call) + ": " + cudaGetErrorString(e_));                      \
     } while (0)
 
+// One diffusion sub-step of every tissue.  V buffers carry a zeroed ghost
+// margin wider than the largest tissue's stencil reach, and out-of-tissue
+// offsets have coefficient 0 in each tissue's table, so a neighbour read past
+// a tissue's edge (the next tissue or the margin) adds exactly 0 and no
+// boundary test is needed; the node's table row is precomputed.
 template <typename R, bool KAHAN, bool SYNC>
 __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev* __restrict__ info,
-                                                           const int* __restrict__ tid, int n, const R* __restrict__ vin,
-                                                           R* vout, const float* cin, float* cout,
-                                                           const R* __restrict__ coef, SyncParams<R> sp) {
+                                                           const int* __restrict__ tid,
+                                                           const uint32_t* __restrict__ rows, int n,
+                                                           const R* __restrict__ vin, R* vout, const float* cin,
+                                                           float* cout, const R* __restrict__ coef, SyncParams<R> sp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const TissueInfoDev t = info[tid[i]];
-    const int local = i - (int)t.off;
-    const int x = local % t.nx;
-    const int yz = local / t.nx;
-    const int y = yz % t.ny;
-    const int z = yz / t.ny;
-    const int cx = x == 0 ? 0 : (x == t.nx - 1 ? 2 : 1);
-    const int cy = y == 0 ? 0 : (y == t.ny - 1 ? 2 : 1);
-    const R* crow = coef + ((size_t)t.coef_off + (size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
+    const R* crow = coef + (size_t)rows[i] * DAETI_ROW;
     const int nx = t.nx, nxy = t.nx * t.ny;
     auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
     R v;
     float cc;
     if (t.dim == 3)
-        stencil_update<R, 3, KAHAN>(crow, cx, cy, z, t.nz, vin[i], KAHAN ? cin[i] : 0.f, fetch, v, cc);
+        stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, vin[i], KAHAN ? cin[i] : 0.f, fetch, v, cc);
     else
-        stencil_update<R, 2, KAHAN>(crow, cx, cy, z, t.nz, vin[i], KAHAN ? cin[i] : 0.f, fetch, v, cc);
+        stencil_update<R, 2, KAHAN, true>(crow, 1, 1, 0, 1, vin[i], KAHAN ? cin[i] : 0.f, fetch, v, cc);
     vout[i] = v;
     if (KAHAN) cout[i] = cc;
     if (SYNC) {
@@ -139,11 +139,11 @@ void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t
     const float* cin = KAHAN ? b->s_all.C[src] : nullptr;
     float* cout = KAHAN ? b->s_all.C[1 - src] : nullptr;
     if (sync)
-        batch_substep_kernel<R, KAHAN, true><<<grid, 256, 0, st>>>(b->info, b->tid, n, vin, vout, cin, cout,
-                                                                  (const R*)b->coef, sp);
+        batch_substep_kernel<R, KAHAN, true><<<grid, 256, 0, st>>>(b->info, b->tid, b->rows, n, vin, vout, cin,
+                                                                  cout, (const R*)b->coef, sp);
     else
-        batch_substep_kernel<R, KAHAN, false><<<grid, 256, 0, st>>>(b->info, b->tid, n, vin, vout, cin, cout,
-                                                                   (const R*)b->coef, sp);
+        batch_substep_kernel<R, KAHAN, false><<<grid, 256, 0, st>>>(b->info, b->tid, b->rows, n, vin, vout, cin,
+                                                                   cout, (const R*)b->coef, sp);
 }
 
 void batch_diffuse_any(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t st) {
@@ -407,7 +407,16 @@ int daeti_batch_prepare(daeti_batch* b) {
     const size_t R = s.prec == P_F64 ? 8 : 4;
     int rc;
     void* p;
-    if ((rc = balloc(b, &s.V[0], R * N)) || (rc = balloc(b, &s.V[1], R * N))) return rc;
+    // V with a zeroed ghost margin of the largest stencil reach on both sides
+    int64_t pad = 0;
+    for (const BatchTissue& bt : b->tissues)
+        pad = std::max<int64_t>(pad, 1 + bt.n[0] + (bt.dim == 3 ? bt.n[0] * bt.n[1] : 0));
+    for (int q = 0; q < 2; ++q) {
+        if ((rc = balloc(b, &p, R * (N + 2 * pad)))) return rc;
+        BCK(cudaMemsetAsync(p, 0, R * (N + 2 * pad), b->stream));
+        s.V[q] = (char*)p + R * pad;
+    }
+    s.vpad = pad;
     if (s.kahan) {
         if ((rc = balloc(b, &p, 4 * N))) return rc;
         s.C[0] = (float*)p;
@@ -436,14 +445,26 @@ int daeti_batch_prepare(daeti_batch* b) {
     if ((rc = balloc(b, &b->coef, R * A.size()))) return rc;
     if ((rc = bupload(b, b->coef, A.data(), (int64_t)A.size()))) return rc;
     std::vector<int> tid(N);
+    std::vector<uint32_t> rows(N);
     for (int t = 0; t < T; ++t) {
         const BatchTissue& bt = b->tissues[t];
-        const int64_t nn = bt.n[0] * bt.n[1] * (bt.dim == 3 ? bt.n[2] : 1);
-        std::fill(tid.begin() + b->off[t], tid.begin() + b->off[t] + nn, t);
+        const int64_t nx = bt.n[0], ny = bt.n[1], nz = bt.dim == 3 ? bt.n[2] : 1;
+        std::fill(tid.begin() + b->off[t], tid.begin() + b->off[t] + nx * ny * nz, t);
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
+                for (int64_t x = 0; x < nx; ++x) {
+                    const int cx = x == 0 ? 0 : (x == nx - 1 ? 2 : 1);
+                    const int cy = y == 0 ? 0 : (y == ny - 1 ? 2 : 1);
+                    rows[b->off[t] + (z * ny + y) * nx + x] = (uint32_t)(info[t].coef_off + (z * 3 + cy) * 3 + cx);
+                }
     }
     if ((rc = balloc(b, &p, 4 * N))) return rc;
     b->tid = (int*)p;
     BCK(cudaMemcpyAsync(p, tid.data(), 4 * N, cudaMemcpyHostToDevice, b->stream));
+    if ((rc = balloc(b, &p, 4 * N))) return rc;
+    b->rows = (uint32_t*)p;
+    BCK(cudaMemcpyAsync(p, rows.data(), 4 * N, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
     if ((rc = balloc(b, &p, sizeof(TissueInfoDev) * T))) return rc;
     b->info = (TissueInfoDev*)p;
     BCK(cudaMemcpyAsync(p, info.data(), sizeof(TissueInfoDev) * T, cudaMemcpyHostToDevice, b->stream));
