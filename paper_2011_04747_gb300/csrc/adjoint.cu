@@ -109,16 +109,14 @@ __device__ __forceinline__ R adj_stim(unsigned mask, const StimDev* stims, doubl
     return J;
 }
 
-// Step A of the adjoint's forward: MODE 0 decide, 1 decide and record, 2 replay.
+// Step A of the adjoint's forward at node i on (v, c): MODE 0 decide, 1 decide
+// and record, 2 replay.  h is read from a.H and written to a.Ho.
 template <typename R, bool KAHAN, int MODE>
-__global__ void adj_react_fwd(AdjReactArgs<R> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+__device__ __forceinline__ void react_node(const AdjReactArgs<R>& a, int i, R& v, float& c) {
     const int k = MODE == 2 ? a.hist_k[i] : a.kk[i];
     const unsigned smask = a.n_stims ? a.stim_mask[i] : 0u;
     const uint16_t rb = MODE == 2 ? a.hist_b[i] : 0;
-    R v = a.V[i], h = a.H[i];
-    float c = KAHAN ? a.C[i] : 0.f;
+    R h = a.H[i];
     float* cp = KAHAN ? &c : nullptr;
     uint16_t bits = 0;
     for (int s = 0; s < k; ++s) {
@@ -127,13 +125,32 @@ __global__ void adj_react_fwd(AdjReactArgs<R> a) {
         bits |= (uint16_t)(low ? 1u << s : 0u);
         ms_substep_b(v, cp, h, a.dtkr[k], J, a.r_in, a.r_out, a.r_open, a.r_close, low);
     }
-    a.Vo[i] = v;
     a.Ho[i] = h;
-    if (KAHAN) a.Co[i] = c;
     if (MODE == 1) {
         a.hist_k[i] = (uint8_t)k;
         a.hist_b[i] = bits;
     }
+}
+
+// The last step-I diffusion sub-step and step A in one launch: node i's
+// diffused value feeds its own reaction directly.  With vmid the diffused
+// value (the reaction's input) is stored as well.
+template <typename R, bool KAHAN, int MODE, int DIM>
+__global__ void __launch_bounds__(128) adj_diff_react_fwd(OpView<R> op, AdjReactArgs<R> a, const R* __restrict__ vin,
+                                                          const float* __restrict__ cin, R* vmid, float* cmid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    R v;
+    float c;
+    diffuse_node<R, DIM, KAHAN>(op, vin, cin, i, v, c);
+    if (!KAHAN) c = 0.f;
+    if (vmid) {
+        vmid[i] = v;
+        if (KAHAN) cmid[i] = c;
+    }
+    react_node<R, KAHAN, MODE>(a, i, v, c);
+    a.Vo[i] = v;
+    if (KAHAN) a.Co[i] = c;
 }
 
 // Reverse of step A per node: recompute the sub-steps, then transpose them.
@@ -201,10 +218,8 @@ struct KrefR {
 // dL/dD_e += -dt_ad mu_out^T K_e v_in on element e of a structured grid (the
 // element product in the state precision, the sum over steps in double).
 template <typename R>
-__global__ void adj_dgrad(int64_t n_elem, int dim, int nx, int ny, const R* __restrict__ mu,
-                          const R* __restrict__ vin, double dt_ad, KrefR<R> kr, double* g) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n_elem) return;
+__device__ __forceinline__ void elem_dgrad(int64_t e, int dim, int nx, int ny, const R* __restrict__ mu,
+                                           const R* __restrict__ vin, double dt_ad, const KrefR<R>& kr, double* g) {
     const int ex = (int)(e % (nx - 1));
     const int64_t t = e / (nx - 1);
     const int ey = (int)(t % (ny - 1));
@@ -220,6 +235,24 @@ __global__ void adj_dgrad(int64_t n_elem, int dim, int nx, int ny, const R* __re
         s = fma(mu[node[a]], r, s);
     }
     g[e] += -dt_ad * (double)s;
+}
+
+// One transposed diffusion sub-step on the costate, mu_out = (I - dt_ad M^-1 K) mu_in
+// (thread t: node t), and in the same launch the element products of that
+// sub-step (thread t: element t); both read mu_in only.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(256) adj_mu_dgrad(OpView<R> op, int n, const R* __restrict__ mu_in,
+                                                    R* __restrict__ mu_out, int64_t n_elem, int dim, int nx,
+                                                    int ny, const R* __restrict__ vin, double dt_ad, KrefR<R> kr,
+                                                    double* g) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) {
+        R v;
+        float cc;
+        diffuse_node<R, DIM, false>(op, mu_in, nullptr, (int)t, v, cc);
+        mu_out[t] = v;
+    }
+    if (t < n_elem) elem_dgrad<R>(t, dim, nx, ny, mu_in, vin, dt_ad, kr, g);
 }
 
 template <typename R>
@@ -243,7 +276,58 @@ __global__ void adj_loss_inject(int n_s, const int* __restrict__ sensors, const 
     }
 }
 
+// Checkpoint save / restore: up to six arrays copied in one launch, each in
+// the widest word (16, 8, 4 or 1 bytes) its addresses and length allow.
+struct CopyList {
+    void* dst[6];
+    const void* src[6];
+    int64_t words[6];
+    int width[6];
+    int n;
+};
+
+template <typename W>
+__device__ __forceinline__ void copy_words(void* d, const void* s, int64_t n, int64_t t, int64_t stride) {
+    W* dw = (W*)d;
+    const W* sw = (const W*)s;
+    for (int64_t i = t; i < n; i += stride) dw[i] = sw[i];
+}
+
+__global__ void adj_copy_arrays(CopyList L) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int q = 0; q < L.n; ++q) {
+        switch (L.width[q]) {
+            case 16: copy_words<uint4>(L.dst[q], L.src[q], L.words[q], t, stride); break;
+            case 8: copy_words<uint2>(L.dst[q], L.src[q], L.words[q], t, stride); break;
+            case 4: copy_words<unsigned>(L.dst[q], L.src[q], L.words[q], t, stride); break;
+            default: copy_words<uint8_t>(L.dst[q], L.src[q], L.words[q], t, stride); break;
+        }
+    }
+}
+
 // --------------------------------------------------------------- host side
+struct CopyBuilder {
+    CopyList L{};
+    int64_t max_words = 0;
+    void add(void* dst, const void* src, size_t bytes) {
+        if (!dst || !src || !bytes) return;
+        const uintptr_t a = (uintptr_t)dst | (uintptr_t)src | (uintptr_t)bytes;
+        const int w = (a & 15) == 0 ? 16 : (a & 7) == 0 ? 8 : (a & 3) == 0 ? 4 : 1;
+        const int q = L.n++;
+        L.dst[q] = dst;
+        L.src[q] = src;
+        L.width[q] = w;
+        L.words[q] = (int64_t)(bytes / (size_t)w);
+        max_words = std::max(max_words, L.words[q]);
+    }
+    void launch(cudaStream_t st) const {
+        if (!L.n) return;
+        const int64_t blocks = std::min<int64_t>((max_words + 255) / 256, 4 * 152);
+        adj_copy_arrays<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(L);
+    }
+};
+
 template <typename R>
 AdjReactArgs<R> react_args(daeti_ctx* c, int buf, int64_t step, uint8_t* hk, uint16_t* hb) {
     AdjReactArgs<R> a;
@@ -283,48 +367,72 @@ struct Adj {
     int mode;            // 0 decide, 1 record, 2 replay
     int mu_cur = 0;
     int64_t fwd_steps = 0;
+    int live_slot = -1;  // checkpoint slot the live state still equals (-1: none)
     size_t R() const { return rsize(c); }
-
-    void copy(void* dst, const void* src, size_t bytes) { cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st); }
 
     void save(int slot, int64_t step) {
         const size_t N = c->n_nodes, r = R();
-        copy(b->sV[slot], c->s.V[c->cur], N * r);
-        if (b->kahan) copy(b->sC[slot], c->s.C[c->cur], N * 4);
-        copy(b->sH[slot], c->s.S, N * r);
-        copy(b->sVs[slot], c->s.vsync, N * r);
-        copy(b->sA[slot], c->s.act, N * r);
-        copy(b->sK[slot], c->s.kk, N);
+        CopyBuilder cb;
+        cb.add(b->sV[slot], c->s.V[c->cur], N * r);
+        if (b->kahan) cb.add(b->sC[slot], c->s.C[c->cur], N * 4);
+        cb.add(b->sH[slot], c->s.S, N * r);
+        cb.add(b->sVs[slot], c->s.vsync, N * r);
+        cb.add(b->sA[slot], c->s.act, N * r);
+        cb.add(b->sK[slot], c->s.kk, N);
+        cb.launch(st);
         b->slot_step[slot] = step;
+        live_slot = slot;
     }
+    // The binomial recursion restores a checkpoint right after saving it; the
+    // live state is then unchanged and the copy is skipped.
     void restore(int slot) {
+        if (live_slot == slot) return;
         const size_t N = c->n_nodes, r = R();
-        copy(c->s.V[c->cur], b->sV[slot], N * r);
-        if (b->kahan) copy(c->s.C[c->cur], b->sC[slot], N * 4);
-        copy(c->s.S, b->sH[slot], N * r);
-        copy(c->s.vsync, b->sVs[slot], N * r);
-        copy(c->s.act, b->sA[slot], N * r);
-        copy(c->s.kk, b->sK[slot], N);
+        CopyBuilder cb;
+        cb.add(c->s.V[c->cur], b->sV[slot], N * r);
+        if (b->kahan) cb.add(c->s.C[c->cur], b->sC[slot], N * 4);
+        cb.add(c->s.S, b->sH[slot], N * r);
+        cb.add(c->s.vsync, b->sVs[slot], N * r);
+        cb.add(c->s.act, b->sA[slot], N * r);
+        cb.add(c->s.kk, b->sK[slot], N);
+        cb.launch(st);
+        live_slot = slot;
     }
 
+    // The last step-I diffusion sub-step (vin, cin -> the reaction's input,
+    // stored to vmid, cmid when given) and step A of step j in one launch.
     template <typename T, bool K>
-    void react_fwd(int buf, int64_t j, void* vin = nullptr, float* cin = nullptr, void* vout = nullptr,
-                   float* cout = nullptr, void* hout = nullptr) {
+    void diff_react(int64_t j, const void* vin, const float* cin, void* vmid, float* cmid, void* vout, float* cout,
+                    void* hout) {
         const int n = (int)c->n_nodes;
         uint8_t* hk = b->hist_k ? b->hist_k + (size_t)j * n : nullptr;
         uint16_t* hb = b->hist_b ? b->hist_b + (size_t)j * n : nullptr;
-        AdjReactArgs<T> a = react_args<T>(c, buf, n0 + j, hk, hb);
-        if (vin) {
-            a.V = (T*)vin;
-            a.C = cin;
-            a.Vo = (T*)vout;
-            a.Co = cout;
-            a.Ho = (T*)hout;
-        }
-        const int grid = (n + 127) / 128;
-        if (mode == 2) adj_react_fwd<T, K, 2><<<grid, 128, 0, st>>>(a);
-        else if (mode == 1) adj_react_fwd<T, K, 1><<<grid, 128, 0, st>>>(a);
-        else adj_react_fwd<T, K, 0><<<grid, 128, 0, st>>>(a);
+        AdjReactArgs<T> a = react_args<T>(c, c->cur, n0 + j, hk, hb);
+        a.V = nullptr;
+        a.C = nullptr;
+        a.Vo = (T*)vout;
+        a.Co = cout;
+        a.Ho = (T*)hout;
+        const int dim = c->op.kind == 1 ? 0 : c->op.dim;
+        if (dim == 0) diff_react_dim<T, K, 0>(a, vin, cin, vmid, cmid);
+        else if (dim == 2) diff_react_dim<T, K, 2>(a, vin, cin, vmid, cmid);
+        else diff_react_dim<T, K, 3>(a, vin, cin, vmid, cmid);
+    }
+    template <typename T, bool K, int DIM>
+    void diff_react_dim(const AdjReactArgs<T>& a, const void* vin, const float* cin, void* vmid, float* cmid) {
+        const OpView<T> op = op_view<T>(c->op);
+        const int grid = (a.n + 127) / 128;
+        const T* vi = (const T*)vin;
+        T* vm = (T*)vmid;
+        if (mode == 2) adj_diff_react_fwd<T, K, 2, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
+        else if (mode == 1) adj_diff_react_fwd<T, K, 1, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
+        else adj_diff_react_fwd<T, K, 0, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
+    }
+    void diff_react_any(int64_t j, const void* vin, const float* cin, void* vmid, float* cmid, void* vout,
+                        float* cout, void* hout) {
+        if (c->s.prec == P_F64) diff_react<double, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout);
+        else if (c->s.kahan) diff_react<float, true>(j, vin, cin, vmid, cmid, vout, cout, hout);
+        else diff_react<float, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout);
     }
 
     // One diffusion sub-step from `in` to `out` (and the Kahan terms), with the
@@ -347,41 +455,39 @@ struct Adj {
     // checkpoint afterwards).
     void fwd_step(int64_t j, bool store) {
         const StepRef ref{nullptr, (long long)(n0 + j)};
+        live_slot = -1;
+        const int l = c->l;
         if (!store) {
             int buf = c->cur;
-            for (int i = 0; i < c->l; ++i) {
+            for (int i = 0; i < l - 1; ++i) {
                 launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
                 buf ^= 1;
             }
-            if (c->s.prec == P_F64) react_fwd<double, false>(buf, j);
-            else if (c->s.kahan) react_fwd<float, true>(buf, j);
-            else react_fwd<float, false>(buf, j);
-            for (int i = 0; i < c->l; ++i) {
-                launch_diffusion(c->s, c->op, buf, i == c->l - 1, 0, c->sargs, ref, false, 256, st);
+            diff_react_any(j, c->s.V[buf], c->s.C[buf], nullptr, nullptr, c->s.V[buf ^ 1], c->s.C[buf ^ 1], c->s.S);
+            buf ^= 1;
+            for (int i = 0; i < l; ++i) {
+                launch_diffusion(c->s, c->op, buf, i == l - 1, 0, c->sargs, ref, false, 256, st);
                 buf ^= 1;
             }
             ++fwd_steps;
             return;
         }
-        const int l = c->l;
         const void* x = c->s.V[c->cur];
         const float* cx = b->kahan ? c->s.C[c->cur] : nullptr;
-        for (int i = 0; i < l; ++i) {
+        for (int i = 0; i < l - 1; ++i) {
             b->d1[i] = x;
             diffuse_view(x, b->P[i], cx, b->kahan ? b->CP[i] : nullptr, false, ref, nullptr);
             x = b->P[i];
             cx = b->kahan ? b->CP[i] : nullptr;
         }
-        b->rv = x;
-        b->rc = cx;
+        b->d1[l - 1] = x;
+        b->rv = b->P[l - 1];
+        b->rc = b->kahan ? b->CP[l - 1] : nullptr;
         b->rh = c->s.S;
         b->kused = c->s.kk;
         void* y = b->P[l];
         float* cy = b->kahan ? b->CP[l] : nullptr;
-        if (c->s.prec == P_F64) react_fwd<double, false>(c->cur, j, const_cast<void*>(x), nullptr, y, nullptr, b->Hout);
-        else if (c->s.kahan)
-            react_fwd<float, true>(c->cur, j, const_cast<void*>(x), const_cast<float*>(cx), y, cy, b->Hout);
-        else react_fwd<float, false>(c->cur, j, const_cast<void*>(x), nullptr, y, nullptr, b->Hout);
+        diff_react_any(j, x, cx, b->P[l - 1], b->kahan ? b->CP[l - 1] : nullptr, y, cy, b->Hout);
         const void* yi = y;
         const float* cyi = cy;
         for (int i = 0; i < l; ++i) {
@@ -407,24 +513,27 @@ struct Adj {
                                               (T*)b->mu[mu_cur], b->acc, inject ? 1 : 0);
     }
 
+    // Reverse of one diffusion sub-step whose input was vin: gradient products, then mu <- D mu.
     template <typename T>
-    void dgrad(const void* vin) {
+    void mu_step(const void* vin) {
         KrefR<T> kr;
         for (int q = 0; q < 64; ++q) kr.k[q] = (T)c->kref[q];
+        const OpView<T> op = op_view<T>(c->op);
+        const int n = (int)c->n_nodes;
         const int64_t ne = c->n_elem;
-        adj_dgrad<T><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, c->dim, (int)c->n[0], (int)c->n[1],
-                                                                   (const T*)b->mu[mu_cur], (const T*)vin,
-                                                                   c->dt_ad, kr, b->g_elem);
-    }
-
-    void mu_substep() {
-        DevState view = c->s;
-        view.vpad = 0;
-        view.V[0] = b->mu[0];
-        view.V[1] = b->mu[1];
-        view.C[0] = view.C[1] = nullptr;
-        view.kahan = false;
-        launch_diffusion(view, c->op, mu_cur, false, 0, c->sargs, StepRef{nullptr, 0}, false, 256, st);
+        const unsigned grid = (unsigned)((std::max<int64_t>(n, ne) + 255) / 256);
+        const int nx = (int)c->n[0], ny = (int)c->n[1];
+        const T* mi = (const T*)b->mu[mu_cur];
+        T* mo = (T*)b->mu[mu_cur ^ 1];
+        if (c->op.kind == 1)
+            adj_mu_dgrad<T, 0><<<grid, 256, 0, st>>>(op, n, mi, mo, ne, c->dim, nx, ny, (const T*)vin, c->dt_ad, kr,
+                                                     b->g_elem);
+        else if (c->op.dim == 2)
+            adj_mu_dgrad<T, 2><<<grid, 256, 0, st>>>(op, n, mi, mo, ne, c->dim, nx, ny, (const T*)vin, c->dt_ad, kr,
+                                                     b->g_elem);
+        else
+            adj_mu_dgrad<T, 3><<<grid, 256, 0, st>>>(op, n, mi, mo, ne, c->dim, nx, ny, (const T*)vin, c->dt_ad, kr,
+                                                     b->g_elem);
         mu_cur ^= 1;
     }
 
@@ -441,15 +550,9 @@ struct Adj {
     template <typename T, bool K>
     void rev_step_t(int64_t j) {
         loss_at<T>(j, b->vend, true);
-        for (int i = c->l - 1; i >= 0; --i) {
-            dgrad<T>(b->d2[i]);
-            mu_substep();
-        }
+        for (int i = c->l - 1; i >= 0; --i) mu_step<T>(b->d2[i]);
         react_bwd<T, K>(j);
-        for (int i = c->l - 1; i >= 0; --i) {
-            dgrad<T>(b->d1[i]);
-            mu_substep();
-        }
+        for (int i = c->l - 1; i >= 0; --i) mu_step<T>(b->d1[i]);
     }
     void rev_step(int64_t j) {
         if (c->s.prec == P_F64) rev_step_t<double, false>(j);
