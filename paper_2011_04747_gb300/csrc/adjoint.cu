@@ -153,61 +153,51 @@ __global__ void __launch_bounds__(128) adj_diff_react_fwd(OpView<R> op, AdjReact
     if (KAHAN) a.Co[i] = c;
 }
 
-// Reverse of step A per node: recompute the sub-steps, then transpose them.
+// Reverse of step A at node i: recompute the sub-steps from the stored input
+// (rv, rc, rh), then transpose them on the costate (mu_i = lambda_v / m_i and
+// lamh[i]).  Returns the new mu_i; gn gets the node's dL/dtau_close share.
 template <typename R, bool KAHAN>
-__global__ void adj_react_bwd(AdjReactArgs<R> a, const R* __restrict__ rv, const float* __restrict__ rc,
-                              const R* __restrict__ rh, const uint8_t* __restrict__ kused, R* mu, R* lamh,
-                              const R* __restrict__ m, double* g_tau) {
-    __shared__ double red[32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double gt = 0.0;
-    if (i < a.n) {
-        const int k = kused[i];
-        const unsigned smask = a.n_stims ? a.stim_mask[i] : 0u;
-        R vs[DAETI_MAX_K], hs[DAETI_MAX_K];
-        bool lows[DAETI_MAX_K];
-        R v = rv[i], h = rh[i];
-        float c = KAHAN ? rc[i] : 0.f;
-        float* cp = KAHAN ? &c : nullptr;
-        const R dt = a.dtkr[k];
+__device__ __forceinline__ R react_bwd_node(const AdjReactArgs<R>& a, int i, const R* __restrict__ rv,
+                                            const float* __restrict__ rc, const R* __restrict__ rh,
+                                            const uint8_t* __restrict__ kused, R mu_i, R* lamh,
+                                            const R* __restrict__ m, R& gn) {
+    const int k = kused[i];
+    const unsigned smask = a.n_stims ? a.stim_mask[i] : 0u;
+    R vs[DAETI_MAX_K], hs[DAETI_MAX_K];
+    bool lows[DAETI_MAX_K];
+    R v = rv[i], h = rh[i];
+    float c = KAHAN ? rc[i] : 0.f;
+    float* cp = KAHAN ? &c : nullptr;
+    const R dt = a.dtkr[k];
 #pragma unroll 1
-        for (int s = 0; s < k; ++s) {
-            const R J = smask ? adj_stim<R>(smask, a.stims, a.t_n + (double)s * a.dtk[k]) : (R)0;
-            const bool low = v < a.vgate;
-            vs[s] = v;
-            hs[s] = h;
-            lows[s] = low;
-            ms_substep_b(v, cp, h, dt, J, a.r_in, a.r_out, a.r_open, a.r_close, low);
-        }
-        R lv = mu[i] * m[i];
-        R lh = lamh[i];
-        // this node's share of dL/dtau_close in the state precision (at most
-        // k_max terms), added to the double block sum once
-        const R tau_fac = dt * a.r_close * a.r_close;
-        R gn = (R)0;
+    for (int s = 0; s < k; ++s) {
+        const R J = smask ? adj_stim<R>(smask, a.stims, a.t_n + (double)s * a.dtk[k]) : (R)0;
+        const bool low = v < a.vgate;
+        vs[s] = v;
+        hs[s] = h;
+        lows[s] = low;
+        ms_substep_b(v, cp, h, dt, J, a.r_in, a.r_out, a.r_open, a.r_close, low);
+    }
+    const R mi = m[i];
+    R lv = mu_i * mi;
+    R lh = lamh[i];
+    // this node's share of dL/dtau_close in the state precision (at most
+    // k_max terms), added to the double block sum once
+    const R tau_fac = dt * a.r_close * a.r_close;
+    gn = (R)0;
 #pragma unroll 1
-        for (int s = k - 1; s >= 0; --s) {
-            const R vi = vs[s], hi = hs[s];
-            const R fv = hi * ((R)2 * vi - (R)3 * vi * vi) * a.r_in - a.r_out;
-            const R fh = vi * vi * ((R)1 - vi) * a.r_in;
-            const R gh = lows[s] ? -a.r_open : -a.r_close;
-            if (!lows[s]) gn += lh * hi * tau_fac;
-            const R nlv = ((R)1 + dt * fv) * lv;
-            lh = dt * fh * lv + ((R)1 + dt * gh) * lh;
-            lv = nlv;
-        }
-        mu[i] = lv / m[i];
-        lamh[i] = lh;
-        gt = (double)gn;
+    for (int s = k - 1; s >= 0; --s) {
+        const R vi = vs[s], hi = hs[s];
+        const R fv = hi * ((R)2 * vi - (R)3 * vi * vi) * a.r_in - a.r_out;
+        const R fh = vi * vi * ((R)1 - vi) * a.r_in;
+        const R gh = lows[s] ? -a.r_open : -a.r_close;
+        if (!lows[s]) gn += lh * hi * tau_fac;
+        const R nlv = ((R)1 + dt * fv) * lv;
+        lh = dt * fh * lv + ((R)1 + dt * gh) * lh;
+        lv = nlv;
     }
-    for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gt;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        gt = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
-        if (threadIdx.x == 0 && gt != 0.0) atomicAdd(g_tau, gt);
-    }
+    lamh[i] = lh;
+    return lv / mi;
 }
 
 template <typename R>
@@ -253,6 +243,37 @@ __global__ void __launch_bounds__(256) adj_mu_dgrad(OpView<R> op, int n, const R
         mu_out[t] = v;
     }
     if (t < n_elem) elem_dgrad<R>(t, dim, nx, ny, mu_in, vin, dt_ad, kr, g);
+}
+
+// As adj_mu_dgrad for the first sub-step of step III, followed at each node by
+// the reverse of its step A (which needs only that node's costate).
+template <typename R, bool KAHAN, int DIM>
+__global__ void __launch_bounds__(256) adj_mu_react_bwd(OpView<R> op, AdjReactArgs<R> a, const R* __restrict__ mu_in,
+                                                        R* __restrict__ mu_out, int64_t n_elem, int dim, int nx,
+                                                        int ny, const R* __restrict__ vin, double dt_ad, KrefR<R> kr,
+                                                        double* g, const R* __restrict__ rv,
+                                                        const float* __restrict__ rc, const R* __restrict__ rh,
+                                                        const uint8_t* __restrict__ kused, R* lamh,
+                                                        const R* __restrict__ m, double* g_tau) {
+    __shared__ double red[32];
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double gt = 0.0;
+    if (t < a.n) {
+        R v, gn;
+        float cc;
+        diffuse_node<R, DIM, false>(op, mu_in, nullptr, (int)t, v, cc);
+        mu_out[t] = react_bwd_node<R, KAHAN>(a, (int)t, rv, rc, rh, kused, v, lamh, m, gn);
+        gt = (double)gn;
+    }
+    if (t < n_elem) elem_dgrad<R>(t, dim, nx, ny, mu_in, vin, dt_ad, kr, g);
+    for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        gt = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) gt += __shfl_xor_sync(0xffffffffu, gt, o);
+        if (threadIdx.x == 0 && gt != 0.0) atomicAdd(g_tau, gt);
+    }
 }
 
 template <typename R>
@@ -537,21 +558,36 @@ struct Adj {
         mu_cur ^= 1;
     }
 
+    // The first sub-step of step III reversed (input vin) and then step A of step j reversed.
     template <typename T, bool K>
-    void react_bwd(int64_t j) {
-        const int n = (int)c->n_nodes;
+    void mu_react_bwd(int64_t j, const void* vin) {
+        KrefR<T> kr;
+        for (int q = 0; q < 64; ++q) kr.k[q] = (T)c->kref[q];
+        const OpView<T> op = op_view<T>(c->op);
         AdjReactArgs<T> a = react_args<T>(c, c->cur, n0 + j, nullptr, nullptr);
-        adj_react_bwd<T, K><<<(n + 127) / 128, 128, 0, st>>>(a, (const T*)b->rv, b->rc, (const T*)b->rh, b->kused,
-                                                            (T*)b->mu[mu_cur], (T*)b->lamh, (const T*)b->mR,
-                                                            b->acc + 1);
+        const int64_t ne = c->n_elem;
+        const unsigned grid = (unsigned)((std::max<int64_t>(a.n, ne) + 255) / 256);
+        const int nx = (int)c->n[0], ny = (int)c->n[1];
+        const T* mi = (const T*)b->mu[mu_cur];
+        T* mo = (T*)b->mu[mu_cur ^ 1];
+        const int dim = c->op.kind == 1 ? 0 : c->op.dim;
+        auto go = [&](auto kern) {
+            kern<<<grid, 256, 0, st>>>(op, a, mi, mo, ne, c->dim, nx, ny, (const T*)vin, c->dt_ad, kr, b->g_elem,
+                                       (const T*)b->rv, b->rc, (const T*)b->rh, b->kused, (T*)b->lamh,
+                                       (const T*)b->mR, b->acc + 1);
+        };
+        if (dim == 0) go(adj_mu_react_bwd<T, K, 0>);
+        else if (dim == 2) go(adj_mu_react_bwd<T, K, 2>);
+        else go(adj_mu_react_bwd<T, K, 3>);
+        mu_cur ^= 1;
     }
 
     // Reverse of step j (the intermediates of fwd_step(j, true) are in place).
     template <typename T, bool K>
     void rev_step_t(int64_t j) {
         loss_at<T>(j, b->vend, true);
-        for (int i = c->l - 1; i >= 0; --i) mu_step<T>(b->d2[i]);
-        react_bwd<T, K>(j);
+        for (int i = c->l - 1; i >= 1; --i) mu_step<T>(b->d2[i]);
+        mu_react_bwd<T, K>(j, b->d2[0]);
         for (int i = c->l - 1; i >= 0; --i) mu_step<T>(b->d1[i]);
     }
     void rev_step(int64_t j) {
