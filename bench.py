@@ -298,7 +298,8 @@ def bench_slab(args, env):
         dv = float(np.max(np.abs(v32 - v64)))
         dact = float(np.max(np.abs(a32[both] - a64[both]))) if both.any() else None
 
-    launches_per_step = 2 * stab["l"] + (0 if tuning_used["fuse_diffusion"] else 1)
+    # launches per step as counted by the per-kernel pass (the same sequence the graphs replay)
+    launches_per_step = (kt["reaction"]["launches"] + kt["diffusion"]["launches"]) / n_steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": env.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec32 * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -315,7 +316,8 @@ def bench_slab(args, env):
         "kernels": kt, "roofline": roof, "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n_nodes * (ns + 2) * 4,
                 "d2h_bytes_per_step": 2 * n_nodes * 8},
-        "gpu_launches": (launches_per_step * n_steps + n_steps // max(tuning_used["graph_steps"], 1) + 2) * args.steps,
+        "gpu_launches": int(round(launches_per_step * n_steps + n_steps // max(tuning_used["graph_steps"], 1) + 2))
+        * args.steps,
     }
     if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline_sample(wl)
@@ -334,13 +336,18 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
     n_steps = int(round(t_end / st["dt"]))
     s.daeti_load_state(ck)
     s.daeti_set_profiling(True)
-    s.daeti_advance(min(t_end, 20 * st["dt"]))
+    prof_steps = int(round(min(t_end, 20 * st["dt"]) / st["dt"]))
+    s.daeti_advance(prof_steps * st["dt"])
     ms, nl = s.daeti_get_kernel_time(1)
     b, _ = s.daeti_kernel_work(1)
+    fused = s.daeti_get_tuning()["fuse_diffusion"]
     s.daeti_set_profiling(False)
     s.close()
-    diff = {"avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b,
-            "GBs": b / (ms / max(nl, 1) / 1e3) / 1e9 if ms else None}
+    # diffusion sub-steps per diffusion launch (a 2D grid's tiled path applies several per launch);
+    # GB/s counts the algorithmic bytes of every sub-step the launch applies
+    sub_per_launch = (2 * st["l"] - (1 if fused else 0)) * prof_steps / max(nl, 1)
+    diff = {"avg_us": 1e3 * ms / max(nl, 1), "bytes_per_substep": b, "substeps_per_launch": sub_per_launch,
+            "GBs": b * sub_per_launch / (ms / max(nl, 1) / 1e3) / 1e9 if ms else None}
     if diff["GBs"]:
         diff["frac_of_measured_hbm"] = diff["GBs"] / _peaks().get("hbm_gbs", 6786.9)
     line = {"metric": UNIT + " (" + name + ")", "value": env.world * wl.n_nodes * n_steps / sec, "unit": UNIT,

@@ -177,16 +177,18 @@ def test_full_slab_bench_config_first_steps(precision):
     _compare(wl, 30, 10, precision)
 
 
-@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3"])
+@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3", "sheet_l4"])
 def test_launch_shapes_do_not_change_results(wl_name):
     """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
     programmatic dependent launch or plain launches, and graphs give
-    bit-identical states."""
+    bit-identical states (l = 1, 3 and 4)."""
     from parity_util import ensure_lib
 
     binding = ensure_lib()
-    wl = {"slab": I.tp06_slab_3d(23, 19, 9, t_end=12), "sheet2d": I.aniso_sheet_2d(n=41, length=1.0, model="tp06"),
-          "sheet_l3": I.aniso_sheet_2d(n=37, length=0.36, model="tp06")}[wl_name]
+    wl, opts = {"slab": (I.tp06_slab_3d(23, 19, 9, t_end=12), {}),
+                "sheet2d": (I.aniso_sheet_2d(n=41, length=1.0, model="tp06"), {}),
+                "sheet_l3": (I.aniso_sheet_2d(n=37, length=0.36, model="tp06"), {}),
+                "sheet_l4": (I.aniso_sheet_2d(n=45, length=0.44, model="tp06"), dict(l_rounding="ceil"))}[wl_name]
     variants = [dict(),
                 dict(fuse_diffusion=0),
                 dict(react_min_blocks=10),
@@ -194,14 +196,17 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 dict(pdl=0),
                 dict(pdl=0, react_block=64, graph_steps=0),
                 dict(bucket_k=0, graph_steps=0),
-                dict(graph_steps=6, diff_block=128)]
+                dict(graph_steps=6, diff_block=128),
+                dict(diff_block=256, fuse_diffusion=0, graph_steps=0)]
     ref = None
     for prec in ("fp32_kahan", "fp64"):
         ref = None
         for v in variants:
-            s = binding.solver_from_workload(wl, precision=prec)
+            s = binding.solver_from_workload(wl, precision=prec, **opts)
+            if wl_name.startswith("sheet_l"):
+                assert s.daeti_get_stability()["l"] == int(wl_name[-1])
             s.daeti_set_tuning(**v)
-            s.daeti_advance(3.0)
+            s.daeti_advance(3.1)        # odd step count: graph segments and plain steps
             s.daeti_advance(7.0)        # two advances: prologue/epilogue of the fused path twice
             out = (s.daeti_read_state(), s.daeti_read_activation())
             s.close()
