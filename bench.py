@@ -271,12 +271,16 @@ def bench_slab(args, env):
     d["bytes_GBs"] = d["bytes_per_launch"] / (d["avg_us"] * 1e-6) / 1e9
     s32.daeti_set_profiling(False)
 
-    # e2e through the C ABI with host buffers
+    # e2e through the C ABI with host buffers: the initial state (published
+    # values at every node, n_states x n doubles) from pinned host memory
+    s32.daeti_init_state(None)
+    init_host = env.torch.empty((s32.n_states, n_nodes), dtype=env.torch.float64, pin_memory=True)
+    init_host.numpy()[:] = s32.daeti_read_state()
     e2e = []
     for it in range(2 + max(1, args.steps // 2)):
         env.torch.cuda.synchronize(env.dev)
         t0 = time.perf_counter()
-        s32.daeti_init_state(None)              # host -> device
+        s32.daeti_init_state(init_host.numpy())     # host -> device
         s32.daeti_advance(T_END)
         s32.daeti_read_v()                      # device -> host (waits)
         s32.daeti_read_activation()
@@ -314,7 +318,7 @@ def bench_slab(args, env):
         "fp32_vs_fp64": {"max_abs_dv_mv_at_500ms": dv, "max_abs_dact_ms": dact},
         "reaction_substeps_per_node_step": sub_per_step / n_nodes if sub_per_step else None,
         "kernels": kt, "roofline": roof, "clocks": clocks,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n_nodes * (ns + 2) * 4,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n_nodes * ns * 8,
                 "d2h_bytes_per_step": 2 * n_nodes * 8},
         "gpu_launches": int(round(launches_per_step * n_steps + n_steps // max(tuning_used["graph_steps"], 1) + 2))
         * args.steps,

@@ -774,44 +774,37 @@ int daeti_init_state(daeti_ctx* c, const double* state) {
     if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
     const int64_t N = c->n_nodes;
     const int ns = c->s.n_states;
+    if (ns > 32) return fail(c, DAETI_EINVAL, "too many states");
     CK(cudaStreamSynchronize(c->stream));
-    std::vector<double> host;
-    if (!state) {
-        host.resize((size_t)ns * N);
-        for (int k = 0; k < ns; ++k) {
-            double v = c->model == DAETI_MODEL_MS ? (k == 0 ? 0.0 : 1.0) : TP06_INIT[k];
-            std::fill(host.begin() + (size_t)k * N, host.begin() + (size_t)(k + 1) * N, v);
-        }
-        state = host.data();
+    InitDefaults def{};
+    for (int k = 0; k < ns; ++k) def.v[k] = c->model == DAETI_MODEL_MS ? (k == 0 ? 0.0 : 1.0) : TP06_INIT[k];
+    const double* src = nullptr;
+    if (state) {
+        // one copy of the caller's array to a device staging buffer; the
+        // finiteness check, the conversion and the chunked layout run on the GPU
+        const size_t bytes = 8 * (size_t)ns * N;
+        int rc;
+        if (!c->stage && (rc = dalloc(c, &c->stage, bytes))) return rc;
+        CK(cudaMemcpyAsync(c->stage, state, bytes, cudaMemcpyHostToDevice, c->stream));
+        int* flag = (int*)c->scratch;
+        CK(cudaMemsetAsync(flag, 0, 4, c->stream));
+        launch_check_finite((const double*)c->stage, (int64_t)ns * N, flag, c->stream);
+        int bad = 0;
+        CK(cpy_(c, &bad, flag, 4, cudaMemcpyDeviceToHost));
+        if (bad) return fail(c, DAETI_EINVAL, "state must be finite");
+        src = (const double*)c->stage;
     }
-    for (int64_t i = 0; i < (int64_t)ns * N; ++i)
-        if (!std::isfinite(state[i])) return fail(c, DAETI_EINVAL, "state must be finite");
-    const size_t R = rsize(c);
-    int rc;
-    if ((rc = upload_real(c, c->s.V[0], state, N))) return rc;
-    if ((rc = upload_real(c, c->s.vsync, state, N))) return rc;
-    {
-        // cell states in chunks of 32 nodes (state_index); lanes past N hold 0
-        const int nsx = ns - 1;
-        std::vector<double> chunked(state_elems(N, nsx), 0.0);
-        for (int k = 0; k < nsx; ++k)
-            for (int64_t i = 0; i < N; ++i) chunked[state_index(i, k, nsx)] = state[(size_t)(k + 1) * N + i];
-        if ((rc = upload_real(c, c->s.S, chunked.data(), (int64_t)chunked.size()))) return rc;
-    }
-    if (c->s.kahan) {
-        CK(set_(c, c->s.C[0], 0, 4 * N));
-        CK(set_(c, c->s.C[1], 0, 4 * N));
-    }
-    std::vector<double> neg(N, -1.0);
-    if ((rc = upload_real(c, c->s.act, neg.data(), N))) return rc;
-    CK(set_(c, c->s.kk, 1, N));
-    CK(set_(c, c->s.counts, 0, 4 * 2 * DAETI_MAX_K));
+    launch_init_state(src, def, N, ns, c->s.prec, c->s.V[0], c->s.vsync, c->s.S, c->s.act,
+                      c->s.kahan ? c->s.C[0] : nullptr, c->s.kahan ? c->s.C[1] : nullptr, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(c->s.kk, 1, N, c->stream));
+    CK(cudaMemsetAsync(c->s.counts, 0, 4 * 2 * DAETI_MAX_K, c->stream));
     launch_rebuild_lists(c->s, 0, c->stream);   // every node in the k = 1 list
+    CK(cudaMemsetAsync(c->s.flags, 0, 16, c->stream));
+    CK(cudaMemsetAsync(c->s.step_ctr, 0, 8, c->stream));
+    CK(cudaMemsetAsync(c->s.substeps, 0, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    CK(set_(c, c->s.flags, 0, 16));
-    CK(set_(c, c->s.step_ctr, 0, 8));
-    CK(set_(c, c->s.substeps, 0, 8));
-    (void)R;
+    CK(cudaGetLastError());
     c->nstep = 0;
     c->cur = 0;
     c->par = 0;

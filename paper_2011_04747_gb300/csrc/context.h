@@ -49,6 +49,7 @@ struct daeti_ctx {
     int cur = 0;
     int par = 0;
     void* scratch = nullptr;   // n doubles for conversions
+    void* stage = nullptr;     // n_states x n doubles: a caller's initial state (allocated on first use)
     void* probe = nullptr;     // probe node indices then values (daeti_read_v_nodes)
     int64_t probe_cap = 0;     // probes the buffer holds
     std::vector<double> mass;  // lumped mass per node (host, FP64)

@@ -2,7 +2,10 @@
 //   dt_s = 0.9 min_i m_ii / (k_ii + sum_{j != i} |k_ij|)
 // as a grid-wide min-reduction over rows, and the building blocks of a power
 // iteration for lambda_max(M_L^-1 K) (apply, M-weighted dot products,
-// scaling).  Also the state/dtype conversion used by the read functions.
+// scaling).  Also the state/dtype conversion used by the read functions and
+// the initial state written in the device layout.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -236,6 +239,54 @@ void launch_gather_state(const void* src, int src_prec, int ns, int s, double* d
     if (!grid) return;
     if (src_prec == P_F64) gather_state_kernel<double><<<grid, 256, 0, st>>>((const double*)src, ns, s, dst, n);
     else gather_state_kernel<float><<<grid, 256, 0, st>>>((const float*)src, ns, s, dst, n);
+}
+
+// Initial state (one thread per node, the last chunk's lanes past n included):
+// state k of node i from src[k * n + i] (or def.v[k] when src is null).
+template <typename R>
+__global__ void init_state_kernel(const double* __restrict__ src, InitDefaults def, int64_t n, int ns, R* V, R* vsync,
+                                  R* S, R* act, float* c0, float* c1) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nsx = ns - 1;
+    if (i >= ((n + 31) & ~(int64_t)31)) return;
+    const bool in = i < n;
+    for (int k = 1; k < ns; ++k) {
+        const double x = in ? (src ? src[(int64_t)k * n + i] : def.v[k]) : 0.0;
+        S[((i >> 5) * nsx + (k - 1)) * 32 + (i & 31)] = (R)x;
+    }
+    if (!in) return;
+    const R v = (R)(src ? src[i] : def.v[0]);
+    V[i] = v;
+    vsync[i] = v;
+    act[i] = (R)-1;
+    if (c0) c0[i] = 0.f;
+    if (c1) c1[i] = 0.f;
+}
+
+__global__ void check_finite_kernel(const double* __restrict__ x, int64_t n, int* flag) {
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+void launch_init_state(const double* src, const InitDefaults& def, int64_t n, int ns, int prec, void* V, void* vsync,
+                       void* S, void* act, float* c0, float* c1, cudaStream_t st) {
+    const int64_t lanes = (n + 31) & ~(int64_t)31;
+    const int grid = (int)((lanes + 255) / 256);
+    if (!grid) return;
+    if (prec == P_F64)
+        init_state_kernel<double><<<grid, 256, 0, st>>>(src, def, n, ns, (double*)V, (double*)vsync, (double*)S,
+                                                        (double*)act, c0, c1);
+    else
+        init_state_kernel<float><<<grid, 256, 0, st>>>(src, def, n, ns, (float*)V, (float*)vsync, (float*)S,
+                                                       (float*)act, c0, c1);
+}
+
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st) {
+    if (n <= 0) return;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * 152);
+    check_finite_kernel<<<grid, 256, 0, st>>>(x, n, flag);
 }
 
 }  // namespace daeti

@@ -167,4 +167,16 @@ void launch_gather_v(const void* src, int src_prec, const float* comp, const int
                      cudaStream_t st);
 // State s of every node from the chunked state array, as double.
 void launch_gather_state(const void* src, int src_prec, int ns, int s, double* dst, int64_t n, cudaStream_t st);
+// Initial state in the device layout: state k of node i from src[k n + i] (ns
+// x n doubles on the device; null: def.v[k] at every node) to V and vsync
+// (k = 0) and to the chunked cell states (k > 0, lanes of the last chunk past
+// n set to 0), in precision prec; act = -1, the compensation terms c0, c1
+// (nullable) 0.
+struct InitDefaults {
+    double v[32];
+};
+void launch_init_state(const double* src, const InitDefaults& def, int64_t n, int ns, int prec, void* V, void* vsync,
+                       void* S, void* act, float* c0, float* c1, cudaStream_t st);
+// *flag |= 1 when one of the n values is not finite.
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
 }  // namespace daeti
