@@ -546,7 +546,7 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
     void* p = nullptr;
     const bool fresh = c->op.coef == nullptr && c->op.val == nullptr;
     if (table) {
-        if (!fresh && c->op.kind != 0) return fail(c, DAETI_EINVAL, "operator layout changed");
+        if (!fresh && (c->op.kind != 0 || c->op.per_node)) return fail(c, DAETI_EINVAL, "operator layout changed");
         c->op.kind = 0;
         c->op.dim = c->dim;
         c->op.nx = tab.nx;
@@ -574,6 +574,34 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
             c->op.cls = (uint16_t*)p;
             CK(cpy_(c, p, cls.data(), 2 * (size_t)N, cudaMemcpyHostToDevice));
         }
+    } else if (c->mesh_kind == 1) {
+        // structured grid with D varying within layers: one stencil row per
+        // node from the CSR rows (entry (dz+1)*9 + (dy+1)*3 + dx+1 for the
+        // neighbour at offset (dx, dy, dz); columns ascend, so the terms are
+        // added in the CSR order)
+        if (!fresh && (c->op.kind != 0 || !c->op.per_node)) return fail(c, DAETI_EINVAL, "operator layout changed");
+        const int64_t nx = c->n[0], ny = c->n[1];
+        c->op.kind = 0;
+        c->op.per_node = 1;
+        c->op.dim = c->dim;
+        c->op.nx = (int)nx;
+        c->op.ny = (int)ny;
+        c->op.nz = c->dim == 3 ? (int)c->n[2] : 1;
+        std::vector<double> A((size_t)N * DAETI_ROW, 0.0);
+        for (int64_t i = 0; i < N; ++i) {
+            const double s = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
+            const int64_t xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+            for (int64_t q = K.rowptr[i]; q < K.rowptr[i + 1]; ++q) {
+                const int64_t j = K.col[q];
+                if (j == i) continue;
+                const int64_t dx = j % nx - xi, dy = (j / nx) % ny - yi, dz = j / (nx * ny) - zi;
+                if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
+                    return fail(c, DAETI_EINVAL, "grid operator reaches beyond the 27-point stencil");
+                A[(size_t)i * DAETI_ROW + (size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))] = K.val[q] * s;
+            }
+        }
+        if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
+        if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
     } else {
         if (!fresh && c->op.kind != 1) return fail(c, DAETI_EINVAL, "operator layout changed");
         std::vector<double> scale(N);
@@ -654,7 +682,7 @@ int daeti_prepare(daeti_ctx* c) {
     void* p = nullptr;
     // V buffers of a structured grid carry a zeroed ghost margin of the stencil
     // reach on both sides, so the stencil needs no per-neighbour boundary tests
-    const int64_t pad = table ? 1 + (int64_t)tab.nx + (tab.dim == 3 ? (int64_t)tab.nx * tab.ny : 0) : 0;
+    const int64_t pad = c->mesh_kind == 1 ? 1 + c->n[0] + (c->dim == 3 ? c->n[0] * c->n[1] : 0) : 0;
     for (int b = 0; b < 2; ++b) {
         if ((rc = dalloc(c, &p, R * (N + 2 * pad)))) return rc;
         CK(set_(c, p, 0, R * (N + 2 * pad)));
@@ -1050,6 +1078,7 @@ int daeti_kernel_work(daeti_ctx* c, int which, double* bytes, double* flops) {
             // plus the fused diffusion sub-step: V and the Kahan term of the source buffer
             b += N * (R + (c->s.kahan ? 4.0 : 0.0));
             if (c->op.kind == 1) b += (double)c->op.nnz_padded * (R + 4.0);
+            if (c->op.per_node) b += N * (c->dim == 3 ? 26.0 : 8.0) * R;
         }
     } else if (which == 1) {
         // one sub-step launch: V and the Kahan term read and written once,
@@ -1057,6 +1086,7 @@ int daeti_kernel_work(daeti_ctx* c, int which, double* bytes, double* flops) {
         const double npts = c->op.kind == 0 ? (c->dim == 3 ? 26.0 : 8.0) : 15.0;
         b = N * (2.0 * R + comp);
         if (c->op.kind == 1) b += (double)c->op.nnz_padded * (R + 4.0);
+        if (c->op.per_node) b += N * npts * R;   // the node's stencil row
         f = N * 2.0 * npts;
     } else {
         b = N * sync;

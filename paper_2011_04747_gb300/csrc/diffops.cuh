@@ -93,6 +93,7 @@ struct OpView {
     int nx, ny, nz;
     const R* coef;
     const uint16_t* cls;  // table row of each node (nullable)
+    int per_node;         // one coefficient row per node
     const int64_t* chunk_ptr;
     const int* chunk_w;
     const int* col;
@@ -111,9 +112,9 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
         const int nxy = op.nx * op.ny;
         const int nx = op.nx;
         auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
-        if (PAD && op.cls) {
+        if (PAD && (op.per_node || op.cls)) {
             // no boundary tests: the table row is all the stencil needs
-            const R* crow = op.coef + (size_t)op.cls[i] * DAETI_ROW;
+            const R* crow = op.coef + (size_t)(op.per_node ? i : op.cls[i]) * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, 1, 1, 1, 3, vi, ci, fetch, vout, cout);
         } else {
             const int x = i % op.nx;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
             const int y = yz % op.ny;
             const int z = yz / op.ny;
             const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
-            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
+            const R* crow = op.coef + (op.per_node ? (size_t)i : (size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
         }
     }
@@ -136,6 +137,7 @@ inline OpView<R> op_view(const DiffOp& op) {
     v.nz = op.nz;
     v.coef = (const R*)op.coef;
     v.cls = op.cls;
+    v.per_node = op.per_node;
     v.chunk_ptr = op.chunk_ptr;
     v.chunk_w = op.chunk_w;
     v.col = op.col;

@@ -6,9 +6,11 @@
 // neighbouring nodes.  Layouts:
 //   * structured grids: a 9-point (2D) / 27-point (3D) stencil whose
 //     coefficients depend only on the node's z layer and its x/y boundary
-//     class (table [nz][3][3][28], the 27 offsets and a pad); used when D
-//     varies at most with z;
-//   * any mesh: SELL-32 sparse rows (chunks of 32 rows, column-major).
+//     class (table [nz][3][3][28], the 27 offsets and a pad) when D varies
+//     at most with z, else one such row per node (neighbour offsets stay
+//     implicit; the entries are SELL's, in the same order);
+//   * unstructured meshes: SELL-32 sparse rows (chunks of 32 rows,
+//     column-major).
 // The launch that ends a diffusion half at t_n also runs the synchronisation
 // epilogue (activation time, k of the next step A, and either the per-k node
 // lists or, after a step with one k at every node, the check that k is still
@@ -161,7 +163,7 @@ template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
                        StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
-    if (dop.kind == 0 && block == 0) {
+    if (dop.kind == 0 && block == 0 && !dop.per_node) {
         // structured grid, shared-memory tiles
         const OpView<R> op = op_view<R>(dop);
         const R* vin = (const R*)s.V[src];

@@ -57,6 +57,7 @@ struct DiffOp {
     int nx = 1, ny = 1, nz = 1;
     void* coef = nullptr;    // table: [nz*9][28] off-diagonal dt_ad K_ij / m_i (centre entry and pad 0)
     uint16_t* cls = nullptr; // table row of each node (nullable)
+    int per_node = 0;        // 1: coef holds one row per node (row i for node i), cls unused
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
     int64_t* chunk_ptr = nullptr;   // start of chunk c in val/col

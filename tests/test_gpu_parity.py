@@ -75,12 +75,20 @@ def test_tet_mesh_sell_path(precision):
     _compare(wl, 300, 20, precision)
 
 
-def test_heterogeneous_grid_uses_sparse_path():
-    wl = I.ms_square_2d(n=23)
-    rng = np.random.default_rng(7)
-    wl.d_long = wl.d_long * rng.uniform(0.3, 1.7, wl.n_elems)
-    wl.d_trans = wl.d_long.copy()
-    _compare(wl, 400, 20, "fp64")
+def _heterogeneous(wl, seed=7):
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.3, 1.7, wl.n_elems)
+    wl.d_long = wl.d_long * f
+    wl.d_trans = wl.d_trans * f
+    return wl
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_heterogeneous_grid_per_node_rows(precision):
+    """Structured grids whose D varies within a layer: one stencil row per node
+    (2D isotropic Mitchell-Schaeffer; 3D TP06 slab with rotating fibres)."""
+    _compare(_heterogeneous(I.ms_square_2d(n=23)), 400, 20, precision)
+    _compare(_heterogeneous(I.tp06_slab_3d(13, 11, 6)), 300, 20, precision)
 
 
 @pytest.mark.parametrize("scheme_name", ["ost", "ostar"])
@@ -204,7 +212,7 @@ def test_full_slab_bench_config_first_steps(precision):
     _compare(wl, 30, 10, precision)
 
 
-@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3", "sheet_l4"])
+@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3", "sheet_l4", "hetero_slab"])
 def test_launch_shapes_do_not_change_results(wl_name):
     """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
     programmatic dependent launch or plain launches, and graphs give
@@ -215,7 +223,8 @@ def test_launch_shapes_do_not_change_results(wl_name):
     wl, opts = {"slab": (I.tp06_slab_3d(23, 19, 9, t_end=12), {}),
                 "sheet2d": (I.aniso_sheet_2d(n=41, length=1.0, model="tp06"), {}),
                 "sheet_l3": (I.aniso_sheet_2d(n=37, length=0.36, model="tp06"), {}),
-                "sheet_l4": (I.aniso_sheet_2d(n=45, length=0.44, model="tp06"), dict(l_rounding="ceil"))}[wl_name]
+                "sheet_l4": (I.aniso_sheet_2d(n=45, length=0.44, model="tp06"), dict(l_rounding="ceil")),
+                "hetero_slab": (_heterogeneous(I.tp06_slab_3d(23, 19, 9, t_end=12)), {})}[wl_name]
     variants = [dict(),
                 dict(fuse_diffusion=0),
                 dict(react_min_blocks=10),
