@@ -132,14 +132,44 @@ __device__ __forceinline__ void react_node(const AdjReactArgs<R>& a, int i, R& v
     }
 }
 
+// Checkpoint traffic carried by the first forward launch after a save or a
+// restore, node by node.  Save: the step-start state (v0, c0, a.H, a.kk and the
+// live vs, act) is copied to the slot arrays s*.  Restore: the launch reads V,
+// the compensation, h and k from the slot directly, and copies the slot's
+// vsync and activation times (rVs, rA) to the live vs, act before the
+// synchronising sub-step reads them.
+template <typename R>
+struct CkSide {
+    R *sV = nullptr, *sH = nullptr, *sVs = nullptr, *sA = nullptr;
+    float* sC = nullptr;
+    uint8_t* sK = nullptr;
+    const R* v0 = nullptr;
+    const float* c0 = nullptr;
+    const R *rVs = nullptr, *rA = nullptr;
+    R *vs = nullptr, *act = nullptr;
+};
+
 // The last step-I diffusion sub-step and step A in one launch: node i's
 // diffused value feeds its own reaction directly.  With vmid the diffused
 // value (the reaction's input) is stored as well.
 template <typename R, bool KAHAN, int MODE, int DIM>
 __global__ void __launch_bounds__(128) adj_diff_react_fwd(OpView<R> op, AdjReactArgs<R> a, const R* __restrict__ vin,
-                                                          const float* __restrict__ cin, R* vmid, float* cmid) {
+                                                          const float* __restrict__ cin, R* vmid, float* cmid,
+                                                          CkSide<R> ck) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    if (ck.sV) {
+        ck.sV[i] = ck.v0[i];
+        if (KAHAN) ck.sC[i] = ck.c0[i];
+        ck.sH[i] = a.H[i];
+        ck.sK[i] = a.kk[i];
+        ck.sVs[i] = ck.vs[i];
+        ck.sA[i] = ck.act[i];
+    }
+    if (ck.rVs) {
+        ck.vs[i] = ck.rVs[i];
+        ck.act[i] = ck.rA[i];
+    }
     R v;
     float c;
     diffuse_node<R, DIM, KAHAN>(op, vin, cin, i, v, c);
@@ -388,72 +418,99 @@ struct Adj {
     int mode;            // 0 decide, 1 record, 2 replay
     int mu_cur = 0;
     int64_t fwd_steps = 0;
-    int live_slot = -1;  // checkpoint slot the live state still equals (-1: none)
+    int live_slot = -1;  // checkpoint slot the live state stands for (-1: none)
+    // Saves and restores are carried out by the next forward step's combined
+    // diffusion-reaction launch (CkSide); pend_save / pend_restore name the slot.
+    int pend_save = -1, pend_restore = -1;
     size_t R() const { return rsize(c); }
 
-    void save(int slot, int64_t step) {
+    void copy_state(bool to_slot, int slot) {
         const size_t N = c->n_nodes, r = R();
+        void* live[6] = {c->s.V[c->cur], b->kahan ? (void*)c->s.C[c->cur] : nullptr, c->s.S, c->s.vsync, c->s.act, c->s.kk};
+        void* sl[6] = {b->sV[slot], b->kahan ? b->sC[slot] : nullptr, b->sH[slot], b->sVs[slot], b->sA[slot],
+                       b->sK[slot]};
+        const size_t bytes[6] = {N * r, N * 4, N * r, N * r, N * r, N};
         CopyBuilder cb;
-        cb.add(b->sV[slot], c->s.V[c->cur], N * r);
-        if (b->kahan) cb.add(b->sC[slot], c->s.C[c->cur], N * 4);
-        cb.add(b->sH[slot], c->s.S, N * r);
-        cb.add(b->sVs[slot], c->s.vsync, N * r);
-        cb.add(b->sA[slot], c->s.act, N * r);
-        cb.add(b->sK[slot], c->s.kk, N);
+        for (int q = 0; q < 6; ++q) cb.add(to_slot ? sl[q] : live[q], to_slot ? live[q] : sl[q], bytes[q]);
         cb.launch(st);
+    }
+    // Carry out pending copies with a copy launch (where no forward step follows).
+    void flush() {
+        if (pend_save >= 0) copy_state(true, pend_save);
+        if (pend_restore >= 0) copy_state(false, pend_restore);
+        pend_save = pend_restore = -1;
+    }
+    void save(int slot, int64_t step) {
+        flush();
+        pend_save = slot;
         b->slot_step[slot] = step;
         live_slot = slot;
     }
     // The binomial recursion restores a checkpoint right after saving it; the
-    // live state is then unchanged and the copy is skipped.
+    // live state then still stands for it and nothing is done.
     void restore(int slot) {
         if (live_slot == slot) return;
-        const size_t N = c->n_nodes, r = R();
-        CopyBuilder cb;
-        cb.add(c->s.V[c->cur], b->sV[slot], N * r);
-        if (b->kahan) cb.add(c->s.C[c->cur], b->sC[slot], N * 4);
-        cb.add(c->s.S, b->sH[slot], N * r);
-        cb.add(c->s.vsync, b->sVs[slot], N * r);
-        cb.add(c->s.act, b->sA[slot], N * r);
-        cb.add(c->s.kk, b->sK[slot], N);
-        cb.launch(st);
+        flush();
+        pend_restore = slot;
         live_slot = slot;
     }
 
     // The last step-I diffusion sub-step (vin, cin -> the reaction's input,
-    // stored to vmid, cmid when given) and step A of step j in one launch.
+    // stored to vmid, cmid when given) and step A of step j in one launch;
+    // h and k from hin, kin; ck: the pending checkpoint copy.
     template <typename T, bool K>
     void diff_react(int64_t j, const void* vin, const float* cin, void* vmid, float* cmid, void* vout, float* cout,
-                    void* hout) {
+                    void* hout, const void* hin, const uint8_t* kin, int save_slot, int restore_slot) {
         const int n = (int)c->n_nodes;
         uint8_t* hk = b->hist_k ? b->hist_k + (size_t)j * n : nullptr;
         uint16_t* hb = b->hist_b ? b->hist_b + (size_t)j * n : nullptr;
         AdjReactArgs<T> a = react_args<T>(c, c->cur, n0 + j, hk, hb);
         a.V = nullptr;
         a.C = nullptr;
+        a.H = (T*)const_cast<void*>(hin);
+        a.kk = kin;
         a.Vo = (T*)vout;
         a.Co = cout;
         a.Ho = (T*)hout;
+        CkSide<T> ck;
+        ck.vs = (T*)c->s.vsync;
+        ck.act = (T*)c->s.act;
+        if (save_slot >= 0) {
+            ck.sV = (T*)b->sV[save_slot];
+            ck.sC = b->kahan ? (float*)b->sC[save_slot] : nullptr;
+            ck.sH = (T*)b->sH[save_slot];
+            ck.sVs = (T*)b->sVs[save_slot];
+            ck.sA = (T*)b->sA[save_slot];
+            ck.sK = (uint8_t*)b->sK[save_slot];
+            ck.v0 = (const T*)c->s.V[c->cur];
+            ck.c0 = b->kahan ? c->s.C[c->cur] : nullptr;
+        }
+        if (restore_slot >= 0) {
+            ck.rVs = (const T*)b->sVs[restore_slot];
+            ck.rA = (const T*)b->sA[restore_slot];
+        }
         const int dim = c->op.kind == 1 ? 0 : c->op.dim;
-        if (dim == 0) diff_react_dim<T, K, 0>(a, vin, cin, vmid, cmid);
-        else if (dim == 2) diff_react_dim<T, K, 2>(a, vin, cin, vmid, cmid);
-        else diff_react_dim<T, K, 3>(a, vin, cin, vmid, cmid);
+        if (dim == 0) diff_react_dim<T, K, 0>(a, vin, cin, vmid, cmid, ck);
+        else if (dim == 2) diff_react_dim<T, K, 2>(a, vin, cin, vmid, cmid, ck);
+        else diff_react_dim<T, K, 3>(a, vin, cin, vmid, cmid, ck);
     }
     template <typename T, bool K, int DIM>
-    void diff_react_dim(const AdjReactArgs<T>& a, const void* vin, const float* cin, void* vmid, float* cmid) {
+    void diff_react_dim(const AdjReactArgs<T>& a, const void* vin, const float* cin, void* vmid, float* cmid,
+                        const CkSide<T>& ck) {
         const OpView<T> op = op_view<T>(c->op);
         const int grid = (a.n + 127) / 128;
         const T* vi = (const T*)vin;
         T* vm = (T*)vmid;
-        if (mode == 2) adj_diff_react_fwd<T, K, 2, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
-        else if (mode == 1) adj_diff_react_fwd<T, K, 1, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
-        else adj_diff_react_fwd<T, K, 0, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid);
+        if (mode == 2) adj_diff_react_fwd<T, K, 2, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid, ck);
+        else if (mode == 1) adj_diff_react_fwd<T, K, 1, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid, ck);
+        else adj_diff_react_fwd<T, K, 0, DIM><<<grid, 128, 0, st>>>(op, a, vi, cin, vm, cmid, ck);
     }
     void diff_react_any(int64_t j, const void* vin, const float* cin, void* vmid, float* cmid, void* vout,
-                        float* cout, void* hout) {
-        if (c->s.prec == P_F64) diff_react<double, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout);
-        else if (c->s.kahan) diff_react<float, true>(j, vin, cin, vmid, cmid, vout, cout, hout);
-        else diff_react<float, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout);
+                        float* cout, void* hout, const void* hin, const uint8_t* kin, int sv, int rs) {
+        if (c->s.prec == P_F64)
+            diff_react<double, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout, hin, kin, sv, rs);
+        else if (c->s.kahan) diff_react<float, true>(j, vin, cin, vmid, cmid, vout, cout, hout, hin, kin, sv, rs);
+        else diff_react<float, false>(j, vin, nullptr, vmid, nullptr, vout, nullptr, hout, hin, kin, sv, rs);
     }
 
     // One diffusion sub-step from `in` to `out` (and the Kahan terms), with the
@@ -473,18 +530,44 @@ struct Adj {
     // One forward step j (from the synchronisation at t_j).  With `store`, every
     // sub-step writes a fresh buffer so that all intermediates the reverse of
     // this step needs stay in place (the state itself is restored from a
-    // checkpoint afterwards).
+    // checkpoint afterwards).  A pending restore makes the step read its
+    // start state from the slot; a pending save is written by its combined
+    // launch (with l >= 3 and no store, the step-I sub-steps before that
+    // launch overwrite the live V, so the save is copied first).
     void fwd_step(int64_t j, bool store) {
         const StepRef ref{nullptr, (long long)(n0 + j)};
-        live_slot = -1;
         const int l = c->l;
+        if (pend_save >= 0 && !store && l >= 3) {
+            copy_state(true, pend_save);
+            pend_save = -1;
+        }
+        const int sv = pend_save, rs = pend_restore;
+        pend_save = pend_restore = -1;
+        live_slot = -1;
+        const void* v0 = rs >= 0 ? b->sV[rs] : c->s.V[c->cur];
+        const float* c0 = b->kahan ? (rs >= 0 ? (const float*)b->sC[rs] : c->s.C[c->cur]) : nullptr;
+        const void* h0 = rs >= 0 ? b->sH[rs] : c->s.S;
+        const uint8_t* k0 = rs >= 0 ? (const uint8_t*)b->sK[rs] : c->s.kk;
         if (!store) {
             int buf = c->cur;
+            const void* x = v0;
+            const float* cx = c0;
             for (int i = 0; i < l - 1; ++i) {
-                launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
+                if (i == 0 && rs >= 0) {
+                    // from the slot (no ghost margin) into the live buffer
+                    DevState v = c->s;
+                    v.vpad = 0;
+                    v.V[buf] = const_cast<void*>(v0);
+                    v.C[buf] = const_cast<float*>(c0);
+                    launch_diffusion(v, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
+                } else {
+                    launch_diffusion(c->s, c->op, buf, false, 0, c->sargs, ref, false, 256, st);
+                }
                 buf ^= 1;
+                x = c->s.V[buf];
+                cx = c->s.C[buf];
             }
-            diff_react_any(j, c->s.V[buf], c->s.C[buf], nullptr, nullptr, c->s.V[buf ^ 1], c->s.C[buf ^ 1], c->s.S);
+            diff_react_any(j, x, cx, nullptr, nullptr, c->s.V[buf ^ 1], c->s.C[buf ^ 1], c->s.S, h0, k0, sv, rs);
             buf ^= 1;
             for (int i = 0; i < l; ++i) {
                 launch_diffusion(c->s, c->op, buf, i == l - 1, 0, c->sargs, ref, false, 256, st);
@@ -493,8 +576,8 @@ struct Adj {
             ++fwd_steps;
             return;
         }
-        const void* x = c->s.V[c->cur];
-        const float* cx = b->kahan ? c->s.C[c->cur] : nullptr;
+        const void* x = v0;
+        const float* cx = c0;
         for (int i = 0; i < l - 1; ++i) {
             b->d1[i] = x;
             diffuse_view(x, b->P[i], cx, b->kahan ? b->CP[i] : nullptr, false, ref, nullptr);
@@ -504,11 +587,11 @@ struct Adj {
         b->d1[l - 1] = x;
         b->rv = b->P[l - 1];
         b->rc = b->kahan ? b->CP[l - 1] : nullptr;
-        b->rh = c->s.S;
-        b->kused = c->s.kk;
+        b->rh = h0;
+        b->kused = k0;
         void* y = b->P[l];
         float* cy = b->kahan ? b->CP[l] : nullptr;
-        diff_react_any(j, x, cx, b->P[l - 1], b->kahan ? b->CP[l - 1] : nullptr, y, cy, b->Hout);
+        diff_react_any(j, x, cx, b->P[l - 1], b->kahan ? b->CP[l - 1] : nullptr, y, cy, b->Hout, h0, k0, sv, rs);
         const void* yi = y;
         const float* cyi = cy;
         for (int i = 0; i < l; ++i) {
@@ -765,6 +848,7 @@ extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors
             else A.loss_at<float>(j, c->s.V[c->cur], false);
         }
         A.restore(0);   // the context keeps its starting state
+        A.flush();
     } else {
         const int64_t key[5] = {n_steps, n_slots, sample_every, n_samples, c->nstep * 2 + c->cur};
         if (!b->graph || std::memcmp(key, b->gkey, sizeof(key)) != 0) {
@@ -786,6 +870,7 @@ extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors
             G.save(0, 0);
             G.reverse(0, n_steps, 0);
             G.restore(0);
+            G.flush();
             cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
             if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("adjoint capture: ") + cudaGetErrorString(e));
             e = cudaGraphInstantiate(&b->graph, g, 0);

@@ -9,12 +9,12 @@ from parity_util import ensure_lib, gpu_available
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
 
 
-def _small(n=12, n_steps=300, seed=0):
+def _small(n=12, n_steps=300, seed=0, d_scale=1.0):
     from oracle import adjoint, fem
 
     wl = I.ms_square_2d(n=n, length=(n - 1) * 0.025)
     rng = np.random.default_rng(seed)
-    d_node = 0.001 * np.exp(0.3 * rng.standard_normal(n * n))
+    d_node = d_scale * 0.001 * np.exp(0.3 * rng.standard_normal(n * n))
     conn = fem.grid_elements(2, wl.n)
     d_elem = adjoint.element_d_from_nodes(conn, d_node)
     sensors = np.sort(rng.choice(n * n, size=8, replace=False))
@@ -49,6 +49,26 @@ def test_adjoint_matches_oracle(precision, tol):
     assert abs(loss - loss_o) <= tol * loss_o
     assert _rel(g, g_o) <= tol
     assert abs(gt - gt_o) <= tol * abs(gt_o)
+
+
+@pytest.mark.parametrize("d_scale,l", [(4.0, 2), (5.0, 3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32_kahan", 2e-3)])
+def test_adjoint_with_diffusion_substeps(d_scale, l, precision, tol):
+    """l > 1 (several diffusion sub-steps per half step, each reversed), with one
+    checkpoint slot (recomputation from the start) and with five."""
+    wl, prob, d_elem, sensors, data, n_steps = _small(n_steps=200, d_scale=d_scale)
+    assert prob.l == l
+    loss_o, g_o, gt_o, _ = prob.gradient(n_steps, sensors, 10, data)
+    for slots in (1, 5):
+        s = _gpu(wl, d_elem, precision)
+        assert s.daeti_get_stability()["l"] == l
+        loss, g, gt = s.daeti_adjoint(sensors, data, n_steps, 10, n_slots=slots, n_elem=len(d_elem))
+        v_end = s.daeti_read_v()
+        s.close()
+        assert abs(loss - loss_o) <= tol * loss_o
+        assert _rel(g, g_o) <= tol
+        assert abs(gt - gt_o) <= tol * abs(gt_o)
+        assert np.all(v_end == 0.0)          # the context is back at its (resting) start
 
 
 def test_checkpoint_slot_count_does_not_change_gradient():
