@@ -38,9 +38,10 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 XU_LANES_PER_SM = 16
 TP06_XU_PER_SUBSTEP = 82.0     # SFU (MUFU) instructions per TP06 sub-step, ncu opcode count (profiles/)
-# DRAM bytes (read + write) per reaction launch from the resting-phase ncu
-# capture in profiles/reaction_tp06_fp32_slab.md (the state stays in L2)
-REACTION_DRAM_BYTES_PER_LAUNCH = 160512.0
+# DRAM bytes (read + write) per reaction launch, mean of three resting-phase
+# launches captured with warm caches (profiles/reaction_tp06_fp32_slab.md; the
+# state stays in L2)
+REACTION_DRAM_BYTES_PER_LAUNCH = 23125.0
 
 
 def _dist():
