@@ -74,10 +74,23 @@ __device__ __forceinline__ void sell_update(const int64_t* __restrict__ chunk_pt
     const int64_t off = chunk_ptr[chunk] + lane;
     const int w = chunk_w[chunk];
     R acc = (R)0;
-    for (int j = 0; j < w; ++j) {
-        const int cj = __ldg(col + off + 32 * (int64_t)j);
-        const R aj = __ldg(val + off + 32 * (int64_t)j);
-        acc = fma(aj, vin[cj] - vi, acc);
+    // batches of 8 entries: all column and value loads of a batch are issued
+    // before its gathers, so a warp keeps up to 16 streaming loads in flight.
+    // Past the row's width an entry is (column i, value 0), like SELL's own
+    // padding, and adds an exact 0; the terms are added in entry order.
+    for (int j = 0; j < w; j += 8) {
+        int cj[8];
+        R aj[8], vj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool in = j + u < w;
+            cj[u] = in ? __ldg(col + off + 32 * (int64_t)(j + u)) : i;
+            aj[u] = in ? __ldg(val + off + 32 * (int64_t)(j + u)) : (R)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vj[u] = vin[cj[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(aj[u], vj[u] - vi, acc);
     }
     R v = vi;
     float cc = ci;
