@@ -430,7 +430,9 @@ static int assemble_and_estimate(daeti_ctx* c, GridTable& tab, bool& table, CsrK
     const double* fib = c->fib_null ? nullptr : c->fib.data();
     std::string err;
     table = false;
-    if (c->mesh_kind == 1) table = build_grid_table(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, tab);
+    // (a grid whose operator already has one row per node keeps that layout)
+    if (c->mesh_kind == 1 && !c->op.per_node)
+        table = build_grid_table(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, tab);
     if (!table) {
         bool ok = c->mesh_kind == 1
                       ? assemble_grid_csr(c->dim, c->n, c->h, c->dl.data(), c->dtr.data(), fib, K, err)
@@ -579,7 +581,12 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
         // node from the CSR rows (entry (dz+1)*9 + (dy+1)*3 + dx+1 for the
         // neighbour at offset (dx, dy, dz); columns ascend, so the terms are
         // added in the CSR order)
-        if (!fresh && (c->op.kind != 0 || !c->op.per_node)) return fail(c, DAETI_EINVAL, "operator layout changed");
+        if (!fresh && c->op.kind != 0) return fail(c, DAETI_EINVAL, "operator layout changed");
+        // a grid prepared with per-layer D gets per-node rows on its first
+        // update with D varying within a layer (a new coefficient array: the
+        // adjoint's captured sweep is dropped)
+        const bool grow = !fresh && !c->op.per_node;
+        if (grow) free_adjoint(c);
         const int64_t nx = c->n[0], ny = c->n[1];
         c->op.kind = 0;
         c->op.per_node = 1;
@@ -600,7 +607,7 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
                 A[(size_t)i * DAETI_ROW + (size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))] = K.val[q] * s;
             }
         }
-        if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
+        if ((fresh || grow) && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
     } else {
         if (!fresh && c->op.kind != 1) return fail(c, DAETI_EINVAL, "operator layout changed");

@@ -91,6 +91,40 @@ def test_heterogeneous_grid_per_node_rows(precision):
     _compare(_heterogeneous(I.tp06_slab_3d(13, 11, 6)), 300, 20, precision)
 
 
+def test_conductivity_update_switches_to_per_node_rows():
+    """A grid prepared with one D per layer gets per-node stencil rows when an
+    update makes D vary within a layer; the run then equals one prepared with
+    that D (same l).  Updating back to the per-layer D keeps per-node rows and
+    agrees with the per-layer table to rounding."""
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    wl = I.tp06_slab_3d(13, 11, 6)
+    f = np.random.default_rng(11).uniform(0.95, 1.0, wl.n_elems)
+    het = (wl.d_long * f, wl.d_trans * f)
+
+    def make(dl, dtr):
+        w = I.Workload(**{**wl.__dict__})
+        w.d_long, w.d_trans = dl, dtr
+        return binding.solver_from_workload(w, precision="fp64")
+
+    a, b = make(wl.d_long, wl.d_trans), make(*het)
+    a.daeti_update_conductivity(het[0], het[1], wl.fibre)
+    assert a.daeti_get_stability()["l"] == b.daeti_get_stability()["l"] == 1
+    a.daeti_advance(10.0)
+    b.daeti_advance(10.0)
+    assert np.array_equal(a.daeti_read_state(), b.daeti_read_state())
+    assert np.array_equal(a.daeti_read_activation(), b.daeti_read_activation())
+    c = make(wl.d_long, wl.d_trans)
+    b.daeti_update_conductivity(wl.d_long, wl.d_trans, wl.fibre)
+    b.daeti_init_state()
+    b.daeti_advance(10.0)
+    c.daeti_advance(10.0)
+    assert np.allclose(b.daeti_read_v(), c.daeti_read_v(), rtol=0.0, atol=1e-9)
+    for s in (a, b, c):
+        s.close()
+
+
 @pytest.mark.parametrize("scheme_name", ["ost", "ostar"])
 def test_scheme_variants(scheme_name):
     wl = I.aniso_sheet_2d(n=21, length=0.2, model="ms")
