@@ -148,10 +148,13 @@ int daeti_add_stimulus(daeti_ctx* ctx, const int64_t* nodes, int64_t n_nodes,
  * ENOMEM, ECUDA. */
 int daeti_prepare(daeti_ctx* ctx);
 
-/* Replace the conductivity after prepare (same mesh and layout) keeping the
- * prepared schedule (dt, l, k_max): reassembles K, recomputes dt_s and
- * lambda_max, and returns DAETI_EUNSTABLE if dt_ad * lambda_max >= 2.  The
- * state is kept.  Used for parameter studies and gradient checks. */
+/* Replace the conductivity after prepare (same mesh) keeping the prepared
+ * schedule (dt, l, k_max): reassembles K, recomputes dt_s and lambda_max,
+ * and returns DAETI_EUNSTABLE if dt_ad * lambda_max >= 2.  On a structured
+ * grid prepared with D constant on each layer, the first update with D
+ * varying within a layer moves the operator to one stencil row per node
+ * (and drops a captured adjoint sweep); that layout is then kept.  The state
+ * is kept.  Used for parameter studies and gradient checks. */
 int daeti_update_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
                               const double* d_trans, const double* fibre);
 
