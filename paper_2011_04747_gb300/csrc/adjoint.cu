@@ -16,7 +16,11 @@
 // States are recomputed from device checkpoints placed by a binomial
 // (revolve-type) schedule: with s free slots and t steps, the next checkpoint
 // goes d = max(1, t - C(s-1+r, s-1)) steps ahead, r the least repetition
-// number with C(s+r, s) >= t.
+// number with C(s+r, s) >= t.  A save or a restore costs no launch of its
+// own: the next forward step's combined diffusion-reaction launch writes
+// the step-start state of each node to the slot (save), or takes V, h and k
+// from the slot and copies its vsync and activation times to the live state
+// (restore).  The whole sweep is one CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
