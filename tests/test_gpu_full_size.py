@@ -1,0 +1,65 @@
+"""The tet-slab and batch workloads at their full bench sizes, in the bench's
+launch configuration (FP32 with compensated V, CUDA graphs of 20 steps).
+
+The oracle cannot run 2 M nodes or 13 M nodes in seconds, so these check
+what holds at any size against paths that the oracle pins at small sizes:
+sampled batch tissues bit for bit against the same tissues advanced alone
+(the single-tissue path is oracle-checked), the smallest Mitchell-Schaeffer
+and TP06 tissues of the batch against the oracle itself, and the full tet
+slab in FP32 against the FP64 path (oracle-checked on small tet meshes)
+within the FP32 tolerances."""
+import numpy as np
+import pytest
+
+import inputs as I
+from parity_util import act_error, ensure_lib, gpu_available, run_oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+
+def test_full_tet_slab_fp32_against_fp64():
+    binding = ensure_lib()
+    wl = I.tet_slab_3d(t_end=50.0)                   # 201 x 201 x 51, 2.06 M nodes
+    out = {}
+    for prec in ("fp32_kahan", "fp64"):
+        s = binding.solver_from_workload(wl, precision=prec, graph_steps=20)
+        assert s.daeti_get_stability()["l"] == 5
+        s.daeti_advance(5.0)
+        out[prec] = (s.daeti_read_v(), s.daeti_read_activation())
+        s.close()
+    (v32, a32), (v64, a64) = out["fp32_kahan"], out["fp64"]
+    assert np.all(np.isfinite(v32))
+    assert float(np.max(np.abs(v32 - v64))) <= 2.0
+    da, same, n_act = act_error(a32, a64)
+    assert same and da <= 0.5
+    assert n_act > 0                                 # the S1 front has started
+
+
+def test_full_batch_sampled_tissues():
+    binding = ensure_lib()
+    wls = I.batch_tissues()                          # 512 tissues, 32..256 nodes a side
+    batch = binding.Batch(precision="fp32_kahan", graph_steps=20)
+    for w in wls:
+        d = binding.describe_workload(w, precision="fp32_kahan")
+        batch.daeti_batch_add(d)
+        d.close()
+    batch.daeti_batch_prepare()
+    assert batch.daeti_batch_info()["n_tissues"] == 512
+    batch.daeti_batch_advance(5.0)
+    sizes = np.array([w.n_nodes for w in wls])
+    rng = np.random.default_rng(20110474)
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes))} | set(rng.choice(len(wls), 6, replace=False).tolist()))
+    for t in picks:
+        s = binding.solver_from_workload(wls[t], precision="fp32_kahan")
+        s.daeti_advance(5.0)
+        assert np.array_equal(batch.daeti_batch_read_v(t), s.daeti_read_v()), t
+        assert np.array_equal(batch.daeti_batch_read_activation(t), s.daeti_read_activation()), t
+        s.close()
+    for model in ("ms", "tp06"):
+        t = min((i for i, w in enumerate(wls) if w.model == model), key=lambda i: sizes[i])
+        o, oa, _ = run_oracle(wls[t], 50, 50)
+        mv = 100.0 if model == "ms" else 1.0
+        assert float(np.max(np.abs(batch.daeti_batch_read_v(t) - o[-1]))) * mv <= 2.0, model
+        da, same, _ = act_error(batch.daeti_batch_read_activation(t), oa)
+        assert same and da <= 0.5, model
+    batch.close()
