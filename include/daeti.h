@@ -133,6 +133,14 @@ int daeti_set_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
  * (params may be NULL for the published defaults). */
 int daeti_set_cell_model(daeti_ctx* ctx, int model, const double* params, int n_params);
 
+/* TP06 cell type of each node (transmural heterogeneity): type[i] in
+ * {0 endocardial, 1 epicardial, 2 mid-myocardial}, n = the mesh's node count,
+ * copied at call; it replaces the single type of daeti_set_cell_model's
+ * parameter.  Before prepare; prepare fails with EINVAL unless the cell model
+ * is TP06 and n still equals the node count.  Errors: EINVAL (n, a null
+ * array or a type out of range), ESTATE (after prepare or before the mesh). */
+int daeti_set_cell_types(daeti_ctx* ctx, int64_t n, const uint8_t* type);
+
 /* Stimulus (Section 3: current injected at a node set): amplitude is added to
  * dV/dt (model units per ms) at every reaction sub-step whose start time t
  * satisfies t0 + p*period <= t < t0 + p*period + duration, p < count

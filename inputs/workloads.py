@@ -60,6 +60,9 @@ class Workload:
     fibre: Optional[np.ndarray] = None       # (n_elem, 3) unit vectors
     stimuli: List[Stimulus] = dataclasses.field(default_factory=list)
     meta: dict = dataclasses.field(default_factory=dict)
+    # TP06 cell type per node (0 endo, 1 epi, 2 mid-myocardial); None: the
+    # type in model_params at every node
+    cell_type: Optional[np.ndarray] = None
 
     @property
     def n_nodes(self) -> int:
@@ -129,13 +132,16 @@ def ms_square_2d(n: int = 41, length: float = 1.0, D: float = 0.001, t_end: floa
 def tp06_slab_3d(nx: int = 101, ny: int = 101, nz: int = 26, h: float = 0.02,
                  d_long: float = 0.0012, d_trans: float = 0.0003, t_end: float = 500.0,
                  celltype: int = 0, corner: float = 0.1, stim_dur: float = 2.0,
-                 amp: float = TP06_CORNER_AMP, dt: float = 0.1) -> Workload:
+                 amp: float = TP06_CORNER_AMP, dt: float = 0.1, transmural: bool = False) -> Workload:
     """3D anisotropic slab (2 x 2 x 0.5 cm at the default size) of trilinear hexes.
 
     Fibres lie in the x-y plane and rotate linearly through the wall: the
     element whose centre is at height z_c has angle
     theta = -60 deg + 120 deg * z_c / L_z, fibre = (cos theta, sin theta, 0).
     Corner stimulus: all nodes with x, y, z <= ``corner`` cm for ``stim_dur`` ms.
+    ``transmural``: TP06 cell type per node by wall depth instead of
+    ``celltype`` everywhere: the lower third of the node layers endocardial,
+    the middle third mid-myocardial, the upper third epicardial.
     """
     n = (nx, ny, nz)
     c = _elem_centres(3, n, h)
@@ -147,11 +153,15 @@ def tp06_slab_3d(nx: int = 101, ny: int = 101, nz: int = 26, h: float = 0.02,
     eps = 1e-9
     corner_nodes = np.nonzero((xyz[:, 0] <= corner + eps) & (xyz[:, 1] <= corner + eps)
                               & (xyz[:, 2] <= corner + eps))[0].astype(np.int64)
+    cell_type = None
+    if transmural:
+        layer = np.arange(nx * ny * nz) // (nx * ny)
+        cell_type = np.where(3 * layer < nz, 0, np.where(3 * layer < 2 * nz, 2, 1)).astype(np.uint8)
     return Workload(
-        name=f"tp06_slab_{nx}x{ny}x{nz}", model="tp06", model_params=(float(celltype),),
-        t_end=t_end, dt=dt, v_threshold=-40.0, dim=3, n=n, h=h,
+        name=f"tp06_slab_{nx}x{ny}x{nz}" + ("_transmural" if transmural else ""), model="tp06",
+        model_params=(float(celltype),), t_end=t_end, dt=dt, v_threshold=-40.0, dim=3, n=n, h=h,
         d_long=np.full(ne, d_long), d_trans=np.full(ne, d_trans), fibre=fib,
-        stimuli=[Stimulus(corner_nodes, 0.0, stim_dur, amp)],
+        stimuli=[Stimulus(corner_nodes, 0.0, stim_dur, amp)], cell_type=cell_type,
     )
 
 

@@ -107,12 +107,26 @@ class TP06:
     GpCa, KpCa, GpK = 0.1238, 0.0005, 0.0146
 
     def __init__(self, celltype=0):
-        self.celltype = int(celltype)
-        self.Gks = 0.098 if self.celltype == 2 else 0.392
-        self.Gto = 0.073 if self.celltype == 0 else 0.294
+        # one cell type for every node, or one per node (an integer array:
+        # transmural heterogeneity); the published per-type constants either way
+        ct = np.asarray(celltype)
+        if ct.ndim == 0:
+            self.celltype = int(ct)
+            self.Gks = 0.098 if self.celltype == 2 else 0.392
+            self.Gto = 0.073 if self.celltype == 0 else 0.294
+        else:
+            self.celltype = ct.astype(np.int64)
+            self.Gks = np.where(self.celltype == 2, 0.098, 0.392)
+            self.Gto = np.where(self.celltype == 0, 0.073, 0.294)
 
     def initial_state(self, n):
         return np.tile(np.asarray(TP06_INIT, dtype=np.float64)[:, None], (1, n))
+
+    def for_nodes(self, idx):
+        """The model of the node subset idx (per-node types follow their nodes)."""
+        if np.ndim(self.celltype) == 0:
+            return self
+        return TP06(self.celltype[idx])
 
     # -- gate steady states and time constants --------------------------------
     def gates(self, V, CaSS):
@@ -142,12 +156,17 @@ class TP06:
         tau_xs = (1400.0 / np.sqrt(1.0 + e((5.0 - V) / 6.0))) * (1.0 / (1.0 + e((V - 35.0) / 15.0))) + 80.0
         r_inf = 1.0 / (1.0 + e((20.0 - V) / 6.0))
         tau_r = 9.5 * e(-(V + 40.0) ** 2 / 1800.0) + 0.8
-        if self.celltype == 0:
-            s_inf = 1.0 / (1.0 + e((V + 28.0) / 5.0))
-            tau_s = 1000.0 * e(-(V + 67.0) ** 2 / 1000.0) + 8.0
+        # s gate: endocardial form for type 0, the other form for types 1 and 2
+        s_inf_endo = 1.0 / (1.0 + e((V + 28.0) / 5.0))
+        tau_s_endo = 1000.0 * e(-(V + 67.0) ** 2 / 1000.0) + 8.0
+        s_inf_other = 1.0 / (1.0 + e((V + 20.0) / 5.0))
+        tau_s_other = 85.0 * e(-(V + 45.0) ** 2 / 320.0) + 5.0 / (1.0 + e((V - 20.0) / 5.0)) + 3.0
+        if np.ndim(self.celltype) == 0:
+            s_inf, tau_s = (s_inf_endo, tau_s_endo) if self.celltype == 0 else (s_inf_other, tau_s_other)
         else:
-            s_inf = 1.0 / (1.0 + e((V + 20.0) / 5.0))
-            tau_s = 85.0 * e(-(V + 45.0) ** 2 / 320.0) + 5.0 / (1.0 + e((V - 20.0) / 5.0)) + 3.0
+            endo = self.celltype == 0
+            s_inf = np.where(endo, s_inf_endo, s_inf_other)
+            tau_s = np.where(endo, tau_s_endo, tau_s_other)
         d_inf = 1.0 / (1.0 + e((-8.0 - V) / 7.5))
         tau_d = ((1.4 / (1.0 + e((-35.0 - V) / 13.0)) + 0.25) * (1.4 / (1.0 + e((V + 5.0) / 5.0)))
                  + 1.0 / (1.0 + e((50.0 - V) / 20.0)))
@@ -258,10 +277,13 @@ class TP06:
         return self.Cm * V / self.F - ions
 
 
-def make_model(name, params=()):
+def make_model(name, params=(), cell_type=None):
+    """cell_type: TP06 type per node (overrides params[0]) or None."""
     if name == "ms":
         return MitchellSchaeffer(*params)
     if name == "tp06":
+        if cell_type is not None:
+            return TP06(np.asarray(cell_type))
         return TP06(int(params[0]) if len(params) else 0)
     if name == "cubic":
         return CubicBistable(*params)

@@ -166,7 +166,7 @@ class Simulation:
             J = self.stimulus_current(idx, t_sub)
             sub = self.S[:, idx]
             if isinstance(self.model, _cells.TP06):
-                self.S[:, idx] = self.model.substep(sub, dt_ar, J, gate_rl=self.gate_rl)
+                self.S[:, idx] = self.model.for_nodes(idx).substep(sub, dt_ar, J, gate_rl=self.gate_rl)
             else:
                 self.S[:, idx] = self.model.substep(sub, dt_ar, J)
 
@@ -207,6 +207,6 @@ class Simulation:
 def simulation_from_workload(wl, scheme="daeti", dt=None, l_round="floor", gate_rl=True):
     """Assemble K, m and build a ``Simulation`` for an ``inputs.Workload``."""
     K, m = _fem.assemble_workload(wl)
-    model = _cells.make_model(wl.model, wl.model_params)
+    model = _cells.make_model(wl.model, wl.model_params, getattr(wl, "cell_type", None))
     return Simulation(K, m, model, wl.stimuli, dt=wl.dt if dt is None else dt, dt0=wl.dt0,
                       scheme=scheme, l_round=l_round, v_threshold=wl.v_threshold, gate_rl=gate_rl)

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "daeti_set_mesh_tet": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, ctypes.c_int64, _I64P]),
     "daeti_set_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
     "daeti_set_cell_model": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
+    "daeti_set_cell_types": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint8)]),
     "daeti_add_stimulus": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]),
     "daeti_prepare": (ctypes.c_int, [_VP]),
@@ -244,6 +245,11 @@ class Solver:
         p = _f64(params) if len(params) else None
         self._check(self.lib.daeti_set_cell_model(self.ctx, m, _ptr(p, ctypes.c_double), 0 if p is None else len(p)))
         self._sizes()
+
+    def daeti_set_cell_types(self, types):
+        """TP06 cell type per node (0 endo, 1 epi, 2 mid-myocardial)."""
+        t = np.ascontiguousarray(types, dtype=np.uint8).reshape(-1)
+        self._check(self.lib.daeti_set_cell_types(self.ctx, t.shape[0], _ptr(t, ctypes.c_uint8)))
 
     def daeti_add_stimulus(self, nodes, t_start, duration, amplitude, period=0.0, count=1):
         nd = _i64(nodes)
@@ -463,6 +469,8 @@ def describe_workload(wl, **options) -> Solver:
     s = Solver(**opts)
     s.daeti_set_mesh_grid(wl.dim, wl.n, wl.h)
     s.daeti_set_conductivity(wl.d_long, wl.d_trans, wl.fibre)
+    if getattr(wl, "cell_type", None) is not None:
+        raise ValueError("a batch tissue takes one cell type (per-node cell types need a Solver)")
     s.daeti_set_cell_model(wl.model, tuple(wl.model_params))
     for st in wl.stimuli:
         s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
@@ -504,6 +512,8 @@ def solver_from_workload(wl, **options) -> Solver:
         s.daeti_set_mesh_grid(wl.dim, wl.n, wl.h)
     s.daeti_set_conductivity(wl.d_long, wl.d_trans, wl.fibre)
     s.daeti_set_cell_model(wl.model, tuple(wl.model_params))
+    if getattr(wl, "cell_type", None) is not None:
+        s.daeti_set_cell_types(wl.cell_type)
     for st in wl.stimuli:
         s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
     s.daeti_prepare()

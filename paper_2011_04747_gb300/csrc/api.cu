@@ -351,6 +351,17 @@ int daeti_set_cell_model(daeti_ctx* c, int model, const double* params, int n_pa
     return DAETI_OK;
 }
 
+int daeti_set_cell_types(daeti_ctx* c, int64_t n, const uint8_t* type) {
+    if (!c) return DAETI_EINVAL;
+    if (c->prepared) return fail(c, DAETI_ESTATE, "cell types cannot change after prepare");
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "set the mesh first");
+    if (n != c->n_nodes || !type) return fail(c, DAETI_EINVAL, "one cell type per node");
+    for (int64_t i = 0; i < n; ++i)
+        if (type[i] > 2) return fail(c, DAETI_EINVAL, "TP06 cell types are 0, 1 or 2");
+    c->ctypes.assign(type, type + n);
+    return DAETI_OK;
+}
+
 int daeti_add_stimulus(daeti_ctx* c, const int64_t* nodes, int64_t n_nodes, double t_start, double duration,
                        double amplitude, double period, int count) {
     if (!c) return DAETI_EINVAL;
@@ -643,6 +654,8 @@ int daeti_prepare(daeti_ctx* c) {
     if (!c->mesh_kind || !c->have_cond || !c->model)
         return fail(c, DAETI_ESTATE, "prepare needs mesh, conductivity and cell model");
     const int64_t N = c->n_nodes;
+    if (!c->ctypes.empty() && (c->model != DAETI_MODEL_TP06 || (int64_t)c->ctypes.size() != N))
+        return fail(c, DAETI_EINVAL, "per-node cell types need the TP06 model and one type per node");
     c->s = DevState();
     c->op = DiffOp();
     c->s.prec = c->opt.precision == DAETI_FP64 ? P_F64 : P_F32;
@@ -706,6 +719,11 @@ int daeti_prepare(daeti_ctx* c) {
     if ((rc = dalloc(c, &c->s.vsync, R * N)) || (rc = dalloc(c, &c->s.act, R * N))) return rc;
     if ((rc = dalloc(c, &p, N))) return rc;
     c->s.kk = (uint8_t*)p;
+    if (!c->ctypes.empty()) {
+        if ((rc = dalloc(c, &p, N))) return rc;
+        CK(cpy_(c, p, c->ctypes.data(), N, cudaMemcpyHostToDevice));
+        c->s.ctype = (const uint8_t*)p;
+    }
     if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
     c->s.counts = (int*)p;
     if ((rc = dalloc(c, &p, sizeof(int) * (size_t)(c->kmax + 1) * N))) return rc;

@@ -49,6 +49,7 @@ struct daeti_ctx {
     int cur = 0;
     int par = 0;
     void* scratch = nullptr;   // n doubles for conversions
+    std::vector<uint8_t> ctypes;  // TP06 cell type per node (empty: the model parameter everywhere)
     void* stage = nullptr;     // n_states x n doubles: a caller's initial state (allocated on first use)
     void* probe = nullptr;     // probe node indices then values (daeti_read_v_nodes)
     int64_t probe_cap = 0;     // probes the buffer holds

@@ -30,6 +30,7 @@ struct DevState {
     int* lists = nullptr;                 // per-k node lists of the next step A: list k at lists + k*n
     int* counts = nullptr;                // [2][DAETI_MAX_K] bucket lengths (k >= 1) by step parity; [par][0]
                                           // = bucketing mode: 1 lists, -K every node expected at k = K
+    const uint8_t* ctype = nullptr;       // TP06 cell type per node (nullable: ModelArgs::celltype everywhere)
     unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
     StimDev* stims = nullptr;             // stimulus table
     int n_stims = 0;

@@ -39,6 +39,7 @@ struct ReactArgs {
     StepRef step;
     R ms_r_in, ms_r_out, ms_r_open, ms_r_close, ms_vgate;
     TP06Params tp;
+    const uint8_t* ctype;   // TP06 cell type per node, or null (tp.celltype everywhere)
 };
 
 // Sum of the amplitudes of the stimuli in `mask` that are on at time t.
@@ -94,15 +95,17 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
         x.f2 = S[15 * 32];
         x.fcass = S[16 * 32];
         x.RR = S[17 * 32];
-        if (a.tp.gate_rl) {
+        TP06Params tp = a.tp;
+        if (a.ctype) tp.celltype = a.ctype[i];
+        if (tp.gate_rl) {
             for (int s = 0; s < k; ++s) {
                 R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-                tp06_substep<R, true>(x, cp, h, J, a.tp);
+                tp06_substep<R, true>(x, cp, h, J, tp);
             }
         } else {
             for (int s = 0; s < k; ++s) {
                 R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-                tp06_substep<R, false>(x, cp, h, J, a.tp);
+                tp06_substep<R, false>(x, cp, h, J, tp);
             }
         }
         a.V[i] = x.V;
@@ -290,6 +293,7 @@ ReactArgs<R> react_args(const DevState& s, const ModelArgs& m, double dt, StepRe
     a.ms_vgate = (R)m.ms[4];
     a.tp.celltype = m.celltype;
     a.tp.gate_rl = m.gate_rl;
+    a.ctype = s.ctype;
     return a;
 }
 

@@ -91,6 +91,44 @@ def test_heterogeneous_grid_per_node_rows(precision):
     _compare(_heterogeneous(I.tp06_slab_3d(13, 11, 6)), 300, 20, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_transmural_slab_per_node_cell_types(precision):
+    """TP06 endocardial, mid-myocardial and epicardial layers through the wall
+    (one cell type per node) against the oracle over the upstroke and plateau."""
+    wl = I.tp06_slab_3d(13, 11, 9, transmural=True)
+    _compare(wl, 1500, 100, precision)
+
+
+def test_per_node_cell_types_of_one_type_equal_the_model_parameter():
+    from parity_util import ensure_lib
+
+    binding = ensure_lib()
+    for ct in (0, 1, 2):
+        wl = I.tp06_slab_3d(9, 7, 5, celltype=ct)
+        w2 = I.Workload(**{**wl.__dict__})
+        w2.cell_type = np.full(wl.n_nodes, ct, dtype=np.uint8)
+        a = binding.solver_from_workload(wl, precision="fp32_kahan")
+        b = binding.solver_from_workload(w2, precision="fp32_kahan")
+        a.daeti_advance(20.0)
+        b.daeti_advance(20.0)
+        assert np.array_equal(a.daeti_read_state(), b.daeti_read_state()), ct
+        a.close()
+        b.close()
+    s = binding.Solver()
+    s.daeti_set_mesh_grid(2, (5, 5), 0.025)
+    for bad in (np.zeros(24, np.uint8), np.full(25, 3, np.uint8)):
+        with pytest.raises(binding.DaetiError) as e:
+            s.daeti_set_cell_types(bad)
+        assert e.value.code == binding.EINVAL
+    s.daeti_set_conductivity(np.full(16, 0.001), None, None)
+    s.daeti_set_cell_model("ms")
+    s.daeti_set_cell_types(np.zeros(25, np.uint8))
+    with pytest.raises(binding.DaetiError) as e:
+        s.daeti_prepare()                        # cell types need the TP06 model
+    assert e.value.code == binding.EINVAL
+    s.close()
+
+
 def test_conductivity_update_switches_to_per_node_rows():
     """A grid prepared with one D per layer gets per-node stencil rows when an
     update makes D vary within a layer; the run then equals one prepared with

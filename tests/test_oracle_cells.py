@@ -196,3 +196,35 @@ def test_tp06_adaptive_k_converges_to_fine_step():
     t_s = np.arange(len(tr)) * 0.1
     dv = metrics.aligned_max_dv(t_s, np.array(tr), np.interp(t_s, t_f, fine), sim.act[0], up_f)
     assert dv < 8.0
+
+
+def test_tp06_per_node_cell_types_match_each_type_alone():
+    """Transmural heterogeneity: a per-node type array integrates every node as
+    the model of that node's type alone (the reaction is local to the node),
+    the three types give three different action potentials, and an array of
+    one type equals the scalar model."""
+    types = np.array([0, 1, 2, 2, 0, 1])
+    mixed = cells.TP06(types)
+    alone = [cells.TP06(int(t)) for t in types]
+    S = mixed.initial_state(len(types))
+    Ss = [m.initial_state(1) for m in alone]
+    dt = 0.1
+    gap = np.zeros(3)                      # largest V difference of type pairs (0,1), (0,2), (1,2)
+    for step in range(3500):
+        J = np.full(len(types), 52.0 if step * dt < 1.0 else 0.0)
+        S = mixed.substep(S, dt, J)
+        for q, m in enumerate(alone):
+            Ss[q] = m.substep(Ss[q], dt, J[q:q + 1])
+        v = S[0]
+        gap = np.maximum(gap, np.abs([v[0] - v[1], v[0] - v[2], v[1] - v[2]]))
+        assert abs(v[0] - v[4]) < 1e-9 and abs(v[1] - v[5]) < 1e-9 and abs(v[2] - v[3]) < 1e-9
+    for q in range(len(types)):
+        assert np.allclose(S[:, q], Ss[q][:, 0], rtol=1e-12, atol=1e-12)
+    assert gap.min() > 5.0                 # the three types repolarise differently
+    one = cells.TP06(np.zeros(3, dtype=np.int64))
+    S1, S0 = one.initial_state(3), cells.TP06(0).initial_state(3)
+    for _ in range(50):
+        S1 = one.substep(S1, 0.1, np.full(3, 52.0))
+        S0 = cells.TP06(0).substep(S0, 0.1, np.full(3, 52.0))
+    assert np.allclose(S1, S0, rtol=1e-14, atol=0.0)
+
