@@ -66,6 +66,10 @@ extern "C" {
 #define DAETI_L_FLOOR 0       /* l = floor(dt / (2 dt_s)), as printed in Section 2 */
 #define DAETI_L_CEIL 1        /* l = ceil(dt / (2 dt_s)) */
 
+/* the dV/dt of Section 2's k rule ("dV/dt at the previous iteration") */
+#define DAETI_K_TOTAL 0       /* (V(t_n) - V(t_{n-1})) / dt of the split solution at the synchronisations */
+#define DAETI_K_REACTION 1    /* the reaction's dV/dt at the last sub-step of the previous step A */
+
 /* cell models */
 #define DAETI_MODEL_MS 1      /* Mitchell-Schaeffer, params {tau_in, tau_out, tau_open, tau_close, v_gate} */
 #define DAETI_MODEL_TP06 2    /* ten Tusscher-Panfilov 2006, params {celltype: 0 endo, 1 epi, 2 mid} */
@@ -88,13 +92,15 @@ typedef struct daeti_options {
     int32_t react_block;       /* threads per block of the reaction kernel (0 = default) */
     int32_t diff_block;        /* threads per block of the diffusion kernel (0 = default) */
     int32_t fuse_diffusion;    /* 1: last diffusion sub-step of step I inside the reaction launch */
+    int32_t k_rule;            /* DAETI_K_TOTAL | DAETI_K_REACTION (single tissues; the batch and the
+                                  adjoint take DAETI_K_TOTAL) */
 } daeti_options;
 
 typedef struct daeti_ctx daeti_ctx;
 
 /* Fill *opt with defaults: FP32_KAHAN, DAETI, FLOOR, dt = 0.1, dt0 = 0.01,
  * v_threshold = NaN, Rush-Larsen gates, bucketing on, 20 steps per graph,
- * default block sizes, fused diffusion on. */
+ * default block sizes, fused diffusion on, k rule DAETI_K_TOTAL. */
 void daeti_default_options(daeti_options* opt);
 
 /* Create a context.  opt may be NULL (defaults).  *out receives the handle.

@@ -45,6 +45,10 @@ class MitchellSchaeffer:
         dv, dh = self.rhs(S, J)
         return np.stack([S[0] + dt * dv, S[1] + dt * dh])
 
+    def dvdt(self, S, J):
+        """dv/dt of a forward-Euler sub-step from S (model units per ms)."""
+        return self.rhs(S, J)[0]
+
 
 class CubicBistable:
     """Test-only Nagumo model dv/dt = a_r v (1 - v)(v - a) (exact front speed known)."""
@@ -62,7 +66,11 @@ class CubicBistable:
 
     def substep(self, S, dt, J):
         v = S[0]
-        return (v + dt * (self.a_r * v * (1.0 - v) * (v - self.a) + J))[None, :]
+        return (v + dt * self.dvdt(S, J))[None, :]
+
+    def dvdt(self, S, J):
+        v = S[0]
+        return self.a_r * v * (1.0 - v) * (v - self.a) + J
 
 
 # ---------------------------------------------------------------------------
@@ -266,6 +274,10 @@ class TP06:
                 out[6 + gi] = g + dt * (inf[gi] - g) / tau[gi]
         out[18] = S[18] + dt * dRR
         return out
+
+    def dvdt(self, S, J):
+        """dV/dt of a sub-step from S (mV/ms)."""
+        return self.rates(S, J)[0]
 
     def total_charge(self, S):
         """Cm V / F minus the cell's ion content (Na, K, buffered Ca): constant along the ODEs."""

@@ -101,7 +101,7 @@ class Simulation:
     """The split scheme on one tissue, plain and unfused (FP64)."""
 
     def __init__(self, K, m, model, stimuli=(), dt=0.1, dt0=0.01, scheme="daeti",
-                 l_round="floor", v_threshold=None, gate_rl=True, state0=None):
+                 l_round="floor", v_threshold=None, gate_rl=True, state0=None, k_rule="total"):
         self.K = sp.csr_matrix(K)
         self.m = np.asarray(m, dtype=np.float64)
         self.n_nodes = self.K.shape[0]
@@ -134,6 +134,13 @@ class Simulation:
         self.n = 0
         self.v_sync = self.S[0].copy()          # V(t_{n-1}) at the last synchronisation
         self.k = np.ones(self.n_nodes, dtype=np.int64)
+        # dV/dt of the k rule (reading R-k): "total", the split solution's
+        # (V(t_n) - V(t_{n-1}))/dt; "reaction" (reading R-k2), the reaction's
+        # dV/dt at each node's last sub-step of the previous step II (0 at t_0)
+        if k_rule not in ("total", "reaction"):
+            raise ValueError(k_rule)
+        self.k_rule = k_rule
+        self.rrate = np.zeros(self.n_nodes)
         self.act = np.full(self.n_nodes, -1.0)
         self.minv = 1.0 / self.m
         self._members = []
@@ -165,10 +172,14 @@ class Simulation:
             t_sub = t_n + s * dt_ar
             J = self.stimulus_current(idx, t_sub)
             sub = self.S[:, idx]
+            model = self.model.for_nodes(idx) if isinstance(self.model, _cells.TP06) else self.model
+            if self.k_rule == "reaction":
+                last = k[idx] == s + 1          # nodes taking their last sub-step
+                self.rrate[idx[last]] = model.dvdt(sub, J)[last]
             if isinstance(self.model, _cells.TP06):
-                self.S[:, idx] = self.model.for_nodes(idx).substep(sub, dt_ar, J, gate_rl=self.gate_rl)
+                self.S[:, idx] = model.substep(sub, dt_ar, J, gate_rl=self.gate_rl)
             else:
-                self.S[:, idx] = self.model.substep(sub, dt_ar, J)
+                self.S[:, idx] = model.substep(sub, dt_ar, J)
 
     # -- synchronisation at t_{n+1} ----------------------------------------------
     def sync(self):
@@ -178,7 +189,10 @@ class Simulation:
             up = (self.act < 0.0) & (self.v_sync < self.v_th) & (V >= self.v_th)
             frac = (self.v_th - self.v_sync[up]) / (V[up] - self.v_sync[up])
             self.act[up] = t_prev + self.dt * frac
-        rate = (V - self.v_sync) / self.dt * self.model.vscale
+        if self.k_rule == "reaction":
+            rate = self.rrate * self.model.vscale
+        else:
+            rate = (V - self.v_sync) / self.dt * self.model.vscale
         self.k = k_rule(rate, self.k_max) if self.adaptive_k else np.ones(self.n_nodes, dtype=np.int64)
         self.v_sync = V.copy()
 
@@ -204,9 +218,10 @@ class Simulation:
         return self.n * self.dt
 
 
-def simulation_from_workload(wl, scheme="daeti", dt=None, l_round="floor", gate_rl=True):
+def simulation_from_workload(wl, scheme="daeti", dt=None, l_round="floor", gate_rl=True, k_rule="total"):
     """Assemble K, m and build a ``Simulation`` for an ``inputs.Workload``."""
     K, m = _fem.assemble_workload(wl)
     model = _cells.make_model(wl.model, wl.model_params, getattr(wl, "cell_type", None))
     return Simulation(K, m, model, wl.stimuli, dt=wl.dt if dt is None else dt, dt0=wl.dt0,
-                      scheme=scheme, l_round=l_round, v_threshold=wl.v_threshold, gate_rl=gate_rl)
+                      scheme=scheme, l_round=l_round, v_threshold=wl.v_threshold, gate_rl=gate_rl,
+                      k_rule=k_rule)

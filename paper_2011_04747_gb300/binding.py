@@ -52,6 +52,7 @@ class daeti_options(ctypes.Structure):
         ("react_block", ctypes.c_int32),
         ("diff_block", ctypes.c_int32),
         ("fuse_diffusion", ctypes.c_int32),
+        ("k_rule", ctypes.c_int32),
     ]
 
 
@@ -170,7 +171,7 @@ class Solver:
 
     def __init__(self, precision="fp32_kahan", scheme="daeti", dt=0.1, dt0=0.01, l_rounding="floor",
                  v_threshold: Optional[float] = None, gate_rush_larsen=True, bucket_k=True, graph_steps=20,
-                 react_block=0, diff_block=0, fuse_diffusion=True, stream=None):
+                 react_block=0, diff_block=0, fuse_diffusion=True, k_rule="total", stream=None):
         self.lib = load_library()
         o = daeti_options()
         self.lib.daeti_default_options(ctypes.byref(o))
@@ -186,6 +187,7 @@ class Solver:
         o.react_block = int(react_block)
         o.diff_block = int(diff_block)
         o.fuse_diffusion = int(bool(fuse_diffusion))
+        o.k_rule = {"total": 0, "reaction": 1}[k_rule] if isinstance(k_rule, str) else int(k_rule)
         self.options = o
         self.precision = o.precision
         h = _VP()

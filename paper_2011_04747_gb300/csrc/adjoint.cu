@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128) adj_diff_react_fwd(OpView<R> op, AdjReact
     }
     R v;
     float c;
-    diffuse_node<R, DIM, KAHAN>(op, vin, cin, i, v, c);
+    diffuse_node<R, DIM, KAHAN, false, true>(op, vin, cin, i, v, c);
     if (!KAHAN) c = 0.f;
     if (vmid) {
         vmid[i] = v;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) adj_mu_dgrad(OpView<R> op, int n, const R
     if (t < n) {
         R v;
         float cc;
-        diffuse_node<R, DIM, false>(op, mu_in, nullptr, (int)t, v, cc);
+        diffuse_node<R, DIM, false, false, true>(op, mu_in, nullptr, (int)t, v, cc);
         mu_out[t] = v;
     }
     if (t < n_elem) elem_dgrad<R>(t, dim, nx, ny, mu_in, vin, dt_ad, kr, g);
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(256) adj_mu_react_bwd(OpView<R> op, AdjReactAr
     if (t < a.n) {
         R v, gn;
         float cc;
-        diffuse_node<R, DIM, false>(op, mu_in, nullptr, (int)t, v, cc);
+        diffuse_node<R, DIM, false, false, true>(op, mu_in, nullptr, (int)t, v, cc);
         mu_out[t] = react_bwd_node<R, KAHAN>(a, (int)t, rv, rc, rh, kused, v, lamh, m, gn);
         gt = (double)gn;
     }
@@ -811,6 +811,7 @@ extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors
     if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
     if (c->model != DAETI_MODEL_MS || c->mesh_kind != 1)
         return fail(c, DAETI_EUNSUPPORTED, "the adjoint supports Mitchell-Schaeffer on structured grids");
+    if (c->s.rrate) return fail(c, DAETI_EUNSUPPORTED, "the adjoint takes the k rule DAETI_K_TOTAL");
     for (int64_t e = 0; e < c->n_elem; ++e)
         if (c->dl[e] != c->dtr[e]) return fail(c, DAETI_EUNSUPPORTED, "the adjoint needs isotropic elements");
     if (n_steps < 1 || n_sensors < 1 || n_sensors > 65536 || sample_every < 1 || !sensors || !data || n_slots < 1)

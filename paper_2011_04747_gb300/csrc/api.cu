@@ -229,7 +229,7 @@ int daeti_create(daeti_ctx** out, const daeti_options* opt) {
         o = *opt;
     }
     if (!(o.dt > 0) || !(o.dt0 > 0) || o.precision < 0 || o.precision > 2 || o.scheme < 0 || o.scheme > 2 ||
-        o.l_rounding < 0 || o.l_rounding > 1 || o.graph_steps < 0)
+        o.l_rounding < 0 || o.l_rounding > 1 || o.graph_steps < 0 || o.k_rule < 0 || o.k_rule > 1)
         return DAETI_EINVAL;
     if (o.graph_steps % 2) o.graph_steps += 1;
     int ndev = 0;
@@ -724,6 +724,9 @@ int daeti_prepare(daeti_ctx* c) {
         CK(cpy_(c, p, c->ctypes.data(), N, cudaMemcpyHostToDevice));
         c->s.ctype = (const uint8_t*)p;
     }
+    if (c->opt.k_rule == DAETI_K_REACTION && c->sargs.adaptive) {
+        if ((rc = dalloc(c, &c->s.rrate, R * N))) return rc;
+    }
     if ((rc = dalloc(c, &p, 4 * 2 * DAETI_MAX_K))) return rc;
     c->s.counts = (int*)p;
     if ((rc = dalloc(c, &p, sizeof(int) * (size_t)(c->kmax + 1) * N))) return rc;
@@ -851,6 +854,7 @@ int daeti_init_state(daeti_ctx* c, const double* state) {
                       c->s.kahan ? c->s.C[0] : nullptr, c->s.kahan ? c->s.C[1] : nullptr, c->stream);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(c->s.kk, 1, N, c->stream));
+    if (c->s.rrate) CK(cudaMemsetAsync(c->s.rrate, 0, rsize(c) * N, c->stream));   // first step: rate 0
     CK(cudaMemsetAsync(c->s.counts, 0, 4 * 2 * DAETI_MAX_K, c->stream));
     launch_rebuild_lists(c->s, 0, c->stream);   // every node in the k = 1 list
     CK(cudaMemsetAsync(c->s.flags, 0, 16, c->stream));

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev*
         SyncParams<R> p = sp;
         p.rate_scale = (R)t.rate_scale;
         p.vth = (R)t.vth;
-        sync_node(p, i, v);
+        sync_node<R, false>(p, i, v);
     }
 }
 
@@ -128,6 +128,7 @@ void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t
     sp.flags = b->s_all.flags;
     sp.dt = b->dt;
     sp.rate_scale = (R)(1.0 / b->dt);
+    sp.rrate = nullptr;
     sp.vth = (R)0;
     sp.kmax = b->kmax;
     sp.adaptive = b->sargs.adaptive;
@@ -228,7 +229,7 @@ int daeti_batch_create(daeti_batch** out, const daeti_options* opt) {
         o = *opt;
     }
     if (!(o.dt > 0) || !(o.dt0 > 0) || o.precision < 0 || o.precision > 2 || o.scheme != DAETI_SCHEME_DAETI ||
-        o.graph_steps < 0)
+        o.graph_steps < 0 || o.k_rule != DAETI_K_TOTAL)
         return DAETI_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DAETI_ECUDA;

@@ -17,19 +17,21 @@ struct MSParams {
 // One Mitchell-Schaeffer forward-Euler sub-step with the gate branch given:
 // v' = h v^2 (1-v)/tau_in - v/tau_out + J; h' = (1-h)/tau_open if `low`
 // (v < v_gate) else -h/tau_close.
+// Returns dv/dt of the sub-step (model units per ms).
 template <typename R>
-__device__ __forceinline__ void ms_substep_b(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out, R r_open,
-                                             R r_close, bool low) {
+__device__ __forceinline__ R ms_substep_b(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out, R r_open,
+                                          R r_close, bool low) {
     R dv = h * v * v * ((R)1 - v) * r_in - v * r_out + J;
     R dh = low ? ((R)1 - h) * r_open : -h * r_close;
     add_comp(v, cv, dt * dv);
     h += dt * dh;
+    return dv;
 }
 
 template <typename R>
-__device__ __forceinline__ void ms_substep(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out,
-                                           R r_open, R r_close, R v_gate) {
-    ms_substep_b(v, cv, h, dt, J, r_in, r_out, r_open, r_close, v < v_gate);
+__device__ __forceinline__ R ms_substep(R& v, float* cv, R& h, R dt, R J, R r_in, R r_out,
+                                        R r_open, R r_close, R v_gate) {
+    return ms_substep_b(v, cv, h, dt, J, r_in, r_out, r_open, r_close, v < v_gate);
 }
 
 // ------------------------------------------------------------------ TP06
@@ -99,8 +101,9 @@ __device__ __forceinline__ double x_over_expm1<double>(double x, double e) {
 // Every exponential exp(a V + b) (and c exp(a V) as exp(a V + ln c)) is
 // written as 2^(a' V + b') with the constants scaled by log2(e) at compile
 // time, one FMA and one SFU operation each.
+// Returns dV/dt of the sub-step (mV/ms).
 template <typename R, bool RL = true>
-__device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
+__device__ __forceinline__ R tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
     typedef TP06Consts C;
     typedef Fm<R> M;
     const R one = (R)1;
@@ -306,6 +309,7 @@ __device__ __forceinline__ void tp06_substep(TP06State<R>& x, float* cv, R dt, R
     x.Nai = fma(dt, dNai, x.Nai);
     x.Ki = fma(dt, dKi, x.Ki);
     x.RR = fma(dt, dRR, x.RR);
+    return dV;
 }
 
 }  // namespace daeti

@@ -151,6 +151,8 @@ struct SyncParams {
     int* uflag;        // set when a node's k differs from the expected uniform k (mode -K)
     double dt;
     R rate_scale;      // (model units -> mV) / dt: dV/dt of the k rule in mV/ms per unit difference
+    const R* rrate = nullptr;   // nullable: dV/dt of each node's last reaction sub-step (model units per ms)
+    R rrate_scale = (R)1;       // model units -> mV
     R vth;             // activation threshold
     int kmax;
     int adaptive;      // 0: k = 1 (OST)
@@ -158,13 +160,15 @@ struct SyncParams {
 };
 
 // Section 2's k rule from the rate of the split solution over the last step
-// (reading R-k) and the first-upward-crossing activation time (R-LAT).
-template <typename R>
+// (reading R-k; with rrate, the reaction's rate at its last sub-step, reading
+// R-k2) and the first-upward-crossing activation time (R-LAT).
+// EXT: p.rrate may be set (compiled out otherwise).
+template <typename R, bool EXT>
 __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) {
     R vold = p.vsync[i];
     int k = 1;
     if (p.adaptive) {
-        R rate = (vnew - vold) * p.rate_scale;
+        R rate = (EXT && p.rrate) ? p.rrate[i] * p.rrate_scale : (vnew - vold) * p.rate_scale;
         int k0 = rate > (R)0 ? 5 : 1;
         R a = fabs(rate);
         a = a < (R)1e6 ? a : (R)1e6;          // also maps NaN to 1e6

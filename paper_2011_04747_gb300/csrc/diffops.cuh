@@ -114,7 +114,9 @@ struct OpView {
 };
 
 // One sub-step at node i from vin (and cin), any layout (PAD: see stencil_update).
-template <typename R, int DIM, bool KAHAN, bool PAD = false>
+// EXT: the operator may hold one row per node (op.per_node); without it the
+// per-node test is compiled out and only the per-class table is read.
+template <typename R, int DIM, bool KAHAN, bool PAD, bool EXT>
 __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __restrict__ vin, const float* cin, int i,
                                              R& vout, float& cout) {
     const R vi = vin[i];
@@ -125,9 +127,10 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
         const int nxy = op.nx * op.ny;
         const int nx = op.nx;
         auto fetch = [&](int dx, int dy, int dz) { return vin[i + dx + dy * nx + dz * nxy]; };
-        if (PAD && (op.per_node || op.cls)) {
+        const bool pn = EXT && op.per_node;
+        if (PAD && (pn || op.cls)) {
             // no boundary tests: the table row is all the stencil needs
-            const R* crow = op.coef + (size_t)(op.per_node ? i : op.cls[i]) * DAETI_ROW;
+            const R* crow = op.coef + (size_t)(pn ? i : op.cls[i]) * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, 1, 1, 1, 3, vi, ci, fetch, vout, cout);
         } else {
             const int x = i % op.nx;
@@ -135,7 +138,7 @@ __device__ __forceinline__ void diffuse_node(const OpView<R>& op, const R* __res
             const int y = yz % op.ny;
             const int z = yz / op.ny;
             const int cx = bclass(x, op.nx), cy = bclass(y, op.ny);
-            const R* crow = op.coef + (op.per_node ? (size_t)i : (size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
+            const R* crow = op.coef + (pn ? (size_t)i : (size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             stencil_update<R, (DIM == 0 ? 3 : DIM), KAHAN, PAD>(crow, cx, cy, z, op.nz, vi, ci, fetch, vout, cout);
         }
     }

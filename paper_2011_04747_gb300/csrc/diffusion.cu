@@ -23,7 +23,9 @@
 
 namespace daeti {
 
-template <typename R, int DIM, bool KAHAN, bool SYNC, bool PAD>
+// EXT: per-node operator rows and the reaction-rate k rule are possible
+// (their tests are compiled out of the plain instance).
+template <typename R, int DIM, bool KAHAN, bool SYNC, bool PAD, bool EXT>
 __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const R* __restrict__ vin, R* vout,
                                                      const float* cin, float* cout, SyncParams<R> sp) {
     pdl_wait();
@@ -34,10 +36,10 @@ __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const
     if (valid) {
         R v;
         float cc;
-        diffuse_node<R, DIM, KAHAN, PAD>(op, vin, cin, i, v, cc);
+        diffuse_node<R, DIM, KAHAN, PAD, EXT>(op, vin, cin, i, v, cc);
         vout[i] = v;
         if (KAHAN) cout[i] = cc;
-        if (SYNC) k = sync_node(sp, i, v);
+        if (SYNC) k = sync_node<R, EXT>(sp, i, v);
     }
     if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, valid);
 }
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, in
                                           KAHAN ? cin[i] : 0.f, fetch, v, cc);
             vout[i] = v;
             if (KAHAN) cout[i] = cc;
-            if (SYNC) k = sync_node(sp, i, v);
+            if (SYNC) k = sync_node<R, false>(sp, i, v);
         }
         if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
         __syncthreads();   // the plane z - 1 buffer is refilled next
@@ -123,6 +125,8 @@ static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef st
     sp.uflag = s.flags + 2 + par;
     sp.dt = sa.dt;
     sp.rate_scale = (R)(sa.vscale / sa.dt);
+    sp.rrate = (const R*)s.rrate;
+    sp.rrate_scale = (R)sa.vscale;
     sp.vth = (R)sa.vth;
     sp.kmax = sa.kmax;
     sp.adaptive = sa.adaptive;
@@ -133,10 +137,18 @@ static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef st
 template <typename R, int DIM, bool KAHAN, bool PAD>
 static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl, const OpView<R>& op, int n,
                        const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
-    if (sync)
-        launch_ex(substep_kernel<R, DIM, KAHAN, true, PAD>, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    const bool ext = op.per_node || (sync && sp.rrate);
+    if (sync && ext)
+        launch_ex(substep_kernel<R, DIM, KAHAN, true, PAD, true>, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else if (sync)
+        launch_ex(substep_kernel<R, DIM, KAHAN, true, PAD, false>, grid, block, st, pdl, op, n, vin, vout, cin, cout,
+                  sp);
+    else if (ext)
+        launch_ex(substep_kernel<R, DIM, KAHAN, false, PAD, true>, grid, block, st, pdl, op, n, vin, vout, cin, cout,
+                  sp);
     else
-        launch_ex(substep_kernel<R, DIM, KAHAN, false, PAD>, grid, block, st, pdl, op, n, vin, vout, cin, cout, sp);
+        launch_ex(substep_kernel<R, DIM, KAHAN, false, PAD, false>, grid, block, st, pdl, op, n, vin, vout, cin,
+                  cout, sp);
 }
 
 template <typename R, int DIM, bool KAHAN>
@@ -163,7 +175,7 @@ template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
                        StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
-    if (dop.kind == 0 && block == 0 && !dop.per_node) {
+    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate)) {
         // structured grid, shared-memory tiles
         const OpView<R> op = op_view<R>(dop);
         const R* vin = (const R*)s.V[src];

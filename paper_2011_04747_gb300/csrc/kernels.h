@@ -31,6 +31,8 @@ struct DevState {
     int* counts = nullptr;                // [2][DAETI_MAX_K] bucket lengths (k >= 1) by step parity; [par][0]
                                           // = bucketing mode: 1 lists, -K every node expected at k = K
     const uint8_t* ctype = nullptr;       // TP06 cell type per node (nullable: ModelArgs::celltype everywhere)
+    void* rrate = nullptr;                // k rule from the reaction rate: dV/dt of each node's last
+                                          // sub-step, written by step A, read by the next synchronisation
     unsigned* stim_mask = nullptr;        // per-node stimulus membership bits (nullable)
     StimDev* stims = nullptr;             // stimulus table
     int n_stims = 0;

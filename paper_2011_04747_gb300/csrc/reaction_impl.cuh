@@ -40,6 +40,7 @@ struct ReactArgs {
     R ms_r_in, ms_r_out, ms_r_open, ms_r_close, ms_vgate;
     TP06Params tp;
     const uint8_t* ctype;   // TP06 cell type per node, or null (tp.celltype everywhere)
+    R* rrate;               // dV/dt of each node's last sub-step (k rule from the reaction rate), or null
 };
 
 // Sum of the amplitudes of the stimuli in `mask` that are on at time t.
@@ -55,7 +56,9 @@ __device__ __forceinline__ R stim_current(unsigned mask, const StimDev* stims, d
 }
 
 // Integrate the k sub-steps of one node (state loaded, advanced, stored).
-template <typename R, int MODEL, bool KAHAN>
+// EXT: per-node TP06 cell types and the reaction-rate record are possible
+// (compiled out of the plain instance).
+template <typename R, int MODEL, bool KAHAN, bool EXT>
 __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, double tn, bool any_stim, R v0,
                                            float c0) {
     const unsigned smask = any_stim ? a.stim_mask[i] : 0u;
@@ -68,7 +71,8 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
         R g = a.S[i];
         for (int s = 0; s < k; ++s) {
             R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-            ms_substep(v, cp, g, h, J, a.ms_r_in, a.ms_r_out, a.ms_r_open, a.ms_r_close, a.ms_vgate);
+            const R dv = ms_substep(v, cp, g, h, J, a.ms_r_in, a.ms_r_out, a.ms_r_open, a.ms_r_close, a.ms_vgate);
+            if (EXT && a.rrate && s == k - 1) a.rrate[i] = dv;
         }
         a.V[i] = v;
         a.S[i] = g;
@@ -96,16 +100,18 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
         x.fcass = S[16 * 32];
         x.RR = S[17 * 32];
         TP06Params tp = a.tp;
-        if (a.ctype) tp.celltype = a.ctype[i];
+        if (EXT && a.ctype) tp.celltype = a.ctype[i];
         if (tp.gate_rl) {
             for (int s = 0; s < k; ++s) {
                 R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-                tp06_substep<R, true>(x, cp, h, J, tp);
+                const R dv = tp06_substep<R, true>(x, cp, h, J, tp);
+                if (EXT && a.rrate && s == k - 1) a.rrate[i] = dv;
             }
         } else {
             for (int s = 0; s < k; ++s) {
                 R J = smask ? stim_current<R>(smask, a.stims, tn + (double)s * dt_ar) : (R)0;
-                tp06_substep<R, false>(x, cp, h, J, tp);
+                const R dv = tp06_substep<R, false>(x, cp, h, J, tp);
+                if (EXT && a.rrate && s == k - 1) a.rrate[i] = dv;
             }
         }
         a.V[i] = x.V;
@@ -145,18 +151,18 @@ __device__ __forceinline__ int item_node(const int* __restrict__ lists, int n, c
 }
 
 // One item: the optional fused diffusion sub-step, then step A of node i.
-template <typename R, int MODEL, bool KAHAN, int DIM, bool PAD>
+template <typename R, int MODEL, bool KAHAN, int DIM, bool PAD, bool EXT>
 __device__ __forceinline__ void react_item(const ReactArgs<R>& a, const OpView<R>& op, int i, int k, double tn,
                                            bool any_stim) {
     R v0;
     float c0 = 0.f;
     if (DIM >= 0) {
-        diffuse_node<R, (DIM < 0 ? 0 : DIM), KAHAN, PAD>(op, a.vsrc, a.csrc, i, v0, c0);
+        diffuse_node<R, (DIM < 0 ? 0 : DIM), KAHAN, PAD, EXT>(op, a.vsrc, a.csrc, i, v0, c0);
     } else {
         v0 = a.V[i];
         if (KAHAN) c0 = a.C[i];
     }
-    react_node<R, MODEL, KAHAN>(a, i, k, tn, any_stim, v0, c0);
+    react_node<R, MODEL, KAHAN, EXT>(a, i, k, tn, any_stim, v0, c0);
 }
 
 // Items are the entries of the per-k lists taken largest k first (list
@@ -168,7 +174,7 @@ __device__ __forceinline__ void react_item(const ReactArgs<R>& a, const OpView<R
 // trade spills against occupancy.  DIM >= 0 fuses one diffusion sub-step
 // before the reaction (0: SELL-32, 2/3: stencil; PAD: V buffers with a ghost
 // margin, no per-neighbour boundary tests).
-template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD>
+template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD, bool EXT>
 __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpView<R> op) {
     __shared__ int off[DAETI_MAX_K];
     __shared__ double sh_tn;
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     const bool any_stim = sh_stim != 0;
     if (!a.lists) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, a.kk[t], tn, any_stim);
+        if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, a.kk[t], tn, any_stim);
         return;
     }
     const int total = sh_total;
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     if (sh_uni) {
         // every node has the same k (common away from wavefronts): item t is
         // node t, no list indirection
-        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, sh_uni, tn, any_stim);
+        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, sh_uni, tn, any_stim);
     } else if (!sh_listed) {
         // k became mixed after a step with the same k everywhere, so no lists
         // were built: item t is node t with its own k (and the sub-step count
@@ -250,11 +256,11 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
             for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
             if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.substeps, w);
         }
-        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, t, kt, tn, any_stim);
+        if (t < total) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, kt, tn, any_stim);
     } else if (t < total) {
         int k;
         const int i = item_node(a.lists, a.n, off, t, k);
-        react_item<R, MODEL, KAHAN, DIM, PAD>(a, op, i, k, tn, any_stim);
+        react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, i, k, tn, any_stim);
     }
 }
 
@@ -294,12 +300,26 @@ ReactArgs<R> react_args(const DevState& s, const ModelArgs& m, double dt, StepRe
     a.tp.celltype = m.celltype;
     a.tp.gate_rl = m.gate_rl;
     a.ctype = s.ctype;
+    a.rrate = (R*)s.rrate;
     return a;
 }
 
-template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD = false>
+template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD = false, bool EXT = false>
 void launch_react_one(const ReactArgs<R>& a, const OpView<R>& op, int grid, int block, bool pdl, cudaStream_t st) {
-    launch_ex(reaction_kernel<R, MODEL, KAHAN, MINB, DIM, PAD>, grid, block, st, pdl, a, op);
+    launch_ex(reaction_kernel<R, MODEL, KAHAN, MINB, DIM, PAD, EXT>, grid, block, st, pdl, a, op);
+}
+
+// The extended instances (per-node operator rows, per-node cell types or the
+// reaction-rate k rule), with 8 resident blocks per SM whatever the tuning.
+template <typename R, int MODEL, bool KAHAN>
+void launch_react_ext(const ReactArgs<R>& a, const OpView<R>& op, const DiffOp& dop, bool fused, bool pad, int grid,
+                      int block, bool pdl, cudaStream_t st) {
+    if (!fused) launch_react_one<R, MODEL, KAHAN, 8, -1, false, true>(a, op, grid, block, pdl, st);
+    else if (dop.kind == 1) launch_react_one<R, MODEL, KAHAN, 8, 0, false, true>(a, op, grid, block, pdl, st);
+    else if (dop.dim == 2 && pad) launch_react_one<R, MODEL, KAHAN, 8, 2, true, true>(a, op, grid, block, pdl, st);
+    else if (dop.dim == 2) launch_react_one<R, MODEL, KAHAN, 8, 2, false, true>(a, op, grid, block, pdl, st);
+    else if (pad) launch_react_one<R, MODEL, KAHAN, 8, 3, true, true>(a, op, grid, block, pdl, st);
+    else launch_react_one<R, MODEL, KAHAN, 8, 3, false, true>(a, op, grid, block, pdl, st);
 }
 
 // Launch of one (model, precision, register cap) over the four operator cases.
@@ -309,6 +329,10 @@ void launch_react_dims(const ReactArgs<R>& a, const DevState& s, const DiffOp& d
     const OpView<R> op = op_view<R>(dop);
     const bool pdl = tune.pdl != 0;
     const bool pad = s.vpad >= stencil_reach(dop);
+    if (s.ctype || s.rrate || dop.per_node) {
+        launch_react_ext<R, MODEL, KAHAN>(a, op, dop, fused, pad, grid, block, pdl, st);
+        return;
+    }
     if (!fused) launch_react_one<R, MODEL, KAHAN, MINB, -1>(a, op, grid, block, pdl, st);
     else if (dop.kind == 1) launch_react_one<R, MODEL, KAHAN, MINB, 0>(a, op, grid, block, pdl, st);
     else if (dop.dim == 2 && pad) launch_react_one<R, MODEL, KAHAN, MINB, 2, true>(a, op, grid, block, pdl, st);

@@ -43,8 +43,9 @@ def run_gpu(wl, n_steps, every, **opts):
     return np.array(snaps), act, stab, state
 
 
-def run_oracle(wl, n_steps, every, scheme_name="daeti", dt=None, l_round="floor", gate_rl=True):
-    sim = scheme.simulation_from_workload(wl, scheme=scheme_name, dt=dt, l_round=l_round, gate_rl=gate_rl)
+def run_oracle(wl, n_steps, every, scheme_name="daeti", dt=None, l_round="floor", gate_rl=True, k_rule="total"):
+    sim = scheme.simulation_from_workload(wl, scheme=scheme_name, dt=dt, l_round=l_round, gate_rl=gate_rl,
+                                          k_rule=k_rule)
     snaps = []
     n = 0
     while n < n_steps:

@@ -129,6 +129,23 @@ def test_per_node_cell_types_of_one_type_equal_the_model_parameter():
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_k_rule_from_the_reaction_rate(precision):
+    """Reading R-k2 (k from the reaction's dV/dt at the previous step's last
+    sub-step) against the oracle with the same reading; it changes the run."""
+    cases = [(I.ms_square_2d(), 600, 50), (I.tp06_slab_3d(13, 11, 6), 300, 50)]
+    for wl, n_steps, every in cases:
+        g, ga, stab, _ = run_gpu(wl, n_steps, every, precision=precision, k_rule="reaction")
+        o, oa, _ = run_oracle(wl, n_steps, every, k_rule="reaction")
+        tv, ta = TOL[precision]
+        assert float(np.max(np.abs(g - o))) * _mv(wl) <= tv, wl.name
+        da, same, n_act = act_error(ga, oa)
+        assert same and da <= ta and n_act > 0, wl.name
+        if wl.model == "tp06":                   # the two readings give different TP06 runs
+            o_total, _, _ = run_oracle(wl, n_steps, every)
+            assert float(np.max(np.abs(o - o_total))) > 5.0
+
+
 def test_conductivity_update_switches_to_per_node_rows():
     """A grid prepared with one D per layer gets per-node stencil rows when an
     update makes D vary within a layer; the run then equals one prepared with

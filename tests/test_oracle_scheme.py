@@ -158,6 +158,29 @@ def test_activation_interpolation():
     assert abs(sim.act[0] - 0.15) < 1e-15      # first crossing only
 
 
+def test_k_rules_on_a_linear_cell():
+    """dv/dt = J (the cubic model with a_r = 0) on one node without diffusion:
+    while the stimulus is on, both readings of 'dV/dt at the previous
+    iteration' give 100 J = 3 mV/ms, k = 5 + 3 = 8 (k = 1 at the first step,
+    rate 0).  The window ends after 4 of the 8 sub-steps of the step at
+    0.5 ms: over that step the split solution rose 4 (0.0125)(0.03), a rate of
+    1.5 mV/ms (k = 5 + 1 = 6), while the reaction's rate at the step's last
+    sub-step is 0 (k = 1)."""
+    ks = {}
+    for rule in ("total", "reaction"):
+        st = I.Stimulus(np.array([0]), 0.0, 0.55, 0.03)
+        sim = scheme.Simulation(np.zeros((1, 1)) + 1e-300, np.ones(1), cells.CubicBistable(a_r=0.0), [st],
+                                dt=0.1, dt0=0.01, k_rule=rule)
+        seq = []
+        for _ in range(7):
+            seq.append(int(sim.k[0]))
+            sim.step()
+        ks[rule] = seq
+        assert abs(sim.S[0, 0] - 0.55 * 0.03) < 1e-15
+    assert ks["total"] == [1, 8, 8, 8, 8, 8, 6]
+    assert ks["reaction"] == [1, 8, 8, 8, 8, 8, 1]
+
+
 def test_ost_is_fixed_step():
     wl = I.ms_square_2d(n=9)
     a = scheme.simulation_from_workload(wl, scheme="ost", dt=0.01)
