@@ -135,6 +135,13 @@ int daeti_set_mesh_tet(daeti_ctx* ctx, int64_t n_nodes, const double* xyz,
 int daeti_set_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
                            const double* d_trans, const double* fibre);
 
+/* The same from per-node values: each element takes the mean of its nodes'
+ * d_long and d_trans (n_nodes doubles each; d_trans may be NULL for
+ * d_long); fibre as above, per element.  Errors as daeti_set_conductivity
+ * (EINVAL if n_nodes differs from the mesh's node count). */
+int daeti_set_conductivity_nodal(daeti_ctx* ctx, int64_t n_nodes, const double* d_long,
+                                 const double* d_trans, const double* fibre);
+
 /* Cell model for every node (DAETI_MODEL_*) with n_params parameters
  * (params may be NULL for the published defaults). */
 int daeti_set_cell_model(daeti_ctx* ctx, int model, const double* params, int n_params);
@@ -171,6 +178,9 @@ int daeti_prepare(daeti_ctx* ctx);
  * is kept.  Used for parameter studies and gradient checks. */
 int daeti_update_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_long,
                               const double* d_trans, const double* fibre);
+/* The same from per-node values (element = mean of its nodes). */
+int daeti_update_conductivity_nodal(daeti_ctx* ctx, int64_t n_nodes, const double* d_long,
+                                    const double* d_trans, const double* fibre);
 
 /* Stability data computed by prepare (any pointer may be NULL). */
 int daeti_get_stability(daeti_ctx* ctx, double* dt_s, double* lambda_max, int* l,
@@ -261,11 +271,15 @@ int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);
  * flags: DAETI_ADJ_RECORD (forward and loss only, recording the schedule),
  * DAETI_ADJ_REPLAY (forward and loss only, with the recorded schedule; same
  * sensors/samples/slots as the recording), DAETI_ADJ_NO_GRADIENT (forward and
- * loss only).  Errors: EUNSUPPORTED (other models/meshes, anisotropy),
- * ESTATE (replay without a recording). */
+ * loss only), DAETI_ADJ_NODAL_GRADIENT (grad_d holds n_nodes values,
+ * dL/dD_i for per-node D whose element values are the means of their nodes:
+ * the sum over the elements of node i of dL/dD_e / nodes per element).
+ * Errors: EUNSUPPORTED (other models/meshes, anisotropy), ESTATE (replay
+ * without a recording). */
 #define DAETI_ADJ_RECORD 1
 #define DAETI_ADJ_REPLAY 2
 #define DAETI_ADJ_NO_GRADIENT 4
+#define DAETI_ADJ_NODAL_GRADIENT 8
 int daeti_adjoint(daeti_ctx* ctx, const int64_t* sensors, int n_sensors, int sample_every,
                   const double* data, int64_t n_steps, int n_slots, int flags, double* loss,
                   double* grad_d, double* grad_tau_close);

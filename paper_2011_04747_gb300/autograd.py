@@ -5,8 +5,8 @@ misfit L = sum_j sum_s (v_s(t_j) - d_js)^2 of a Mitchell-Schaeffer tissue on
 a structured grid whose element conductivity is the mean of its nodal values,
 and back-propagates dL/d(d_node) and dL/d(tau_close).  The library computes the
 loss and both gradients in one call (forward with binomial checkpoints, then
-the reverse sweep); this wrapper only moves arrays and applies the chain rule
-of the element mean.
+the reverse sweep); its nodal entry points form the element means and apply
+their chain rule to the gradient, so this wrapper only moves arrays.
 """
 from __future__ import annotations
 
@@ -44,24 +44,20 @@ class MisfitProblem:
 
 
 def _solve(problem: MisfitProblem, d_node: np.ndarray, tau_close: float):
-    conn = problem.elements()
-    d_elem = d_node[conn].mean(axis=1)
     params = list(problem.ms_params)
     params[3] = float(tau_close)
     s = binding.Solver(precision=problem.precision, dt=problem.dt, graph_steps=0)
     try:
         s.daeti_set_mesh_grid(problem.dim, problem.n, problem.h)
-        s.daeti_set_conductivity(d_elem, d_elem, None)
+        s.daeti_set_conductivity_nodal(d_node)       # element D = mean of its nodes
         s.daeti_set_cell_model("ms", tuple(params))
         for st in problem.stimuli:
             s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
         s.daeti_prepare()
-        loss, g_elem, g_tau = s.daeti_adjoint(problem.sensors, problem.data, problem.n_steps,
-                                              problem.sample_every, problem.n_slots, 0, n_elem=conn.shape[0])
+        loss, g_node, g_tau = s.daeti_adjoint(problem.sensors, problem.data, problem.n_steps,
+                                              problem.sample_every, problem.n_slots, 0, nodal=True)
     finally:
         s.close()
-    g_node = np.zeros(d_node.shape[0])
-    np.add.at(g_node, conn, (g_elem / conn.shape[1])[:, None])
     return loss, g_node, g_tau
 
 

@@ -24,7 +24,8 @@ L_FLOOR, L_CEIL = 0, 1
 MODEL_MS, MODEL_TP06 = 1, 2
 DTYPE_F64, DTYPE_F32 = 0, 1
 KERNEL_REACTION, KERNEL_DIFFUSION, KERNEL_OTHER = 0, 1, 2
-ADJ_RECORD, ADJ_REPLAY, ADJ_NO_GRADIENT = 1, 2, 4
+ADJ_RECORD, ADJ_REPLAY, ADJ_NO_GRADIENT, NODAL_GRADIENT = 1, 2, 4, 8
+K_TOTAL, K_REACTION = 0, 1
 
 _PREC = {"fp64": FP64, "fp32_kahan": FP32_KAHAN, "fp32": FP32}
 _SCHEME = {"daeti": SCHEME_DAETI, "ostar": SCHEME_OSTAR, "ost": SCHEME_OST}
@@ -88,6 +89,7 @@ _SIGNATURES = {
     "daeti_set_mesh_grid": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_double]),
     "daeti_set_mesh_tet": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, ctypes.c_int64, _I64P]),
     "daeti_set_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
+    "daeti_set_conductivity_nodal": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
     "daeti_set_cell_model": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
     "daeti_set_cell_types": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint8)]),
     "daeti_add_stimulus": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
@@ -113,6 +115,7 @@ _SIGNATURES = {
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
     "daeti_update_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
+    "daeti_update_conductivity_nodal": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
     "daeti_adjoint": (ctypes.c_int, [_VP, _I64P, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_int, _DP, _DP, _DP]),
     "daeti_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(daeti_options)]),
@@ -336,6 +339,22 @@ class Solver:
         b = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(self.lib.daeti_load_state(self.ctx, b.ctypes.data_as(_VP), b.shape[0]))
 
+    def daeti_set_conductivity_nodal(self, d_long, d_trans=None, fibre=None):
+        """Per-node d_long, d_trans (element value = mean of its nodes); fibre per element."""
+        dl = _f64(d_long)
+        dtr = _f64(d_trans) if d_trans is not None else None
+        fb = _f64(fibre) if fibre is not None else None
+        self._check(self.lib.daeti_set_conductivity_nodal(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
+                                                          _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
+
+    def daeti_update_conductivity_nodal(self, d_long, d_trans=None, fibre=None):
+        dl = _f64(d_long)
+        dtr = _f64(d_trans) if d_trans is not None else None
+        fb = _f64(fibre) if fibre is not None else None
+        self._check(self.lib.daeti_update_conductivity_nodal(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
+                                                             _ptr(dtr, ctypes.c_double),
+                                                             _ptr(fb, ctypes.c_double)))
+
     def daeti_update_conductivity(self, d_long, d_trans=None, fibre=None):
         dl = _f64(d_long)
         dtr = _f64(d_trans) if d_trans is not None else None
@@ -343,17 +362,20 @@ class Solver:
         self._check(self.lib.daeti_update_conductivity(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
                                                        _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
 
-    def daeti_adjoint(self, sensors, data, n_steps, sample_every, n_slots=32, flags=0, n_elem=None):
-        """Returns (loss, dL/dD_e (n_elem,) or None, dL/dtau_close or None)."""
+    def daeti_adjoint(self, sensors, data, n_steps, sample_every, n_slots=32, flags=0, n_elem=None, nodal=False):
+        """Returns (loss, dL/dD_e (n_elem,) or None, dL/dtau_close or None); with nodal,
+        the gradient is per node (n_nodes,) for element D = mean of nodal D."""
         sn = _i64(sensors)
         dd = _f64(data).reshape(-1)
         loss = ctypes.c_double()
         gt = ctypes.c_double()
-        grad = None if flags else np.empty(int(n_elem), dtype=np.float64)
+        grad = None if flags else np.empty(int(self.n_nodes if nodal else n_elem), dtype=np.float64)
+        if nodal:
+            flags |= NODAL_GRADIENT
         self._check(self.lib.daeti_adjoint(self.ctx, _ptr(sn, ctypes.c_int64), sn.shape[0], int(sample_every),
                                            _ptr(dd, ctypes.c_double), int(n_steps), int(n_slots), int(flags),
                                            ctypes.byref(loss), _ptr(grad, ctypes.c_double), ctypes.byref(gt)))
-        return loss.value, grad, (None if flags else gt.value)
+        return loss.value, grad, (None if grad is None else gt.value)
 
     def daeti_get_substeps(self):
         n = ctypes.c_int64()

@@ -898,7 +898,19 @@ extern "C" int daeti_adjoint(daeti_ctx* c, const int64_t* sensors, int n_sensors
     if (loss) *loss = acc[0];
     if (!no_grad) {
         if (grad_tau_close) *grad_tau_close = acc[1];
-        if (grad_d) CK(cpy_(c, grad_d, b->g_elem, 8 * (size_t)c->n_elem, cudaMemcpyDeviceToHost));
+        if (grad_d && (flags & DAETI_ADJ_NODAL_GRADIENT)) {
+            // chain rule of D_e = mean of its nodes' D
+            std::vector<double> ge(c->n_elem);
+            CK(cpy_(c, ge.data(), b->g_elem, 8 * (size_t)c->n_elem, cudaMemcpyDeviceToHost));
+            std::fill(grad_d, grad_d + c->n_nodes, 0.0);
+            int64_t nd[8];
+            for (int64_t e = 0; e < c->n_elem; ++e) {
+                const int nl = elem_nodes(c, e, nd);
+                for (int a = 0; a < nl; ++a) grad_d[nd[a]] += ge[e] / nl;
+            }
+        } else if (grad_d) {
+            CK(cpy_(c, grad_d, b->g_elem, 8 * (size_t)c->n_elem, cudaMemcpyDeviceToHost));
+        }
     }
     c->adj_fwd_steps = A.fwd_steps;
     return DAETI_OK;

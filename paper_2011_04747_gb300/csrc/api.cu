@@ -64,6 +64,32 @@ int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count) {
 const double TP06_INIT[19] = {-85.23, 0.000126, 3.64, 0.00036, 8.604, 136.89, 0.00172, 0.7444, 0.7045, 0.00621,
                               0.4712, 0.0095, 2.42e-8, 0.999998, 3.373e-5, 0.7888, 0.9755, 0.9953, 0.9073};
 
+// Nodes of element e (structured grids: x fastest, 2^dim nodes; tets: 4).
+int elem_nodes(const daeti_ctx* c, int64_t e, int64_t* out) {
+    if (c->mesh_kind == 2) {
+        for (int a = 0; a < 4; ++a) out[a] = c->tets[e * 4 + a];
+        return 4;
+    }
+    const int64_t nx = c->n[0], ny = c->n[1];
+    const int64_t ex = e % (nx - 1), t = e / (nx - 1), ey = t % (ny - 1), ez = t / (ny - 1);
+    const int nl = 1 << c->dim;
+    for (int a = 0; a < nl; ++a)
+        out[a] = (ex + (a & 1)) + nx * ((ey + ((a >> 1) & 1)) + ny * (ez + ((a >> 2) & 1)));
+    return nl;
+}
+
+// Element values as the means of their nodes' values.
+void elem_means(const daeti_ctx* c, const double* nodal, std::vector<double>& out) {
+    out.assign(c->n_elem, 0.0);
+    int64_t nd[8];
+    for (int64_t e = 0; e < c->n_elem; ++e) {
+        const int nl = elem_nodes(c, e, nd);
+        double s = 0.0;
+        for (int a = 0; a < nl; ++a) s += nodal[nd[a]];
+        out[e] = s / nl;
+    }
+}
+
 }  // namespace daeti_host
 
 namespace {
@@ -331,6 +357,28 @@ int daeti_set_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long, c
     else c->fib.clear();
     c->have_cond = true;
     return DAETI_OK;
+}
+
+int daeti_set_conductivity_nodal(daeti_ctx* c, int64_t n_nodes, const double* d_long, const double* d_trans,
+                                 const double* fibre) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "set the mesh first");
+    if (n_nodes != c->n_nodes || !d_long) return fail(c, DAETI_EINVAL, "n_nodes does not match the mesh");
+    std::vector<double> el, et;
+    elem_means(c, d_long, el);
+    elem_means(c, d_trans ? d_trans : d_long, et);
+    return daeti_set_conductivity(c, c->n_elem, el.data(), et.data(), fibre);
+}
+
+int daeti_update_conductivity_nodal(daeti_ctx* c, int64_t n_nodes, const double* d_long, const double* d_trans,
+                                    const double* fibre) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->mesh_kind) return fail(c, DAETI_ESTATE, "set the mesh first");
+    if (n_nodes != c->n_nodes || !d_long) return fail(c, DAETI_EINVAL, "n_nodes does not match the mesh");
+    std::vector<double> el, et;
+    elem_means(c, d_long, el);
+    elem_means(c, d_trans ? d_trans : d_long, et);
+    return daeti_update_conductivity(c, c->n_elem, el.data(), et.data(), fibre);
 }
 
 int daeti_set_cell_model(daeti_ctx* c, int model, const double* params, int n_params) {

@@ -142,6 +142,35 @@ def test_full_adjoint_config_against_central_differences():
     assert worst32 <= 1e-3, worst32
 
 
+def test_nodal_conductivity_and_nodal_gradient():
+    """Per-node D (daeti_set_conductivity_nodal: element D = mean of its nodes)
+    runs like the element means given directly, and the per-node gradient is
+    the chain rule of the element gradient (the oracle's nodal_gradient)."""
+    from oracle import adjoint, fem
+
+    wl, prob, d_elem, sensors, data, n_steps = _small(n=10, n_steps=150)
+    rng = np.random.default_rng(3)
+    d_node = 0.001 * np.exp(0.3 * rng.standard_normal(wl.n_nodes))
+    conn = fem.grid_elements(2, wl.n)
+    de = adjoint.element_d_from_nodes(conn, d_node)
+    binding = ensure_lib()
+    a = _gpu(wl, de, "fp64")
+    b = binding.Solver(precision="fp64", dt=wl.dt, dt0=wl.dt0, v_threshold=wl.v_threshold)
+    b.daeti_set_mesh_grid(wl.dim, wl.n, wl.h)
+    b.daeti_set_conductivity_nodal(d_node)
+    b.daeti_set_cell_model(wl.model, tuple(wl.model_params))
+    for st in wl.stimuli:
+        b.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
+    b.daeti_prepare()
+    la, ga, ta = a.daeti_adjoint(sensors, data, n_steps, 10, n_slots=6, n_elem=len(de))
+    lb, gb, tb = b.daeti_adjoint(sensors, data, n_steps, 10, n_slots=6, nodal=True)
+    assert gb.shape == (wl.n_nodes,)
+    assert abs(la - lb) <= 1e-12 * la and abs(ta - tb) <= 1e-12 * abs(ta)
+    assert _rel(gb, adjoint.nodal_gradient(conn, ga, wl.n_nodes)) <= 1e-12
+    a.close()
+    b.close()
+
+
 def test_autograd_wrapper():
     import torch
 
