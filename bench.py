@@ -236,7 +236,10 @@ def bench_slab(args, env):
     s32 = make("fp32_kahan")
     tune = None
     if not args.no_autotune:
-        rep = autotune.autotune(s32, sim_ms=20.0, extra_key="|slab")
+        # 100 ms: the stimulus, the upstroke and the start of the plateau (a
+        # 20 ms window, stimulus and upstroke only, favoured shapes that lose
+        # over the whole run)
+        rep = autotune.autotune(s32, sim_ms=100.0, extra_key="|slab|100ms")
         tune = {k: rep[k] for k in ("cached", "candidates", "rejected") if k in rep}
         s32.daeti_set_stream(env.stream)
     stab = s32.daeti_get_stability()
