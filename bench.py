@@ -240,7 +240,7 @@ def bench_slab(args, env):
         # 20 ms window, stimulus and upstroke only, favoured shapes that lose
         # over the whole run)
         rep = autotune.autotune(s32, sim_ms=100.0, extra_key="|slab|100ms")
-        tune = {k: rep[k] for k in ("cached", "candidates", "rejected") if k in rep}
+        tune = {k: rep[k] for k in ("cached", "candidates", "rejected", "search_s", "ms_per_sim_ms") if k in rep}
         s32.daeti_set_stream(env.stream)
     stab = s32.daeti_get_stability()
     ck = s32.daeti_save_state()
