@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -244,8 +245,10 @@ def bench_slab(args, env):
         s32.daeti_set_stream(env.stream)
     stab = s32.daeti_get_stability()
     ck = s32.daeti_save_state()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{env.rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    # raw nvidia-smi samples: a temporary file unless DAETI_CLOCKS_DIR names a folder to keep them in
+    clk_dir = os.environ.get("DAETI_CLOCKS_DIR") or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, f"daeti_clocks_rank{env.rank}.csv")
+    os.makedirs(clk_dir, exist_ok=True)
     sampler, fh = _clock_sampler(clk_path)
     sec32 = env.timed(lambda: s32.daeti_advance(T_END), args.steps, args.warmup,
                       reset=lambda: s32.daeti_load_state(ck))

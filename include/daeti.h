@@ -51,7 +51,7 @@ extern "C" {
 #define DAETI_EUNSTABLE 5     /* dt_ad * lambda_max >= 2 (explicit diffusion would diverge) */
 #define DAETI_ENONFINITE 6    /* V became NaN/Inf during advance */
 #define DAETI_ETIMEOUT 7      /* a bounded device wait gave up */
-#define DAETI_EUNSUPPORTED 8  /* valid request this build does not implement */
+#define DAETI_EUNSUPPORTED 8  /* valid request the library does not implement */
 
 /* arithmetic of the time stepping */
 #define DAETI_FP64 0          /* every state, operator and update in double */
