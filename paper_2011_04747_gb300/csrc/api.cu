@@ -653,21 +653,28 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
         c->op.nx = (int)nx;
         c->op.ny = (int)ny;
         c->op.nz = c->dim == 3 ? (int)c->n[2] : 1;
-        std::vector<double> A((size_t)N * DAETI_ROW, 0.0);
-        for (int64_t i = 0; i < N; ++i) {
-            const double s = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
-            const int64_t xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
-            for (int64_t q = K.rowptr[i]; q < K.rowptr[i + 1]; ++q) {
-                const int64_t j = K.col[q];
-                if (j == i) continue;
-                const int64_t dx = j % nx - xi, dy = (j / nx) % ny - yi, dz = j / (nx * ny) - zi;
-                if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
-                    return fail(c, DAETI_EINVAL, "grid operator reaches beyond the 27-point stencil");
-                A[(size_t)i * DAETI_ROW + (size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))] = K.val[q] * s;
+        if ((fresh || grow) && (rc = dalloc(c, &c->op.coef, R * (size_t)N * DAETI_ROW))) return rc;
+        // built and uploaded in blocks of rows (bounded host memory on large grids)
+        const int64_t B = 65536;
+        std::vector<double> A;
+        for (int64_t i0 = 0; i0 < N; i0 += B) {
+            const int64_t nb = std::min(B, N - i0);
+            A.assign((size_t)nb * DAETI_ROW, 0.0);
+            for (int64_t i = i0; i < i0 + nb; ++i) {
+                const double s = K.m[i] > 0 ? c->dt_ad / K.m[i] : 0.0;
+                const int64_t xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+                for (int64_t q = K.rowptr[i]; q < K.rowptr[i + 1]; ++q) {
+                    const int64_t j = K.col[q];
+                    if (j == i) continue;
+                    const int64_t dx = j % nx - xi, dy = (j / nx) % ny - yi, dz = j / (nx * ny) - zi;
+                    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
+                        return fail(c, DAETI_EINVAL, "grid operator reaches beyond the 27-point stencil");
+                    A[(size_t)(i - i0) * DAETI_ROW + (size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))] = K.val[q] * s;
+                }
             }
+            if ((rc = upload_real(c, (char*)c->op.coef + R * (size_t)i0 * DAETI_ROW, A.data(), (int64_t)A.size())))
+                return rc;
         }
-        if ((fresh || grow) && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
-        if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
     } else {
         if (!fresh && c->op.kind != 1) return fail(c, DAETI_EINVAL, "operator layout changed");
         std::vector<double> scale(N);
