@@ -181,7 +181,6 @@ static void assemble_csr_generic(int64_t n_nodes, int64_t n_elem, int nl, const 
     out.n = n_nodes;
     out.rowptr.assign(n_nodes + 1, 0);
     std::vector<int> buf;
-    std::vector<std::vector<int>> rows(0);
     out.col.clear();
     out.col.reserve((size_t)n_nodes * 16);
     for (int64_t i = 0; i < n_nodes; ++i) {
