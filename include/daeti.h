@@ -274,8 +274,8 @@ int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);
  * loss only), DAETI_ADJ_NODAL_GRADIENT (grad_d holds n_nodes values,
  * dL/dD_i for per-node D whose element values are the means of their nodes:
  * the sum over the elements of node i of dL/dD_e / nodes per element).
- * Errors: EUNSUPPORTED (other models/meshes, anisotropy), ESTATE (replay
- * without a recording). */
+ * Errors: EUNSUPPORTED (other models/meshes, anisotropy, the k rule
+ * DAETI_K_REACTION), ESTATE (replay without a recording). */
 #define DAETI_ADJ_RECORD 1
 #define DAETI_ADJ_REPLAY 2
 #define DAETI_ADJ_NO_GRADIENT 4
