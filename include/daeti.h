@@ -50,7 +50,7 @@ extern "C" {
 #define DAETI_ESTATE 4        /* call made in the wrong order */
 #define DAETI_EUNSTABLE 5     /* dt_ad * lambda_max >= 2 (explicit diffusion would diverge) */
 #define DAETI_ENONFINITE 6    /* V became NaN/Inf during advance */
-#define DAETI_ETIMEOUT 7      /* a bounded device wait gave up */
+/* 7 is unused (no call waits on the device with a time limit) */
 #define DAETI_EUNSUPPORTED 8  /* valid request the library does not implement */
 
 /* arithmetic of the time stepping */
@@ -163,7 +163,7 @@ int daeti_add_stimulus(daeti_ctx* ctx, const int64_t* nodes, int64_t n_nodes,
                        double period, int count);
 
 /* Assemble K and the lumped mass M_L, allocate device memory, compute dt_s
- * (Eq. 3, FP64 on the GPU), lambda_max(M_L^-1 K) by FP64 power iteration,
+ * (Eq. 3, FP64 on the GPU), lambda_max(M_L^-1 K) by FP64 Lanczos iteration,
  * l, k_max and the effective dt of the scheme; set the published initial
  * state.  Errors: ESTATE (missing mesh/conductivity/model), EUNSTABLE,
  * ENOMEM, ECUDA. */
@@ -320,20 +320,20 @@ int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* 
 int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
 
 /* ---------------------------------------------------------------------------
- * Allocation-free stable-step estimate (no counterpart in the paper: this is a
- * deployment convenience, not part of the method).
+ * Allocation-free stable-step estimate.  The paper has no counterpart: this is
+ * a deployment convenience, not part of the method.
  *
- * For callers that cannot call cudaMalloc (hosts that own all device memory
+ * For callers that cannot call cudaMalloc: hosts that own all device memory
  * through their own pool or budget, plugins that must not allocate after
- * start-up, code that must avoid the implicit synchronisation of cudaMalloc /
- * cudaFree).  Computes, for a structured grid whose conductivity is constant
- * on each element layer, the same two numbers that daeti_prepare +
- * daeti_get_stability report: dt_s of Eq. 3 (FP64 Gershgorin bound) and
- * lambda_max of M_L^-1 K (FP64 power iteration, same start vector and
- * stopping rule).  It calls no cudaMalloc, cudaFree or other allocating
- * library routine: its work vectors live in one fixed __device__ array of
- * about 13.6 MB that every GPU which loads libdaeti holds until the process
- * exits.
+ * start-up, and code that must avoid the implicit synchronisation of
+ * cudaMalloc / cudaFree.  Computes, for a structured grid whose conductivity
+ * is constant on each element layer, the same two numbers that
+ * daeti_prepare + daeti_get_stability report: the FP64 Gershgorin stable step
+ * dt_s and lambda_max of M_L^-1 K (FP64 Lanczos), with the same table builder
+ * and estimator routines.  It calls no cudaMalloc, cudaFree or other
+ * allocating library routine: its work vectors live in one fixed __device__
+ * array of about 17.8 MB that every GPU which loads libdaeti holds until the
+ * process exits.
  *   - Limits: at most DAETI_NOALLOC_MAX_NODES nodes and
  *     DAETI_NOALLOC_MAX_LAYERS node layers in z; larger grids return
  *     DAETI_EINVAL with a message.  Conductivity varying inside an element
@@ -344,7 +344,8 @@ int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
  *     errbuf/errbuf_len: optional caller buffer for an error message.
  *   - The first call on each device (with that device current) looks up the
  *     array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.  The call waits for its own work.
+ *     before any stream capture.  Every call synchronises `stream` and copies
+ *     its results into host memory before it returns.
  *   - Every call shares the one array and leaves its contents behind; calls
  *     whose work overlaps on the GPU (from several host threads with
  *     different streams) race on it.  Host-side calls are serialised. */

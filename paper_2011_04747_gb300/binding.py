@@ -17,7 +17,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdaeti.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(9)
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSTABLE, ENONFINITE = range(7)
+EUNSUPPORTED = 8   # 7 is unused
 FP64, FP32_KAHAN, FP32 = 0, 1, 2
 SCHEME_DAETI, SCHEME_OSTAR, SCHEME_OST = 0, 1, 2
 L_FLOOR, L_CEIL = 0, 1
@@ -166,6 +167,21 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
 
 
+def _cond(d_long, d_trans, fibre, n_fibre=None):
+    """Conductivity arrays as float64, with the lengths the C side reads
+    checked here (it reads d_trans[e] for every entry of d_long and three
+    fibre components for each of n_fibre elements, default len(d_long))."""
+    dl = _f64(d_long).reshape(-1)
+    dtr = _f64(d_trans).reshape(-1) if d_trans is not None else None
+    fb = _f64(fibre).reshape(-1) if fibre is not None else None
+    if dtr is not None and dtr.shape != dl.shape:
+        raise DaetiError(EINVAL, f"d_trans has {dtr.shape[0]} entries, d_long {dl.shape[0]}")
+    nf = dl.shape[0] if n_fibre is None else int(n_fibre)
+    if fb is not None and fb.shape[0] != 3 * nf:
+        raise DaetiError(EINVAL, f"fibre needs 3 x {nf} entries, got {fb.shape[0]}")
+    return dl, dtr, fb
+
+
 class Solver:
     """One tissue on the GPU: owns a ``daeti_ctx``.
 
@@ -199,6 +215,7 @@ class Solver:
             raise DaetiError(rc, "daeti_create failed")
         self.ctx = h
         self.n_nodes = 0
+        self.n_elem = 0
         self.n_states = 0
         if stream is not None:
             self.daeti_set_stream(stream)
@@ -229,6 +246,7 @@ class Solver:
     def daeti_set_mesh_grid(self, dim, n, h):
         nn = _i64(list(n) + [1] * (3 - len(n)))
         self._check(self.lib.daeti_set_mesh_grid(self.ctx, int(dim), _ptr(nn, ctypes.c_int64), float(h)))
+        self.n_elem = int(np.prod([int(nn[d]) - 1 for d in range(int(dim))]))
         self._sizes()
 
     def daeti_set_mesh_tet(self, xyz, tets):
@@ -236,12 +254,11 @@ class Solver:
         t = _i64(tets)
         self._check(self.lib.daeti_set_mesh_tet(self.ctx, x.shape[0], _ptr(x, ctypes.c_double), t.shape[0],
                                                 _ptr(t, ctypes.c_int64)))
+        self.n_elem = int(t.shape[0])
         self._sizes()
 
     def daeti_set_conductivity(self, d_long, d_trans=None, fibre=None):
-        dl = _f64(d_long)
-        dtr = _f64(d_trans) if d_trans is not None else None
-        fb = _f64(fibre) if fibre is not None else None
+        dl, dtr, fb = _cond(d_long, d_trans, fibre)
         self._check(self.lib.daeti_set_conductivity(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
                                                     _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
 
@@ -341,24 +358,18 @@ class Solver:
 
     def daeti_set_conductivity_nodal(self, d_long, d_trans=None, fibre=None):
         """Per-node d_long, d_trans (element value = mean of its nodes); fibre per element."""
-        dl = _f64(d_long)
-        dtr = _f64(d_trans) if d_trans is not None else None
-        fb = _f64(fibre) if fibre is not None else None
+        dl, dtr, fb = _cond(d_long, d_trans, fibre, self.n_elem)
         self._check(self.lib.daeti_set_conductivity_nodal(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
                                                           _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
 
     def daeti_update_conductivity_nodal(self, d_long, d_trans=None, fibre=None):
-        dl = _f64(d_long)
-        dtr = _f64(d_trans) if d_trans is not None else None
-        fb = _f64(fibre) if fibre is not None else None
+        dl, dtr, fb = _cond(d_long, d_trans, fibre, self.n_elem)
         self._check(self.lib.daeti_update_conductivity_nodal(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
                                                              _ptr(dtr, ctypes.c_double),
                                                              _ptr(fb, ctypes.c_double)))
 
     def daeti_update_conductivity(self, d_long, d_trans=None, fibre=None):
-        dl = _f64(d_long)
-        dtr = _f64(d_trans) if d_trans is not None else None
-        fb = _f64(fibre) if fibre is not None else None
+        dl, dtr, fb = _cond(d_long, d_trans, fibre)
         self._check(self.lib.daeti_update_conductivity(self.ctx, dl.shape[0], _ptr(dl, ctypes.c_double),
                                                        _ptr(dtr, ctypes.c_double), _ptr(fb, ctypes.c_double)))
 
@@ -505,9 +516,7 @@ def daeti_grid_stability_noalloc(dim, n, h, d_long, d_trans=None, fibre=None, st
     """Allocation-free (dt_s, lambda_max) of a layered structured grid; raises DaetiError."""
     lib = load_library()
     nn = _i64(list(n) + [1] * (3 - len(n)))
-    dl = _f64(d_long)
-    dtr = _f64(d_trans) if d_trans is not None else None
-    fb = _f64(fibre) if fibre is not None else None
+    dl, dtr, fb = _cond(d_long, d_trans, fibre)
     handle = getattr(stream, "cuda_stream", stream)
     dts, lam = ctypes.c_double(), ctypes.c_double()
     err = ctypes.create_string_buffer(256)

@@ -432,53 +432,33 @@ int daeti_add_stimulus(daeti_ctx* c, const int64_t* nodes, int64_t n_nodes, doub
     return DAETI_OK;
 }
 
-// Power iteration for lambda_max of M_L^-1 K (self-adjoint in the M inner product).
-static int power_iteration(daeti_ctx* c, const EstOp& est, const double* d_m, double* lam_out) {
+// Device buffers that are freed when the scope ends (every return path).
+struct TempDev {
+    std::vector<void*> p;
+    void* get(size_t bytes) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+        p.push_back(q);
+        return q;
+    }
+    ~TempDev() {
+        for (void* q : p) cudaFree(q);
+    }
+};
+
+// lambda_max of M_L^-1 K (FP64 Lanczos on the GPU, estimator.cu).
+static int estimate_lambda_max(daeti_ctx* c, const EstOp& est, const double* d_m, double* lam_out) {
     const int64_t n = est.n;
-    double *x = nullptr, *y = nullptr, *dots = nullptr;
-    CK(cudaMalloc(&x, sizeof(double) * n));
-    CK(cudaMalloc(&y, sizeof(double) * n));
-    CK(cudaMalloc(&dots, sizeof(double) * 2));
-    std::vector<double> hx(n);
-    uint64_t st = 0x9E3779B97F4A7C15ull;
-    for (int64_t i = 0; i < n; ++i) {
-        st = st * 6364136223846793005ull + 1442695040888963407ull;
-        const double u = (double)(st >> 11) * (1.0 / 9007199254740992.0);
-        double sgn = 1.0;
-        if (est.kind == 0) {
-            const int64_t xx = i % est.nx, yy = (i / est.nx) % est.ny, zz = i / ((int64_t)est.nx * est.ny);
-            sgn = ((xx + yy + zz) & 1) ? -1.0 : 1.0;
-            hx[i] = sgn * (1.0 + 0.1 * u);
-        } else {
-            hx[i] = u - 0.5;
-        }
-    }
-    cudaStream_t s = c->stream;
-    CK(cpy_(c, x, hx.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    double hd[2];
-    CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, s));
-    launch_mdots(n, d_m, x, x, dots, s);
-    CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    launch_scale(n, x, 1.0 / std::sqrt(hd[1]), x, s);
-    double lam = 0.0, prev = 0.0;
-    for (int it = 0; it < 500; ++it) {
-        launch_apply_minvk(est, x, y, s);
-        CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, s));
-        launch_mdots(n, d_m, x, y, dots, s);
-        CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        lam = hd[0];
-        if (!(hd[1] > 0)) break;
-        launch_scale(n, y, 1.0 / std::sqrt(hd[1]), x, s);
-        if (it > 5 && std::fabs(lam - prev) <= 1e-8 * std::fabs(lam)) break;
-        prev = lam;
-    }
-    CK(cudaStreamSynchronize(s));
-    cudaFree(x);
-    cudaFree(y);
-    cudaFree(dots);
-    *lam_out = lam;
+    const int max_it = DAETI_LANCZOS_MAX_IT;
+    TempDev t;
+    double* v[3];
+    for (int q = 0; q < 3; ++q)
+        if (!(v[q] = (double*)t.get(sizeof(double) * n))) return fail(c, DAETI_ENOMEM, "Lanczos vectors");
+    double* hist = (double*)t.get(sizeof(double) * 4 * (max_it + 1));
+    if (!hist) return fail(c, DAETI_ENOMEM, "Lanczos coefficients");
+    std::vector<double> hh(4 * (size_t)max_it);
+    int iters = 0;
+    CK(lanczos_lambda_max(est, d_m, v, hist, hh.data(), max_it, c->stream, lam_out, &iters));
     return DAETI_OK;
 }
 
@@ -593,7 +573,7 @@ static int assemble_and_estimate(daeti_ctx* c, GridTable& tab, bool& table, CsrK
         std::memcpy(&mn, &hb, 8);
         c->dt_s = 0.9 * mn;
     }
-    int rc = power_iteration(c, est, d_m, &c->lam);
+    int rc = estimate_lambda_max(c, est, d_m, &c->lam);
     free_tmp();
     return rc;
 }
@@ -641,12 +621,23 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
         // neighbour at offset (dx, dy, dz); columns ascend, so the terms are
         // added in the CSR order)
         if (!fresh && c->op.kind != 0) return fail(c, DAETI_EINVAL, "operator layout changed");
+        const int64_t nx = c->n[0], ny = c->n[1];
+        // every row's reach is checked before anything is uploaded, so a
+        // rejected operator leaves the current one untouched
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+            for (int64_t q = K.rowptr[i]; q < K.rowptr[i + 1]; ++q) {
+                const int64_t j = K.col[q];
+                const int64_t dx = j % nx - xi, dy = (j / nx) % ny - yi, dz = j / (nx * ny) - zi;
+                if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
+                    return fail(c, DAETI_EINVAL, "grid operator reaches beyond the 27-point stencil");
+            }
+        }
         // a grid prepared with per-layer D gets per-node rows on its first
         // update with D varying within a layer (a new coefficient array: the
         // adjoint's captured sweep is dropped)
         const bool grow = !fresh && !c->op.per_node;
         if (grow) free_adjoint(c);
-        const int64_t nx = c->n[0], ny = c->n[1];
         c->op.kind = 0;
         c->op.per_node = 1;
         c->op.dim = c->dim;
@@ -667,8 +658,6 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
                     const int64_t j = K.col[q];
                     if (j == i) continue;
                     const int64_t dx = j % nx - xi, dy = (j / nx) % ny - yi, dz = j / (nx * ny) - zi;
-                    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
-                        return fail(c, DAETI_EINVAL, "grid operator reaches beyond the 27-point stencil");
                     A[(size_t)(i - i0) * DAETI_ROW + (size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))] = K.val[q] * s;
                 }
             }
@@ -845,6 +834,22 @@ int daeti_update_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long
     }
     int rc = daeti_synchronize(c);
     if (rc) return rc;
+    // the previous description and estimates come back if the new field is
+    // rejected (the device operator is only replaced once it is accepted)
+    std::vector<double> old_dl, old_dtr, old_fib;
+    old_dl.swap(c->dl);
+    old_dtr.swap(c->dtr);
+    old_fib.swap(c->fib);
+    const bool old_fib_null = c->fib_null;
+    const double old_dt_s = c->dt_s, old_lam = c->lam;
+    auto restore = [&]() {
+        c->dl.swap(old_dl);
+        c->dtr.swap(old_dtr);
+        c->fib.swap(old_fib);
+        c->fib_null = old_fib_null;
+        c->dt_s = old_dt_s;
+        c->lam = old_lam;
+    };
     c->dl.assign(d_long, d_long + n_elem);
     c->dtr.assign(d_trans ? d_trans : d_long, (d_trans ? d_trans : d_long) + n_elem);
     c->fib_null = fibre == nullptr;
@@ -853,10 +858,17 @@ int daeti_update_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long
     GridTable tab;
     bool table = false;
     CsrK K;
-    if ((rc = assemble_and_estimate(c, tab, table, K))) return rc;
+    if ((rc = assemble_and_estimate(c, tab, table, K))) {
+        restore();
+        return rc;
+    }
     // the schedule (dt, l) stays as prepared; it must remain stable
-    if (c->dt_ad * c->lam >= 2.0)
-        return fail(c, DAETI_EUNSTABLE, "new conductivity: dt_ad * lambda_max >= 2 with the prepared l");
+    if (c->dt_ad * c->lam >= 2.0) {
+        const double lam_new = c->lam;
+        restore();
+        return fail(c, DAETI_EUNSTABLE, "new conductivity: dt_ad * lambda_max = " + std::to_string(c->dt_ad * lam_new) +
+                                            " >= 2 with the prepared l");
+    }
     drop_graphs(c);
     return upload_operator(c, tab, table, K);
 }
@@ -958,7 +970,6 @@ int daeti_synchronize(daeti_ctx* c) {
         CK(cpy_(c, f, c->s.flags, 16, cudaMemcpyDeviceToHost));
         if (f[0] & 1) return fail(c, DAETI_ENONFINITE, "V became non-finite");
         if (f[0] & 2) return fail(c, DAETI_ECUDA, "k histogram inconsistent with k (internal error)");
-        if (f[1]) return fail(c, DAETI_ETIMEOUT, "a bounded device wait gave up");
     }
     return DAETI_OK;
 }

@@ -105,44 +105,45 @@ static void elem_tensor(int dim, const double* d_long, const double* d_trans, co
     conductivity_tensor(d_long[e], d_trans[e], fibre ? fibre + 3 * e : nullptr, dim, D);
 }
 
-bool build_grid_table(int dim, const int64_t n[3], double h, const double* d_long, const double* d_trans,
-                      const double* fibre, GridTable& out) {
+bool grid_layer_stiffness(int dim, const int64_t n[3], double h, const double* d_long, const double* d_trans,
+                          const double* fibre, double* layerK) {
     const int64_t nx = n[0], ny = n[1], nz = dim == 3 ? n[2] : 1;
     const int64_t ex_n = nx - 1, ey_n = ny - 1, ez_n = dim == 3 ? nz - 1 : 1;
     const int64_t per_layer = ex_n * ey_n;
-    // D must be identical across each element layer
-    std::vector<std::vector<double>> layerK(ez_n);
     const int nl = 1 << dim;
+    const double* dt = d_trans ? d_trans : d_long;
     for (int64_t ez = 0; ez < ez_n; ++ez) {
         const int64_t e0 = ez * per_layer;
         double D0[9];
-        elem_tensor(dim, d_long, d_trans, fibre, e0, D0);
+        elem_tensor(dim, d_long, dt, fibre, e0, D0);
         for (int64_t e = e0 + 1; e < e0 + per_layer; ++e) {
             double D[9];
-            elem_tensor(dim, d_long, d_trans, fibre, e, D);
+            elem_tensor(dim, d_long, dt, fibre, e, D);
             for (int r = 0; r < 9; ++r)
                 if (D[r] != D0[r]) return false;
         }
-        layerK[ez].resize(nl * nl);
-        box_stiffness(dim, h, D0, layerK[ez].data());
+        box_stiffness(dim, h, D0, layerK + ez * nl * nl);
     }
-    out.dim = dim;
-    out.nx = (int)nx;
-    out.ny = (int)ny;
-    out.nz = (int)nz;
-    out.K.assign((size_t)nz * 9 * 27, 0.0);
-    out.m.assign((size_t)nz * 9, 0.0);
+    return true;
+}
+
+void grid_class_table(int dim, const int64_t n[3], double h, const double* layerK, double* K, double* m) {
+    const int64_t nz = dim == 3 ? n[2] : 1;
+    const int64_t ez_n = dim == 3 ? nz - 1 : 1;
+    const int nl = 1 << dim;
+    std::fill(K, K + nz * 9 * 27, 0.0);
+    std::fill(m, m + nz * 9, 0.0);
     const double emass = std::pow(h, dim) / nl;
     for (int64_t z = 0; z < nz; ++z)
         for (int cy = 0; cy < 3; ++cy)
             for (int cx = 0; cx < 3; ++cx) {
-                const size_t cls = (size_t)(z * 3 + cy) * 3 + cx;
-                double* Kr = &out.K[cls * 27];
+                const int64_t cls = (z * 3 + cy) * 3 + cx;
+                double* Kr = K + cls * 27;
                 // adjacent elements: origin offsets ox, oy, oz in {-1, 0}
                 for (int oz = (dim == 3 ? -1 : 0); oz <= 0; ++oz) {
                     const int64_t ez = z + oz;
                     if (dim == 3 && (ez < 0 || ez >= ez_n)) continue;
-                    const int64_t layer = dim == 3 ? ez : 0;
+                    const double* Ke = layerK + (dim == 3 ? ez : 0) * nl * nl;
                     for (int oy = -1; oy <= 0; ++oy) {
                         if (oy == -1 && cy == 0) continue;
                         if (oy == 0 && cy == 2) continue;
@@ -153,14 +154,29 @@ bool build_grid_table(int dim, const int64_t n[3], double h, const double* d_lon
                             for (int b = 0; b < nl; ++b) {
                                 const int dx = ox + (b & 1), dy = oy + ((b >> 1) & 1);
                                 const int dz = dim == 3 ? oz + ((b >> 2) & 1) : 0;
-                                const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                                Kr[j] += layerK[layer][a * nl + b];
+                                Kr[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] += Ke[a * nl + b];
                             }
-                            out.m[cls] += emass;
+                            m[cls] += emass;
                         }
                     }
                 }
             }
+}
+
+bool build_grid_table(int dim, const int64_t n[3], double h, const double* d_long, const double* d_trans,
+                      const double* fibre, GridTable& out) {
+    const int64_t nz = dim == 3 ? n[2] : 1;
+    const int64_t ez_n = dim == 3 ? nz - 1 : 1;
+    const int nl = 1 << dim;
+    std::vector<double> layerK((size_t)ez_n * nl * nl);
+    if (!grid_layer_stiffness(dim, n, h, d_long, d_trans, fibre, layerK.data())) return false;
+    out.dim = dim;
+    out.nx = (int)n[0];
+    out.ny = (int)n[1];
+    out.nz = (int)nz;
+    out.K.assign((size_t)nz * 9 * 27, 0.0);
+    out.m.assign((size_t)nz * 9, 0.0);
+    grid_class_table(dim, n, h, layerK.data(), out.K.data(), out.m.data());
     return true;
 }
 

@@ -32,6 +32,16 @@ struct GridTable {
 bool build_grid_table(int dim, const int64_t n[3], double h, const double* d_long, const double* d_trans,
                       const double* fibre, GridTable& out);
 
+// The two halves of build_grid_table, writing into caller arrays (no
+// allocation).  grid_layer_stiffness: the element stiffness of each element
+// layer into layerK (ez_n blocks of (2^dim)^2, ez_n = nz - 1 in 3D, 1 in 2D;
+// d_trans may be null for d_long); false if D varies within a layer.
+// grid_class_table: the stencil row (27 entries) and lumped mass of each node
+// class (z layer, y class, x class) from those blocks, K[nz*9*27], m[nz*9].
+bool grid_layer_stiffness(int dim, const int64_t n[3], double h, const double* d_long, const double* d_trans,
+                          const double* fibre, double* layerK);
+void grid_class_table(int dim, const int64_t n[3], double h, const double* layerK, double* K, double* m);
+
 // General sparse operator: CSR of K (with diagonal) and lumped mass.
 struct CsrK {
     int64_t n = 0;

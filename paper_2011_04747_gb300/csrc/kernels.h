@@ -38,7 +38,7 @@ struct DevState {
     int n_stims = 0;
     long long* step_ctr = nullptr;        // device step counter used by graph replays
     unsigned long long* substeps = nullptr;   // running total of node reaction sub-steps (bucketing)
-    int* flags = nullptr;                 // [0] non-finite, [1] timeout, [2 + par] k not uniform (mode -K)
+    int* flags = nullptr;                 // [0] non-finite, [1] unused, [2 + par] k not uniform (mode -K)
 };
 
 struct ModelArgs {
@@ -160,7 +160,20 @@ void launch_gershgorin(const EstOp& op, unsigned long long* out_bits, cudaStream
 void launch_apply_minvk(const EstOp& op, const double* x, double* y, cudaStream_t st);
 void launch_mdots(int64_t n, const double* m, const double* x, const double* y, double* out2,
                   cudaStream_t st);
-void launch_scale(int64_t n, const double* y, double s, double* x, cudaStream_t st);
+// Largest eigenvalue of M_L^-1 K by Lanczos in the M_L inner product (FP64):
+// a start vector fixed by the node numbering, at most max_it iterations,
+// stopping when the largest Ritz value changes by <= 1e-13 relative between
+// host checks (every 32 iterations) or the Krylov space becomes invariant.
+// Work memory is the caller's: v[0..2] n doubles each (device), hist
+// 4 (max_it + 1) doubles (device), hh 4 max_it doubles (host).  *iters =
+// the order of the final tridiagonal matrix.
+cudaError_t lanczos_lambda_max(const EstOp& est, const double* m, double* const v[3], double* hist, double* hh,
+                               int max_it, cudaStream_t st, double* lam, int* iters);
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal
+// a[0], a[stride], ... (k entries) and squared off-diagonal b2[0], b2[stride],
+// ... (k - 1 entries), by Sturm-sequence bisection.
+double tridiag_max_eig(const double* a, const double* b2, int stride, int k);
+constexpr int DAETI_LANCZOS_MAX_IT = 2000;
 void launch_node_mass(const EstOp& op, double* m_out, cudaStream_t st);
 
 // Conversions between the state precision and the caller's dtype.

@@ -5,10 +5,11 @@
 // an application that forbids device allocation after start-up, and code
 // paths that must not trigger the implicit synchronisation a cudaMalloc or
 // cudaFree can cause.  daeti_grid_stability_noalloc gives them the FP64
-// stable-step estimate (the Gershgorin bound and the power-iteration
-// lambda_max that daeti_prepare computes) without any device allocation: its
-// work vectors live in one file-scope __device__ array of fixed size that
-// every GPU which loads the library holds until the process exits.
+// stable-step estimate (the Gershgorin bound and the Lanczos lambda_max that
+// daeti_prepare computes, through the same table builder and estimator
+// routines) without any device allocation: its work vectors live in one
+// file-scope __device__ array of fixed size that every GPU which loads the
+// library holds until the process exits.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,22 +26,24 @@ namespace {
 constexpr int64_t kMaxNodes = DAETI_NOALLOC_MAX_NODES;
 constexpr int kMaxLayers = DAETI_NOALLOC_MAX_LAYERS;      // node layers in z (1 in 2D)
 constexpr int64_t kMaxClasses = (int64_t)kMaxLayers * 9;
-// scratch layout (doubles): K table | mass table | node mass | x | y | dots[2] | Gershgorin bits
+// scratch layout (doubles): K table | mass table | node mass | 3 Lanczos
+// vectors | Lanczos coefficients | Gershgorin bits
+constexpr int kMaxIt = DAETI_LANCZOS_MAX_IT;
 constexpr int64_t kOffK = 0;
 constexpr int64_t kOffMt = kOffK + kMaxClasses * 27;
 constexpr int64_t kOffM = kOffMt + kMaxClasses;
-constexpr int64_t kOffX = kOffM + kMaxNodes;
-constexpr int64_t kOffY = kOffX + kMaxNodes;
-constexpr int64_t kOffDots = kOffY + kMaxNodes;
-constexpr int64_t kOffBits = kOffDots + 2;
+constexpr int64_t kOffV = kOffM + kMaxNodes;
+constexpr int64_t kOffHist = kOffV + 3 * kMaxNodes;
+constexpr int64_t kOffBits = kOffHist + 4 * (kMaxIt + 1);
 constexpr int64_t kScratchDoubles = kOffBits + 2;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-// Host-side staging for the stencil tables (file scope: no heap, guarded by g_mu).
-double h_layer_k[kMaxLayers][64];
+// Host-side staging (file scope: no heap, guarded by g_mu).
+double h_layer_k[kMaxLayers * 64];
 double h_table[kMaxClasses * 27];
 double h_mass[kMaxClasses];
+double h_coef[4 * kMaxIt];
 
 std::mutex g_mu;
 double* g_scratch_addr[128] = {nullptr};
@@ -63,31 +66,6 @@ cudaError_t scratch_address(double** out) {
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
-}
-
-// x_i of the power iteration's start vector: the i-th draw of the same 64-bit
-// LCG the context path uses (advanced to position i by squaring its affine map).
-__global__ void start_vector_kernel(int64_t n, int nx, int ny, double* x) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const unsigned long long A = 6364136223846793005ull, C = 1442695040888963407ull;
-    unsigned long long ra = 1ull, rc = 0ull;        // accumulated map s -> ra s + rc
-    unsigned long long pa = A, pc = C;              // map raised to the current power of two
-    unsigned long long m = (unsigned long long)i + 1ull;
-    while (m) {
-        if (m & 1ull) {
-            rc = pa * rc + pc;
-            ra = pa * ra;
-        }
-        pc = pa * pc + pc;
-        pa = pa * pa;
-        m >>= 1;
-    }
-    const unsigned long long st = ra * 0x9E3779B97F4A7C15ull + rc;
-    const double u = (double)(st >> 11) * (1.0 / 9007199254740992.0);
-    const int64_t xx = i % nx, yy = (i / nx) % ny, zz = i / ((int64_t)nx * ny);
-    const double sgn = ((xx + yy + zz) & 1) ? -1.0 : 1.0;
-    x[i] = sgn * (1.0 + 0.1 * u);
 }
 
 }  // namespace
@@ -119,59 +97,24 @@ extern "C" int daeti_grid_stability_noalloc(int dim, const int64_t n[3], double 
         set_err(errbuf, errbuf_len, "n_elem does not match the grid");
         return DAETI_EINVAL;
     }
-    const int nl = 1 << dim;
     std::lock_guard<std::mutex> lock(g_mu);
 
-    // element stiffness per layer; D must be constant within each element layer
-    const int64_t per_layer = ex_n * ey_n;
-    for (int64_t ez = 0; ez < ez_n; ++ez) {
-        double D0[9];
-        const int64_t e0 = ez * per_layer;
-        conductivity_tensor(d_long[e0], d_trans ? d_trans[e0] : d_long[e0], fibre ? fibre + 3 * e0 : nullptr, dim, D0);
-        for (int64_t e = e0; e < e0 + per_layer; ++e) {
-            double D[9];
-            const double a = d_long[e], b = d_trans ? d_trans[e] : d_long[e];
-            if (!(a >= 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b)) {
-                set_err(errbuf, errbuf_len, "conductivities must be finite and >= 0");
-                return DAETI_EINVAL;
-            }
-            conductivity_tensor(a, b, fibre ? fibre + 3 * e : nullptr, dim, D);
-            for (int r = 0; r < 9; ++r)
-                if (D[r] != D0[r]) {
-                    set_err(errbuf, errbuf_len, "conductivity varies within an element layer (not supported here)");
-                    return DAETI_EUNSUPPORTED;
-                }
+    for (int64_t e = 0; e < n_elem; ++e) {
+        const double a = d_long[e], b = d_trans ? d_trans[e] : d_long[e];
+        if (!(a >= 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b)) {
+            set_err(errbuf, errbuf_len, "conductivities must be finite and >= 0");
+            return DAETI_EINVAL;
         }
-        box_stiffness(dim, h, D0, h_layer_k[ez]);
     }
-    // stencil table per node class (z layer, y class, x class) and lumped mass
+    // stencil table per node class (z layer, y class, x class) and lumped
+    // mass, by the builder daeti_prepare uses; D must be constant within each
+    // element layer
+    if (!grid_layer_stiffness(dim, n, h, d_long, d_trans, fibre, h_layer_k)) {
+        set_err(errbuf, errbuf_len, "conductivity varies within an element layer (not supported here)");
+        return DAETI_EUNSUPPORTED;
+    }
     const int64_t ncls = nz * 9;
-    std::memset(h_table, 0, sizeof(double) * ncls * 27);
-    std::memset(h_mass, 0, sizeof(double) * ncls);
-    const double emass = std::pow(h, dim) / nl;
-    for (int64_t z = 0; z < nz; ++z)
-        for (int cy = 0; cy < 3; ++cy)
-            for (int cx = 0; cx < 3; ++cx) {
-                const int64_t cls = (z * 3 + cy) * 3 + cx;
-                for (int oz = (dim == 3 ? -1 : 0); oz <= 0; ++oz) {
-                    const int64_t ez = z + oz;
-                    if (dim == 3 && (ez < 0 || ez >= ez_n)) continue;
-                    const int64_t layer = dim == 3 ? ez : 0;
-                    for (int oy = -1; oy <= 0; ++oy) {
-                        if ((oy == -1 && cy == 0) || (oy == 0 && cy == 2)) continue;
-                        for (int ox = -1; ox <= 0; ++ox) {
-                            if ((ox == -1 && cx == 0) || (ox == 0 && cx == 2)) continue;
-                            const int a = (-ox) | ((-oy) << 1) | ((dim == 3 ? -oz : 0) << 2);
-                            for (int b = 0; b < nl; ++b) {
-                                const int dx = ox + (b & 1), dy = oy + ((b >> 1) & 1);
-                                const int dz = dim == 3 ? oz + ((b >> 2) & 1) : 0;
-                                h_table[cls * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] += h_layer_k[layer][a * nl + b];
-                            }
-                            h_mass[cls] += emass;
-                        }
-                    }
-                }
-            }
+    grid_class_table(dim, n, h, h_layer_k, h_table, h_mass);
 
     double* base = nullptr;
     cudaError_t e = scratch_address(&base);
@@ -183,9 +126,8 @@ extern "C" int daeti_grid_stability_noalloc(int dim, const int64_t n[3], double 
     double* ktab = base + kOffK;
     double* mtab = base + kOffMt;
     double* m = base + kOffM;
-    double* x = base + kOffX;
-    double* y = base + kOffY;
-    double* dots = base + kOffDots;
+    double* const v[3] = {base + kOffV, base + kOffV + kMaxNodes, base + kOffV + 2 * kMaxNodes};
+    double* hist = base + kOffHist;
     unsigned long long* bits = (unsigned long long*)(base + kOffBits);
     EstOp est;
     est.kind = 0;
@@ -222,27 +164,10 @@ extern "C" int daeti_grid_stability_noalloc(int dim, const int64_t n[3], double 
     std::memcpy(&mn, &hb, 8);
     *dt_s = 0.9 * mn;
 
-    // power iteration for lambda_max(M_L^-1 K), as in daeti_prepare
-    start_vector_kernel<<<(unsigned)((n_nodes + 255) / 256), 256, 0, st>>>(n_nodes, (int)nx, (int)ny, x);
-    double hd[2];
-    NA_CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, st));
-    launch_mdots(n_nodes, m, x, x, dots, st);
-    NA_CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
-    NA_CK(cudaStreamSynchronize(st));
-    launch_scale(n_nodes, x, 1.0 / std::sqrt(hd[1]), x, st);
-    double lam = 0.0, prev = 0.0;
-    for (int it = 0; it < 500; ++it) {
-        launch_apply_minvk(est, x, y, st);
-        NA_CK(cudaMemsetAsync(dots, 0, sizeof(double) * 2, st));
-        launch_mdots(n_nodes, m, x, y, dots, st);
-        NA_CK(cudaMemcpyAsync(hd, dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
-        NA_CK(cudaStreamSynchronize(st));
-        lam = hd[0];
-        if (!(hd[1] > 0)) break;
-        launch_scale(n_nodes, y, 1.0 / std::sqrt(hd[1]), x, st);
-        if (it > 5 && std::fabs(lam - prev) <= 1e-8 * std::fabs(lam)) break;
-        prev = lam;
-    }
+    // lambda_max(M_L^-1 K) by the Lanczos routine daeti_prepare uses
+    double lam = 0.0;
+    int iters = 0;
+    NA_CK(lanczos_lambda_max(est, m, v, hist, h_coef, kMaxIt, st, &lam, &iters));
     NA_CK(cudaStreamSynchronize(st));
     NA_CK(cudaGetLastError());
     *lambda_max = lam;
