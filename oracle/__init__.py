@@ -29,7 +29,12 @@ matrix exponential, conservation, the Strang/merge structure, the k and l
 rules, Mitchell-Schaeffer fixed points / threshold / APD asymptote, the cubic
 front speed, the adjoint (dot-product test and central differences).
 TP06: parity unpinned against the TP06 publication itself (its equations are
-not part of the paper); pinned only by charge conservation, gate bounds,
-consistency of its fast-gate steady states with its published initial state,
-and fine-step self-convergence.
+not part of the paper); pinned by the thermal voltage from SI constants, the
+reversal potential of every current (Nernst, GHK and exchanger zeros), the
+pump half-saturation points, bounded monotone gates with positive time
+constants, the published initial state being a resting state (fast gates at
+steady state, net current balanced, 1000 ms unstimulated drift < 0.5 mV),
+charge conservation, AP plausibility and fine-step self-convergence.  The
+magnitudes of currents that vanish at rest (GNa, GKr, GKs, Gto, GpK) and the
+SR/buffer constants are pinned only by AP plausibility.
 """

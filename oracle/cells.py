@@ -92,6 +92,31 @@ class TP06:
     which makes the total charge of the cell an exact invariant of the ODEs.
     The I_CaL factor (V-15)/(exp(2(V-15)F/RT) - 1) is evaluated through
     x / expm1(x) with its limit 1 at x = 0 (removable singularity at 15 mV).
+
+    Parity: unpinned against the model's publication (the paper does not
+    contain it).  What pins each part (tests/test_oracle_tp06_pins.py,
+    tests/test_oracle_cells.py):
+
+    * constants R, T, F: the thermal voltage k_B T / e from SI constants;
+    * ``gates``: steady states in [0, 1] and monotone in V, time constants
+      positive and finite (a sign or offset typo in an exponent fails), the
+      published resting state holding m, h, xr2, r, s, d at their steady
+      states within 0.3 %; the slow gates' time constants only by the AP
+      plausibility test (peak, APD90);
+    * ``currents``: each (V - E) current vanishes at its Nernst potential
+      with the sign of V - E (E_K, E_Na, E_Ca, E_Ks); I_CaL at its GHK zero;
+      I_NaCa at 3 E_Na - 2 E_Ca + (RT/F) ln(alf); the I_NaK and I_pCa
+      half-saturation points; the resting balance of the published state
+      (|dV/dt| < 0.002 mV/ms), which fails for a change of a few per cent in
+      GK1, knaca, knak, GbNa, GbCa, GpCa, KmNa, KpCa, alf, Ko or GCaL;
+      GNa, GKr, GKs, Gto and GpK (currents that are ~0 at rest) only by the AP
+      plausibility test;
+    * ``rates``: charge conservation converging with dt (the stoichiometry
+      of Na, K and Ca fluxes and the Cm/(V F) factors); the SR and buffer
+      constants (Vmaxup, Vrel, Vleak, Vxfer, k1p..., Vc, Vsr, Vss) only by
+      the AP plausibility test and the 1000 ms resting drift (< 0.5 mV);
+    * ``substep``: the adaptive step A against a 0.004 ms integration
+      (self-convergence) and gates kept in [0, 1] through an AP.
     """
 
     name = "tp06"
