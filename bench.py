@@ -35,6 +35,10 @@ UNIT = "node-steps/s"
 SLAB = dict(nx=101, ny=101, nz=26, h=0.02)
 T_END = 500.0
 ORACLE_SAMPLE_STEPS = 20
+# the CPU-baseline window: Strang steps 100..119 (10-12 ms), while the
+# wavefront crosses the slab (the first 2 ms are the stimulus at rest)
+ORACLE_WINDOW_START = 100
+REDUCED_SLAB = dict(nx=25, ny=23, nz=7)    # FP32 vs the oracle over the whole 500 ms
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 XU_LANES_PER_SM = 16
@@ -93,35 +97,117 @@ def _peaks():
 
 
 # ------------------------------------------------------------------ reference arm
+def _oracle_at_window(wl):
+    """The oracle advanced (untimed) to the start of the CPU-baseline window."""
+    from oracle import scheme
+
+    sim = scheme.simulation_from_workload(wl)
+    sim.run(ORACLE_WINDOW_START)
+    return sim
+
+
+def _oracle_snapshot(sim):
+    return (sim.S.copy(), sim.n, sim.v_sync.copy(), sim.k.copy(), sim.act.copy(), sim.rrate.copy())
+
+
+def _oracle_restore(sim, snap):
+    S, n, vs, k, act, rr = snap
+    sim.S[:] = S
+    sim.n = n
+    sim.v_sync[:] = vs
+    sim.k[:] = k
+    sim.act[:] = act
+    sim.rrate[:] = rr
+
+
+def _oracle_window_seconds(sim, snap, steps):
+    _oracle_restore(sim, snap)
+    t0 = time.perf_counter()
+    sim.run(steps)
+    return time.perf_counter() - t0
+
+
+def _window_worker(slab, t_end, steps, barrier, out):
+    """One host core of the all-core baseline: its own oracle on the same window."""
+    import inputs
+
+    sim = _oracle_at_window(inputs.tp06_slab_3d(**slab, t_end=t_end))
+    snap = _oracle_snapshot(sim)
+    barrier.wait()
+    out.put(_oracle_window_seconds(sim, snap, steps))
+
+
+def _all_core_window(steps):
+    """Every host core runs the oracle on the window at once (spawned
+    processes, one numpy thread each); aggregate node-steps/s."""
+    import multiprocessing as mp
+
+    import inputs
+
+    cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_window_worker, args=(SLAB, T_END, steps, barrier, out)) for _ in range(cores)]
+    for p in procs:
+        p.start()
+    secs = [out.get() for _ in procs]
+    for p in procs:
+        p.join()
+    n = inputs.tp06_slab_3d(**SLAB, t_end=T_END).n_nodes
+    return {"value": sum(n * steps / t for t in secs), "cores": cores, "max_s": max(secs)}
+
+
 def run_reference(args):
-    """CPU oracle on a bounded sample of the slab workload (rank 0 only)."""
+    """CPU oracle on a bounded sample of the slab workload (rank 0 only):
+    each timed step runs the oracle over Strang steps 100..119 (10-12 ms,
+    the wavefront crossing the slab) from a state the oracle reached itself."""
     rank, world = _dist()
     if rank != 0:
         return
     import inputs
-    from oracle import scheme
 
     wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
+    sim = _oracle_at_window(wl)
+    snap = _oracle_snapshot(sim)
     times = []
     for it in range(args.warmup + args.steps):
-        sim = scheme.simulation_from_workload(wl)
-        t0 = time.perf_counter()
-        sim.run(ORACLE_SAMPLE_STEPS)
+        sec = _oracle_window_seconds(sim, snap, ORACLE_SAMPLE_STEPS)
         if it >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(sec)
     sec = sum(times) / len(times)
     value = wl.n_nodes * ORACLE_SAMPLE_STEPS / sec
-    sample = (f"full slab ({wl.n_nodes} nodes), first {ORACLE_SAMPLE_STEPS} Strang steps (2 ms, stimulus on) "
-              f"per step, numpy FP64 on one host core")
+    sample = (f"full slab ({wl.n_nodes} nodes), Strang steps {ORACLE_WINDOW_START}..{ORACLE_WINDOW_START + ORACLE_SAMPLE_STEPS - 1} "
+              f"(wavefront) per step, numpy FP64 on one host core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "tp06_slab_101x101x26_h0.02", "sample_steps": ORACLE_SAMPLE_STEPS},
+        "config": {"workload": "tp06_slab_101x101x26_h0.02", "sample_steps": ORACLE_SAMPLE_STEPS,
+                   "window_start_step": ORACLE_WINDOW_START},
         "sim_ms_per_wall_s": ORACLE_SAMPLE_STEPS * 0.1 / sec,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def _cpu_baseline_slab(wl, all_cores=True):
+    """The oracle on the wavefront window of the slab: one core, and every core at once."""
+    sim = _oracle_at_window(wl)
+    snap = _oracle_snapshot(sim)
+    sec = _oracle_window_seconds(sim, snap, ORACLE_SAMPLE_STEPS)
+    out = {"value": wl.n_nodes * ORACLE_SAMPLE_STEPS / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{wl.name}: Strang steps {ORACLE_WINDOW_START}..{ORACLE_WINDOW_START + ORACLE_SAMPLE_STEPS - 1} "
+                     f"(10-12 ms, wavefront) from the oracle's own state, numpy FP64, one host core, {sec:.1f} s"}
+    if all_cores:
+        try:
+            out["all_cores"] = _all_core_window(ORACLE_SAMPLE_STEPS)
+            out["all_cores"]["unit"] = UNIT
+            out["all_cores"]["sample"] = "the same window run by one oracle process per host core at once"
+        except Exception as e:          # reported, not fatal: the GPU numbers stand without it
+            out["all_cores"] = {"error": repr(e)}
+    return out
 
 
 def _cpu_baseline_sample(wl, steps=ORACLE_SAMPLE_STEPS):
@@ -198,6 +284,140 @@ class Env:
         return self.max_over_ranks(sum(times) / len(times))
 
 
+def _aligned_max_dv(snaps_a, snaps_b, act_a, act_b, every_ms, after_ms=5.0):
+    """max over nodes and snapshots t >= act_a + after_ms of |V_a(t) - V_b(t + act_b - act_a)|
+    (V_b linearly interpolated between snapshots; reading R-dV: traces aligned
+    by their activation times; the upstroke itself is left out, where 1 ms
+    snapshots cannot resolve a ~300 mV/ms slope)."""
+    import numpy as np
+
+    m, n = snaps_a.shape
+    t = (np.arange(m) + 1) * every_ms
+    both = (act_a >= 0) & (act_b >= 0)
+    shift = np.where(both, act_b - act_a, 0.0)
+    worst = 0.0
+    cols = np.arange(n)
+    for j in range(m):
+        ok = both & (t[j] >= act_a + after_ms)
+        f = (t[j] + shift) / every_ms - 1.0
+        i0 = np.floor(f).astype(np.int64)
+        ok &= (i0 >= 0) & (i0 < m - 1)
+        if not ok.any():
+            continue
+        i0c = np.clip(i0, 0, m - 2)
+        w = f - i0c
+        vb = (1.0 - w) * snaps_b[i0c, cols] + w * snaps_b[i0c + 1, cols]
+        d = np.abs(snaps_a[j].astype(np.float64) - vb)[ok]
+        worst = max(worst, float(d.max()))
+    return worst
+
+
+def _fp32_vs_fp64(s32, ck, s64, n_steps, dt, every=10):
+    """Lockstep FP32 and FP64 runs of the same workload from the same initial
+    state, V of every node every `every` steps (1 ms) over the whole run."""
+    import numpy as np
+
+    s32.daeti_load_state(ck)
+    s64.daeti_init_state(None)
+    m = n_steps // every
+    n = s32.n_nodes
+    a32, a64 = np.empty((m, n), np.float32), np.empty((m, n), np.float32)
+    for j in range(m):
+        t = (j + 1) * every * dt
+        s32.daeti_advance(t)
+        s64.daeti_advance(t)
+        a32[j] = s32.daeti_read_v()
+        a64[j] = s64.daeti_read_v()
+    act32, act64 = s32.daeti_read_activation(), s64.daeti_read_activation()
+    dv_t = np.abs(a32.astype(np.float64) - a64.astype(np.float64)).max(axis=1)
+    both = (act32 >= 0) & (act64 >= 0)
+    out = {"snapshots": m, "snapshot_every_ms": every * dt,
+           "max_abs_dv_mv": float(dv_t.max()), "at_ms": float((int(np.argmax(dv_t)) + 1) * every * dt),
+           "max_abs_dv_mv_at_end": float(dv_t[-1]),
+           "max_abs_dv_mv_aligned_from_5ms_after_activation":
+               _aligned_max_dv(a32, a64, act32, act64, every * dt),
+           "max_abs_dact_ms": float(np.abs(act32[both] - act64[both]).max()) if both.any() else None,
+           "same_activated_set": bool(np.array_equal(act32 >= 0, act64 >= 0))}
+    del a32, a64
+    return out
+
+
+def _fp32_vs_oracle_reduced(binding):
+    """FP32 GPU vs the FP64 oracle on a reduced slab (same physics, 25 x 23 x 7
+    nodes) over the whole 500 ms, V of every node every 1 ms."""
+    import numpy as np
+
+    import inputs
+    from oracle import scheme
+
+    wl = inputs.tp06_slab_3d(**REDUCED_SLAB, t_end=T_END)
+    n_steps, every = int(round(T_END / wl.dt)), 10
+    g = binding.solver_from_workload(wl, precision="fp32_kahan")
+    sim = scheme.simulation_from_workload(wl)
+    t0 = time.perf_counter()
+    m = n_steps // every
+    gs, os_ = np.empty((m, wl.n_nodes)), np.empty((m, wl.n_nodes))
+    for j in range(m):
+        g.daeti_advance((j + 1) * every * wl.dt)
+        gs[j] = g.daeti_read_v()
+        sim.run(every)
+        os_[j] = sim.S[0]
+    ga = g.daeti_read_activation()
+    g.close()
+    dv_t = np.abs(gs - os_).max(axis=1)
+    both = (ga >= 0) & (sim.act >= 0)
+    return {"workload": f"tp06_slab_{wl.n[0]}x{wl.n[1]}x{wl.n[2]}_h0.02_500ms", "nodes": wl.n_nodes,
+            "max_abs_dv_mv": float(dv_t.max()), "at_ms": float((int(np.argmax(dv_t)) + 1) * every * wl.dt),
+            "max_abs_dv_mv_aligned_from_5ms_after_activation": _aligned_max_dv(gs, os_, ga, sim.act, every * wl.dt),
+            "max_abs_dact_ms": float(np.abs(ga[both] - sim.act[both]).max()) if both.any() else None,
+            "same_activated_set": bool(np.array_equal(ga >= 0, sim.act >= 0)),
+            "oracle_s": time.perf_counter() - t0}
+
+
+def _adjoint_precision(binding, stream):
+    """Adjoint workload (256 x 256 MS, 2000 steps, 64 sensors every 1 ms,
+    32 slots): FP32 gradient against the FP64 gradient of the same schedule."""
+    import numpy as np
+
+    import inputs
+
+    wl, d_node, sensors, _ = inputs.ms_adjoint_2d()
+    nx = wl.n[0]
+    ey, ex = np.meshgrid(np.arange(nx - 1), np.arange(nx - 1), indexing="ij")
+    conn = (ex + nx * ey).ravel()[:, None] + np.array([0, 1, nx, nx + 1])[None, :]
+
+    def solver(de, prec):
+        w = inputs.Workload(**{**wl.__dict__, "d_long": de, "d_trans": de, "fibre": None})
+        s = binding.solver_from_workload(w, precision=prec)
+        s.daeti_set_stream(stream)
+        return s
+
+    n_steps, every = 2000, 10
+    g2 = inputs.lognormal_field_2d(nx, wl.h, seed_index=23) / 0.001
+    tgt = solver((d_node * g2 ** 0.5)[conn].mean(axis=1), "fp64")
+    data = []
+    for j in range(n_steps // every):
+        tgt.daeti_advance((j + 1) * every * wl.dt)
+        data.append(tgt.daeti_read_v()[sensors])
+    tgt.close()
+    data = np.array(data)
+    de = d_node[conn].mean(axis=1)
+    res = {}
+    for prec in ("fp64", "fp32_kahan"):
+        s = solver(de, prec)
+        res[prec] = s.daeti_adjoint(sensors, data, n_steps, every, 32, n_elem=len(de))
+        s.close()
+    (l64, g64, t64), (l32, g32, t32) = res["fp64"], res["fp32_kahan"]
+    rng = np.random.default_rng(2011047 + 4)
+    dirs = [rng.standard_normal(len(de)) * de for _ in range(20)]
+    dd = [abs(g32 @ u - g64 @ u) / abs(g64 @ u) for u in dirs]
+    return {"workload": "ms_adjoint_256x256_2000steps_32slots", "loss_rel_err": abs(l32 - l64) / abs(l64),
+            "grad_d_rel_err_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+            "grad_d_rel_err_max": float(np.abs(g32 - g64).max() / np.abs(g64).max()),
+            "directional_rel_err_max_20_dirs": float(max(dd)),
+            "grad_tau_close_rel_err": abs(t32 - t64) / abs(t64)}
+
+
 def _reaction_roofline(solver, clocks, sub_per_step):
     """ALU roofline of the reaction kernel from the per-launch event-timed pass."""
     ms, nl = solver.daeti_get_kernel_time(0)
@@ -257,26 +477,33 @@ def bench_slab(args, env):
         sampler.wait()
         fh.close()
     clocks = _clock_summary(clk_path, env.local)
-    v32 = s32.daeti_read_v()
-    a32 = s32.daeti_read_activation()
     sub_total = s32.daeti_get_substeps()          # counted since the last load_state: one 500 ms run
     sub_per_step = sub_total / n_steps if sub_total else 0.0
     value = env.world * n_nodes * n_steps / sec32
 
-    # per-kernel timing pass (events around every launch, plain launches)
-    s32.daeti_load_state(ck)
-    s32.daeti_set_profiling(True)
-    s32.daeti_advance(T_END)
-    s32.daeti_synchronize()
-    kt = {}
-    for which, name in ((0, "reaction"), (1, "diffusion")):
-        ms, nl = s32.daeti_get_kernel_time(which)
-        b, f = s32.daeti_kernel_work(which)
-        kt[name] = {"total_ms": ms, "launches": nl, "avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b}
-    roof = _reaction_roofline(s32, clocks, sub_per_step)
-    d = kt["diffusion"]
-    d["bytes_GBs"] = d["bytes_per_launch"] / (d["avg_us"] * 1e-6) / 1e9
-    s32.daeti_set_profiling(False)
+    # per-kernel timing passes over the same 500 ms: mode 2 = event-record
+    # nodes around every launch inside the captured graphs (the roofline's
+    # kernel time), mode 1 = events around plain launches (adds the host
+    # launch cost to each interval; kept for comparison)
+    kt, kt_plain = {}, {}
+    for mode, dst in ((2, kt), (1, kt_plain)):
+        s32.daeti_load_state(ck)
+        s32.daeti_set_profiling(mode)
+        s32.daeti_advance(T_END)
+        s32.daeti_synchronize()
+        for which, name in ((0, "reaction"), (1, "diffusion")):
+            ms, nl = s32.daeti_get_kernel_time(which)
+            b, f = s32.daeti_kernel_work(which)
+            dst[name] = {"total_ms": ms, "launches": nl, "avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b}
+        if mode == 2:
+            roof = _reaction_roofline(s32, clocks, sub_per_step)
+        else:
+            roof["plain_launch_frac"] = _reaction_roofline(s32, clocks, sub_per_step)["frac"]
+        d = dst["diffusion"]
+        d["bytes_GBs"] = d["bytes_per_launch"] / (d["avg_us"] * 1e-6) / 1e9
+        s32.daeti_set_profiling(0)
+    roof["timing"] = ("CUDA events recorded by graph nodes around each reaction launch of the 500 ms run "
+                      "(graphs of the tuned length, launched without programmatic dependent launch)")
 
     # e2e through the C ABI with host buffers: the initial state (published
     # values at every node, n_states x n doubles) from pinned host memory
@@ -296,19 +523,22 @@ def bench_slab(args, env):
     e2e_val = env.world * n_nodes * n_steps / env.max_over_ranks(sum(e2e) / len(e2e))
     ns = s32.n_states
     tuning_used = s32.daeti_get_tuning()
-    s32.close()
 
-    sec64 = dv = dact = None
+    sec64 = err64 = None
     if not args.no_fp64:
         s64 = make("fp64")
         sec64 = env.timed(lambda: s64.daeti_advance(T_END), max(1, args.steps // 2), 1,
                           reset=lambda: s64.daeti_init_state(None))
-        v64, a64 = s64.daeti_read_v(), s64.daeti_read_activation()
+        # V of every node every 1 ms of the whole run in both precisions
+        err64 = _fp32_vs_fp64(s32, ck, s64, n_steps, wl.dt)
         s64.close()
-        both = (a32 >= 0) & (a64 >= 0)
-        dv = float(np.max(np.abs(v32 - v64)))
-        dact = float(np.max(np.abs(a32[both] - a64[both]))) if both.any() else None
+    err_oracle = adj_err = None
+    if env.rank == 0 and not args.no_cpu_baseline:
+        err_oracle = _fp32_vs_oracle_reduced(binding)
+    if not args.no_fp64:
+        adj_err = _adjoint_precision(binding, env.stream)
 
+    s32.close()
     # launches per step as counted by the per-kernel pass (the same sequence the graphs replay)
     launches_per_step = (kt["reaction"]["launches"] + kt["diffusion"]["launches"]) / n_steps
     line = {
@@ -322,16 +552,18 @@ def bench_slab(args, env):
         "sim_ms_per_wall_s": env.world * T_END / sec32,
         "fp64": None if sec64 is None else {"value": env.world * n_nodes * n_steps / sec64,
                                              "ms_per_step": sec64 * 1e3, "sim_ms_per_wall_s": T_END / sec64},
-        "fp32_vs_fp64": {"max_abs_dv_mv_at_500ms": dv, "max_abs_dact_ms": dact},
+        "fp32_vs_fp64": err64,
+        "fp32_vs_oracle": err_oracle,
+        "adjoint_fp32_vs_fp64": adj_err,
         "reaction_substeps_per_node_step": sub_per_step / n_nodes if sub_per_step else None,
-        "kernels": kt, "roofline": roof, "clocks": clocks,
+        "kernels": kt, "kernels_plain_launches": kt_plain, "roofline": roof, "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n_nodes * ns * 8,
                 "d2h_bytes_per_step": 2 * n_nodes * 8},
         "gpu_launches": int(round(launches_per_step * n_steps + n_steps // max(tuning_used["graph_steps"], 1) + 2))
         * args.steps,
     }
     if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline_sample(wl)
+        line["cpu_baseline"] = _cpu_baseline_slab(wl)
     return line
 
 

@@ -306,10 +306,15 @@ int daeti_batch_info(daeti_batch* batch, int64_t* n_nodes, int* n_tissues, int* 
 int daeti_batch_read_v(daeti_batch* batch, int tissue, double* out);
 int daeti_batch_read_activation(daeti_batch* batch, int tissue, double* out);
 
-/* Per-kernel timing (CUDA events around every launch of the plain-launch
- * path; graphs are not used while it is on).  which: 0 reaction,
- * 1 diffusion (plain sub-steps and fused step B), 2 other.  Returns total milliseconds and launch count
- * since profiling was enabled. */
+/* Per-kernel timing.  enable = 1: CUDA events around every launch of the
+ * plain-launch path (graphs are not used; each timed interval includes the
+ * host launch cost).  enable = 2: runs of graph_steps steps replay captured
+ * graphs in which every launch is bracketed by event-record nodes and
+ * launched without programmatic dependent launch; the intervals are read
+ * after each replay (steps outside whole graphs are timed as with 1).
+ * 0 = off.  which: 0 reaction, 1 diffusion (plain sub-steps and fused step
+ * B), 2 other.  Returns total milliseconds and launch count since profiling
+ * was last set.  Errors: EINVAL (mode). */
 int daeti_set_profiling(daeti_ctx* ctx, int enable);
 int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* launches);
 

@@ -410,7 +410,9 @@ class Solver:
         return self.daeti_get_tuning()
 
     def daeti_set_profiling(self, enable=True):
-        self._check(self.lib.daeti_set_profiling(self.ctx, int(bool(enable))))
+        """True/1: events around plain launches; 2: event-record nodes inside graphs; False/0: off."""
+        mode = enable if isinstance(enable, int) and not isinstance(enable, bool) else int(bool(enable))
+        self._check(self.lib.daeti_set_profiling(self.ctx, mode))
 
     def daeti_get_kernel_time(self, which):
         ms = ctypes.c_double()

@@ -95,11 +95,16 @@ void elem_means(const daeti_ctx* c, const double* nodal, std::vector<double>& ou
 namespace {
 
 void drop_graphs(daeti_ctx* c) {
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
         if (c->graphs[i]) {
             cudaGraphExecDestroy(c->graphs[i]);
             c->graphs[i] = nullptr;
         }
+        if (c->pgraphs[i]) {
+            cudaGraphExecDestroy(c->pgraphs[i]);
+            c->pgraphs[i] = nullptr;
+        }
+    }
 }
 
 void free_device(daeti_ctx* c) {
@@ -121,16 +126,39 @@ int n_states_of(int model) { return model == DAETI_MODEL_MS ? 2 : 19; }
 StepRef plain_ref(int64_t n) { return StepRef{nullptr, (long long)n}; }
 
 // ---- launch wrappers (optionally timed with events: 0 reaction, 1 diffusion, 2 other)
+// Plain launches: events on both sides, waited for.  Inside the capture of a
+// profiling graph: event-record nodes on both sides (cudaEventRecordExternal),
+// read after each replay.
+void gmark(daeti_ctx* c, cudaStream_t st, int which, bool begin) {
+    const int q = c->gnext++;
+    while ((int)c->gev.size() <= q) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        c->gev.push_back(e);
+    }
+    if (begin) {
+        if ((int)c->gwhich.size() <= q / 2) c->gwhich.resize(q / 2 + 1);
+        c->gwhich[q / 2] = which;
+    }
+    cudaEventRecordWithFlags(c->gev[q], st, cudaEventRecordExternal);
+}
+
 struct Timer {
     daeti_ctx* c;
     cudaStream_t st;
     bool on;
     int which;
     Timer(daeti_ctx* c_, cudaStream_t st_, bool on_, int which_) : c(c_), st(st_), on(on_), which(which_) {
-        if (on) cudaEventRecord(c->ev[0], st);
+        if (!on) return;
+        if (c->gcap) gmark(c, st, which, true);
+        else cudaEventRecord(c->ev[0], st);
     }
     ~Timer() {
         if (!on) return;
+        if (c->gcap) {
+            gmark(c, st, which, false);
+            return;
+        }
         cudaEventRecord(c->ev[1], st);
         cudaEventSynchronize(c->ev[1]);
         float ms = 0.f;
@@ -183,15 +211,26 @@ void enqueue_step(daeti_ctx* c, StepRef ref, cudaStream_t st, bool timed, bool q
 
 // Capture graph_steps steps from the current list parity (quiet: for
 // segments in which no stimulus window is open).
+// A profiling graph (c->prof == 2) brackets every launch with event-record
+// nodes and launches without programmatic dependent launch.
 int capture_graph(daeti_ctx* c, cudaGraphExec_t* out, bool quiet) {
     const int G = c->graph_steps;
     const int par0 = c->par;
+    const bool profiling = c->prof == 2;
+    const int pdl0 = c->rtune.pdl;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    if (profiling) {
+        c->gcap = true;
+        c->gnext = 0;
+        c->rtune.pdl = 0;
+    }
     for (int j = 0; j < G; ++j)
-        enqueue_step(c, StepRef{c->s.step_ctr, (long long)j}, c->cap_stream, false, quiet);
+        enqueue_step(c, StepRef{c->s.step_ctr, (long long)j}, c->cap_stream, profiling, quiet);
     launch_tick(c->s.step_ctr, G, c->cap_stream);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->gcap = false;
+    c->rtune.pdl = pdl0;
     c->par = par0;   // capture only recorded the launches
     if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -206,16 +245,28 @@ int capture_graph(daeti_ctx* c, cudaGraphExec_t* out, bool quiet) {
 // Replay whole graphs while at least `reserve` + graph_steps steps remain.
 int replay_graphs(daeti_ctx* c, int64_t& remaining, int64_t reserve, cudaStream_t st) {
     const int G = c->graph_steps;
-    if (c->prof || G <= 0 || remaining - reserve < G) return DAETI_OK;
+    if (c->prof == 1 || G <= 0 || remaining - reserve < G) return DAETI_OK;
+    const bool profiling = c->prof == 2;
+    cudaGraphExec_t* table = profiling ? c->pgraphs : c->graphs;
     launch_set_counter(c->s.step_ctr, c->nstep, st);
     while (remaining - reserve >= G) {
         const bool quiet = !stimulus_in_steps(c->stim_dev.data(), (int)c->stim_dev.size(), c->dt_eff, c->nstep, G);
         const int key = (c->cur * 2 + c->par) * 2 + (quiet ? 1 : 0);
-        if (!c->graphs[key]) {
-            int rc = capture_graph(c, &c->graphs[key], quiet);
+        if (!table[key]) {
+            int rc = capture_graph(c, &table[key], quiet);
             if (rc) return rc;
         }
-        CK(cudaGraphLaunch(c->graphs[key], st));
+        CK(cudaGraphLaunch(table[key], st));
+        if (profiling) {
+            // the graph's events hold this replay's times until the next replay
+            CK(cudaStreamSynchronize(st));
+            for (size_t p = 0; p < c->gwhich.size() && 2 * p + 1 < c->gev.size(); ++p) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->gev[2 * p], c->gev[2 * p + 1]));
+                c->ktime[c->gwhich[p]] += ms;
+                c->klaunch[c->gwhich[p]] += 1;
+            }
+        }
         c->nstep += G;
         remaining -= G;
     }
@@ -284,6 +335,7 @@ int daeti_destroy(daeti_ctx* c) {
     free_device(c);
     for (int i = 0; i < 4; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -947,7 +999,7 @@ int daeti_advance(daeti_ctx* c, double t_end) {
     int64_t remaining = target - c->nstep;
     if (remaining == 0) return DAETI_OK;
     cudaStream_t st = c->stream;
-    const bool timed = c->prof;
+    const bool timed = c->prof != 0;   // plain steps outside whole graphs are timed in both modes
     int rc;
     while (remaining > 0) {
         if ((rc = replay_graphs(c, remaining, 0, st))) return rc;
@@ -1141,7 +1193,10 @@ int daeti_get_substeps(daeti_ctx* c, int64_t* total) {
 
 int daeti_set_profiling(daeti_ctx* c, int enable) {
     if (!c) return DAETI_EINVAL;
-    c->prof = enable != 0;
+    if (enable < 0 || enable > 2) return fail(c, DAETI_EINVAL, "profiling mode is 0, 1 or 2");
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    c->prof = enable;
     for (int i = 0; i < 3; ++i) {
         c->ktime[i] = 0.0;
         c->klaunch[i] = 0;

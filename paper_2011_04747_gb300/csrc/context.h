@@ -68,8 +68,14 @@ struct daeti_ctx {
     // graphs of graph_steps steps, keyed by (start V buffer, list parity,
     // stimulus-free segment)
     cudaGraphExec_t graphs[8] = {};
-    // profiling
-    bool prof = false;
+    // profiling: 1 = events around plain launches; 2 = event-record nodes
+    // around every launch inside captured graphs (graph_steps > 0)
+    int prof = 0;
+    bool gcap = false;                  // capturing a profiling graph
+    int gnext = 0;                      // next event of the capture
+    std::vector<cudaEvent_t> gev;       // begin/end event of each launch of a profiling graph
+    std::vector<int> gwhich;            // kernel class of each begin/end pair
+    cudaGraphExec_t pgraphs[8] = {};    // profiling graphs, keyed like graphs
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double ktime[3] = {0, 0, 0};
     int64_t klaunch[3] = {0, 0, 0};
