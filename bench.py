@@ -284,6 +284,31 @@ class Env:
         return self.max_over_ranks(sum(times) / len(times))
 
 
+ROOF_OPS = 450.0   # counted arithmetic operations per TP06 node sub-step (daeti_kernel_work)
+
+
+def _launch_samples(s, ck, n_steps, dt, every_ms=10.0, count=20):
+    """Reaction and synchronising-diffusion launch durations (us) at states of
+    one run, by daeti_time_launches, with the run's sub-steps per launch."""
+    s.daeti_load_state(ck)
+    out = []
+    t = every_ms / 2
+    while t < n_steps * dt:
+        s.daeti_advance(t)
+        snap = s.daeti_save_state()
+        sub0 = s.daeti_get_substeps()
+        r_ms = s.daeti_time_launches(0, count)
+        sub = (s.daeti_get_substeps() - sub0) / (2 * count)      # warm-up replay + timed replay
+        s.daeti_load_state(snap)
+        s.daeti_advance(t + dt)                                   # back in the run's bucketing mode
+        d_ms = s.daeti_time_launches(2, count)
+        s.daeti_load_state(snap)
+        out.append({"t_ms": t, "reaction_us": r_ms * 1e3, "sync_diffusion_us": d_ms * 1e3,
+                    "substeps_per_launch": sub})
+        t += every_ms
+    return out
+
+
 def _aligned_max_dv(snaps_a, snaps_b, act_a, act_b, every_ms, after_ms=5.0):
     """max over nodes and snapshots t >= act_a + after_ms of |V_a(t) - V_b(t + act_b - act_a)|
     (V_b linearly interpolated between snapshots; reading R-dV: traces aligned
@@ -502,8 +527,33 @@ def bench_slab(args, env):
         d = dst["diffusion"]
         d["bytes_GBs"] = d["bytes_per_launch"] / (d["avg_us"] * 1e-6) / 1e9
         s32.daeti_set_profiling(0)
-    roof["timing"] = ("CUDA events recorded by graph nodes around each reaction launch of the 500 ms run "
-                      "(graphs of the tuned length, launched without programmatic dependent launch)")
+    roof["event_nodes_frac"] = roof["frac"]
+
+    # Launch durations in graph context: every 10 ms of the run (at 5, 15,
+    # ..., 495 ms), 20 back-to-back launches of the reaction kernel and of the
+    # synchronising diffusion sub-step, each replayed as one graph between two
+    # CUDA events at the run's own state (saved before, restored after; one
+    # step is re-run after a restore so that the bucketing mode is the run's)
+    samples = _launch_samples(s32, ck, n_steps, wl.dt)
+    r_ops = sum(ROOF_OPS * sm["substeps_per_launch"] for sm in samples)
+    r_s = sum(sm["reaction_us"] for sm in samples) * 1e-6
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    roof.update({"achieved": r_ops / r_s / 1e12, "frac": r_ops / r_s / 1e12 / peak,
+                 "avg_launch_us": r_s * 1e6 / len(samples),
+                 "substeps_per_launch": sum(sm["substeps_per_launch"] for sm in samples) / len(samples),
+                 "xu_frac": TP06_XU_PER_SUBSTEP * r_ops / ROOF_OPS / r_s / (SM_COUNT * XU_LANES_PER_SM * mhz * 1e6),
+                 "timing": ("graph replays of 20 back-to-back reaction launches at the run's state every 10 ms "
+                            "(50 samples), CUDA events around each replay on the launching stream; "
+                            "event_nodes_frac: event-record nodes around every launch of the 500 ms run; "
+                            "plain_launch_frac: events around plain launches"),
+                 "samples": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in sm.items()}
+                             for sm in samples[::5]]})
+    bytes_launch = roof["bytes_per_launch"]
+    roof["bytes_frac_of_measured_hbm"] = bytes_launch / (r_s / len(samples)) / 1e9 / _peaks().get("hbm_gbs", 6780.0)
+    d_s = sum(sm["sync_diffusion_us"] for sm in samples) * 1e-6 / len(samples)
+    kt["diffusion"]["graph_replay_avg_us"] = d_s * 1e6
+    kt["reaction"]["graph_replay_avg_us"] = r_s * 1e6 / len(samples)
 
     # e2e through the C ABI with host buffers: the initial state (published
     # values at every node, n_states x n doubles) from pinned host memory
@@ -569,22 +619,32 @@ def bench_slab(args, env):
 
 def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_sample=10):
     """node-steps/s of one single-tissue workload (not the headline)."""
+    from paper_2011_04747_gb300 import autotune
+
     binding = env.binding
     t_end = t_end or wl.t_end
     s = binding.solver_from_workload(wl, precision=precision, graph_steps=args.graph_steps)
     s.daeti_set_stream(env.stream)
+    tune = None
+    if not args.no_autotune:
+        rep = autotune.autotune(s, sim_ms=min(t_end, 20.0), extra_key="|" + name)
+        tune = {k: rep[k] for k in ("cached", "candidates", "rejected", "search_s") if k in rep}
+        s.daeti_set_stream(env.stream)
     st = s.daeti_get_stability()
     ck = s.daeti_save_state()
     sec = env.timed(lambda: s.daeti_advance(t_end), args.steps, args.warmup, reset=lambda: s.daeti_load_state(ck))
     n_steps = int(round(t_end / st["dt"]))
     s.daeti_load_state(ck)
-    s.daeti_set_profiling(True)
-    prof_steps = int(round(min(t_end, 20 * st["dt"]) / st["dt"]))
+    # kernel times inside graphs (event-record nodes around each launch)
+    s.daeti_set_profiling(2)
+    prof_steps = int(round(min(t_end, 100 * st["dt"]) / st["dt"]))
     s.daeti_advance(prof_steps * st["dt"])
+    s.daeti_synchronize()
     ms, nl = s.daeti_get_kernel_time(1)
     b, _ = s.daeti_kernel_work(1)
-    fused = s.daeti_get_tuning()["fuse_diffusion"]
-    s.daeti_set_profiling(False)
+    tuning_used = s.daeti_get_tuning()
+    fused = tuning_used["fuse_diffusion"]
+    s.daeti_set_profiling(0)
     s.close()
     # diffusion sub-steps per diffusion launch (a 2D grid's tiled path applies several per launch);
     # GB/s counts the algorithmic bytes of every sub-step the launch applies
@@ -597,7 +657,8 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
             "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
             "data": "synthetic", "config": {"workload": name, "nodes": wl.n_nodes, "strang_steps": n_steps,
-                                            "l": st["l"], "dt_s_ms": st["dt_s"]},
+                                            "l": st["l"], "dt_s_ms": st["dt_s"], "tuning": tuning_used,
+                                            "autotune": tune},
             "sim_ms_per_wall_s": t_end / sec, "diffusion_launch": diff}
     if env.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline_sample(wl, steps_sample)

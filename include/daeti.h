@@ -318,6 +318,18 @@ int daeti_batch_read_activation(daeti_batch* batch, int tissue, double* out);
 int daeti_set_profiling(daeti_ctx* ctx, int enable);
 int daeti_get_kernel_time(daeti_ctx* ctx, int which, double* total_ms, int64_t* launches);
 
+/* Duration of one launch of a kernel in graph context at the current state:
+ * captures `count` (1..1000) back-to-back launches of the launch the next
+ * step would make (which = 0: the reaction launch, with the fused diffusion
+ * sub-step if enabled; 1: a diffusion sub-step; 2: the synchronising
+ * diffusion sub-step), replays the graph once untimed and once between two
+ * CUDA events on the context's stream, and returns the elapsed time / count
+ * in *ms_per_launch.  The launches change the state (cells integrated, V
+ * diffused, bucket lists appended past their step): save the state before
+ * and load it after (daeti_save_state / daeti_load_state).  Waits for the
+ * replays.  Errors: EINVAL, ESTATE, ECUDA. */
+int daeti_time_launches(daeti_ctx* ctx, int which, int count, double* ms_per_launch);
+
 /* Algorithmic bytes of one launch of kernel `which` at the current problem
  * and its arithmetic operations: for which = 1 (diffusion) per launch, for
  * which = 0 (reaction) per node sub-step (multiply by daeti_get_substeps per

@@ -113,6 +113,7 @@ _SIGNATURES = {
     "daeti_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(daeti_tuning)]),
     "daeti_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(daeti_tuning)]),
     "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "daeti_time_launches": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
     "daeti_update_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
@@ -408,6 +409,12 @@ class Solver:
             setattr(t, f, int(cur[f]))
         self._check(self.lib.daeti_set_tuning(self.ctx, ctypes.byref(t)))
         return self.daeti_get_tuning()
+
+    def daeti_time_launches(self, which, count=20):
+        """ms per launch of `count` back-to-back launches in a graph (changes the state)."""
+        ms = ctypes.c_double()
+        self._check(self.lib.daeti_time_launches(self.ctx, int(which), int(count), ctypes.byref(ms)))
+        return ms.value
 
     def daeti_set_profiling(self, enable=True):
         """True/1: events around plain launches; 2: event-record nodes inside graphs; False/0: off."""

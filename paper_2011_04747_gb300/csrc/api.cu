@@ -1204,6 +1204,40 @@ int daeti_set_profiling(daeti_ctx* c, int enable) {
     return DAETI_OK;
 }
 
+int daeti_time_launches(daeti_ctx* c, int which, int count, double* ms_per_launch) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (which < 0 || which > 2 || count < 1 || count > 1000 || !ms_per_launch)
+        return fail(c, DAETI_EINVAL, "which must be 0, 1 or 2 and count in 1..1000");
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    const bool quiet = !stimulus_in_steps(c->stim_dev.data(), (int)c->stim_dev.size(), c->dt_eff, c->nstep, 1);
+    const StepRef ref = plain_ref(c->nstep);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < count; ++q) {
+        if (which == 0) L_react(c, ref, c->cur, c->fused, c->cap_stream, false, quiet);
+        else L_diff(c, ref, c->cur, which == 2, c->cap_stream, false);
+    }
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    float ms = 0.f;
+    e = cudaGraphLaunch(ge, c->stream);   // warm-up replay
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], c->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev[3], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return fail(c, DAETI_ECUDA, std::string("timing replay: ") + cudaGetErrorString(e));
+    *ms_per_launch = (double)ms / count;
+    return DAETI_OK;
+}
+
 int daeti_get_kernel_time(daeti_ctx* c, int which, double* total_ms, int64_t* launches) {
     if (!c || which < 0 || which > 2) return DAETI_EINVAL;
     if (total_ms) *total_ms = c->ktime[which];

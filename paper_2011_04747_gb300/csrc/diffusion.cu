@@ -44,72 +44,151 @@ __global__ void __launch_bounds__(256) substep_kernel(OpView<R> op, int n, const
     if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, valid);
 }
 
-// Structured grids: a block owns a TX x TY tile in x-y and marches through a
-// run of z planes, keeping three planes of V (tile plus a one-node halo) in
-// shared memory; the 27 (9) neighbours then come from shared memory and every
-// V value is read from global memory about once per plane it feeds.
+// 2D structured grids, shared-memory tiles: a block owns a TX x TY tile with
+// a one-node halo in shared memory; the 9 neighbours come from there.
 constexpr int TX = 32, TY = 8;
 
-template <typename R, int DIM, bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(TX * TY) tiled_substep_kernel(OpView<R> op, int n, int zrun,
-                                                               const R* __restrict__ vin, R* vout,
-                                                               const float* cin, float* cout, SyncParams<R> sp) {
+template <typename R, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(TX * TY) tiled2d_substep_kernel(OpView<R> op, int n, const R* __restrict__ vin,
+                                                                 R* vout, const float* cin, float* cout,
+                                                                 SyncParams<R> sp) {
     pdl_wait();
     pdl_trigger();
     constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;
-    constexpr int NP = DIM == 3 ? 3 : 1;
-    __shared__ R buf[NP][PLANE];
+    __shared__ R buf[PLANE];
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int nx = op.nx, ny = op.ny, nz = op.nz;
-    const int z_begin = DIM == 3 ? blockIdx.z * zrun : 0;
-    const int z_end = DIM == 3 ? min(nz, z_begin + zrun) : 1;
-    const int nxy = nx * ny;
-
-    auto load_plane = [&](int z) {
-        R* dst = buf[DIM == 3 ? (z % 3) : 0];
-        for (int q = threadIdx.x; q < PLANE; q += TX * TY) {
-            const int lx = q % PX, ly = q / PX;
-            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && z >= 0 && z < nz;
-            dst[q] = in ? vin[gx + nx * gy + nxy * z] : (R)0;
-        }
-    };
-    if (DIM == 3) {
-        if (z_begin - 1 >= 0) load_plane(z_begin - 1);
-        load_plane(z_begin);
+    const int nx = op.nx, ny = op.ny;
+    for (int q = threadIdx.x; q < PLANE; q += TX * TY) {
+        const int gx = x0 + q % PX - 1, gy = y0 + q / PX - 1;
+        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        buf[q] = in ? vin[gx + nx * gy] : (R)0;
     }
+    __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
     const bool col_in = gx < nx && gy < ny;
+    int k = 1, i = 0;
+    if (col_in) {
+        const int cx = gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1);
+        const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
+        const int li = (ty + 1) * PX + (tx + 1);
+        i = gx + nx * gy;
+        const R* crow = op.coef + ((size_t)cy * 3 + cx) * DAETI_ROW;
+        auto fetch = [&](int dx, int dy, int) { return buf[li + dx + dy * PX]; };
+        R v;
+        float cc;
+        stencil_update<R, 2, KAHAN>(crow, cx, cy, 0, 1, buf[li], KAHAN ? cin[i] : 0.f, fetch, v, cc);
+        vout[i] = v;
+        if (KAHAN) cout[i] = cc;
+        if (SYNC) k = sync_node<R, false>(sp, i, v);
+    }
+    if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
+}
+
+// ---------------------------------------------------------------- 3D z-march
+// 3D structured grids with ghost-padded V buffers and the per-class table:
+// a block owns a ZX x ZY column of nodes and marches through a run of z
+// planes.  V planes (tile plus a one-node halo) and the Kahan terms are
+// copied into a ring of ZS shared-memory slots by cp.async, ZD planes ahead
+// of the plane being computed, so each block keeps several KB of loads in
+// flight; every thread keeps the 3 x 3 neighbourhoods of planes z-1, z and
+// z+1 in registers and reads only the new plane's 9 values per step.  The
+// terms are added in the table's order, as in stencil_update everywhere, so
+// the results equal the one-thread-per-node kernel's bit for bit.
+constexpr int ZX = 32, ZY = 8, ZD = 6, ZS = ZD + 1;
+
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename R, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(ZX * ZY) zmarch_substep_kernel(OpView<R> op, int n, int zrun,
+                                                                const R* __restrict__ vin, R* vout,
+                                                                const float* __restrict__ cin, float* cout,
+                                                                SyncParams<R> sp) {
+    constexpr int PX = ZX + 2, PY = ZY + 2, PLANE = PX * PY, NT = ZX * ZY;
+    __shared__ R vbuf[ZS][PLANE];
+    __shared__ float cbuf[KAHAN ? ZS : 1][NT];
+    pdl_wait();
+    pdl_trigger();
+    const int tid = threadIdx.x;
+    const int tx = tid % ZX, ty = tid / ZX;
+    const int x0 = blockIdx.x * ZX, y0 = blockIdx.y * ZY;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const long long nxy = (long long)nx * ny;
+    const int z0 = blockIdx.z * zrun;
+    const int z1 = min(nz, z0 + zrun);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool col_in = gx < nx && gy < ny;
+    // One cp.async group per plane p (z0 - 1 <= p): V of plane p over the tile
+    // and its halo (p <= z1; halo nodes past the far faces are never read by a
+    // node of the grid and are skipped), and the Kahan terms of plane p - 1.
+    // Offsets reach at most one plane, row and node beyond the grid, inside the
+    // buffers' ghost margins.
+    auto issue = [&](int p) {
+        if (p <= z1) {
+            R* dst = vbuf[(p + ZS) % ZS];
+            for (int q = tid; q < PLANE; q += NT) {
+                const int hx = x0 - 1 + q % PX, hy = y0 - 1 + q / PX;
+                if (hx <= nx && hy <= ny) cp_async_elem(dst + q, vin + (hx + (long long)nx * hy + nxy * p));
+            }
+        }
+        if (KAHAN && p - 1 >= z0 && p - 1 < z1 && col_in)
+            cp_async_elem(&cbuf[(p - 1) % ZS][tid], cin + (gx + (long long)nx * gy + nxy * (p - 1)));
+        cp_async_commit();
+    };
+    auto load9 = [&](R* r, int p) {
+        const R* src = vbuf[(p + ZS) % ZS] + ty * PX + tx;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) r[dy * 3 + dx] = src[dy * PX + dx];
+    };
+    for (int p = z0 - 1; p < z0 + ZD; ++p) issue(p);   // ZD + 1 groups: planes z0 - 1 .. z0 + ZD - 1
+    cp_async_wait<ZD - 1>();                          // planes z0 - 1 and z0 have landed
+    __syncthreads();
+    R a[9], b[9], c[9];                               // planes z - 1, z, z + 1
+    load9(a, z0 - 1);
+    load9(b, z0);
+    __syncthreads();                                  // slot of plane z0 - 1 is refilled next
     const int cx = gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1);
     const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
-    const int li = (ty + 1) * PX + (tx + 1);
-    for (int z = z_begin; z < z_end; ++z) {
-        if (DIM == 3) {
-            if (z + 1 < nz) load_plane(z + 1);
-        } else {
-            load_plane(0);
-        }
+    for (int z = z0; z < z1; ++z) {
+        issue(z + ZD);
+        cp_async_wait<ZD - 1>();                      // plane z + 1 and the Kahan terms of plane z
         __syncthreads();
-        int k = 1;
-        int i = 0;
+        load9(c, z + 1);
+        int k = 1, i = 0;
         if (col_in) {
-            i = gx + nx * gy + nxy * z;
+            i = (int)(gx + (long long)nx * gy + nxy * z);
             const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             auto fetch = [&](int dx, int dy, int dz) {
-                return buf[DIM == 3 ? ((z + dz + 3) % 3) : 0][li + dx + dy * PX];
+                const int j = (dy + 1) * 3 + (dx + 1);
+                return dz < 0 ? a[j] : (dz == 0 ? b[j] : c[j]);
             };
             R v;
             float cc;
-            stencil_update<R, DIM, KAHAN>(crow, cx, cy, z, nz, buf[DIM == 3 ? (z % 3) : 0][li],
-                                          KAHAN ? cin[i] : 0.f, fetch, v, cc);
+            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, b[4], KAHAN ? cbuf[z % ZS][tid] : 0.f, fetch, v, cc);
             vout[i] = v;
             if (KAHAN) cout[i] = cc;
             if (SYNC) k = sync_node<R, false>(sp, i, v);
         }
         if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
-        __syncthreads();   // the plane z - 1 buffer is refilled next
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            a[j] = b[j];
+            b[j] = c[j];
+        }
     }
+    cp_async_wait<0>();
 }
 
 template <typename R>
@@ -151,39 +230,68 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl
                   cout, sp);
 }
 
-template <typename R, int DIM, bool KAHAN>
+// Resident blocks per SM of a kernel at `threads` threads, and the SM count
+// (queried once per kernel instance; 4 and 152 if a query fails).
+template <typename K>
+static int resident_blocks(K kern, int threads) {
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        cached = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0) == cudaSuccess && nb > 0 ? nb : 4;
+    }
+    return cached;
+}
+static int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cached = cudaGetDevice(&dev) == cudaSuccess &&
+                         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
+                     ? v
+                     : 152;
+    }
+    return cached;
+}
+
+// Shared-memory launch shapes of structured grids (diff_block = 0): 2D tiles,
+// or the 3D z-march with the z range split into runs so that the blocks fill
+// the GPU's resident slots about once.
+template <typename R, bool KAHAN>
 static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
                          const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
-    const int gx = (dop.nx + TX - 1) / TX, gy = (dop.ny + TY - 1) / TY;
-    int zrun = 1, gz = 1;
-    if (DIM == 3) {
-        // enough blocks to fill the GPU (about 8 per SM), long z runs otherwise
-        const long tiles = (long)gx * gy;
-        zrun = (int)std::max<long>(1, std::min<long>(dop.nz, (tiles * dop.nz + 1215) / 1216));
-        gz = (dop.nz + zrun - 1) / zrun;
+    if (dop.dim == 2) {
+        const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
+        if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
+        else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
+        return;
     }
-    const dim3 grid(gx, gy, gz);
+    const long tiles = (long)((dop.nx + ZX - 1) / ZX) * ((dop.ny + ZY - 1) / ZY);
+    const int nb = sync ? resident_blocks(zmarch_substep_kernel<R, KAHAN, true>, ZX * ZY)
+                        : resident_blocks(zmarch_substep_kernel<R, KAHAN, false>, ZX * ZY);
+    const long slots = (long)sm_count() * nb;
+    const int nsplit = (int)std::max<long>(1, std::min<long>(dop.nz, (slots + tiles / 2) / tiles));
+    const int zrun = (dop.nz + nsplit - 1) / nsplit;
+    const dim3 grid((dop.nx + ZX - 1) / ZX, (dop.ny + ZY - 1) / ZY, (dop.nz + zrun - 1) / zrun);
     if (sync)
-        launch_ex(tiled_substep_kernel<R, DIM, KAHAN, true>, grid, TX * TY, st, pdl, op, n, zrun, vin, vout, cin, cout,
-                  sp);
+        launch_ex(zmarch_substep_kernel<R, KAHAN, true>, grid, ZX * ZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
     else
-        launch_ex(tiled_substep_kernel<R, DIM, KAHAN, false>, grid, TX * TY, st, pdl, op, n, zrun, vin, vout, cin,
-                  cout, sp);
+        launch_ex(zmarch_substep_kernel<R, KAHAN, false>, grid, ZX * ZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
 }
 
 template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
                        StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
-    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate)) {
-        // structured grid, shared-memory tiles
+    const bool padded = s.vpad >= stencil_reach(dop);
+    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
+        // structured grid, shared-memory tiles (3D: the z-march, which reads
+        // the ghost margins of padded V buffers)
         const OpView<R> op = op_view<R>(dop);
         const R* vin = (const R*)s.V[src];
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        if (dop.dim == 2) tiled_launch<R, 2, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
-        else tiled_launch<R, 3, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
         return;
     }
     if (block <= 0) block = 256;

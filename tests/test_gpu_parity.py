@@ -303,11 +303,12 @@ def test_full_slab_bench_config_first_steps(precision):
     _compare(wl, 30, 10, precision)
 
 
-@pytest.mark.parametrize("wl_name", ["slab", "sheet2d", "sheet_l3", "sheet_l4", "hetero_slab"])
+@pytest.mark.parametrize("wl_name", ["slab", "slab_wide", "sheet2d", "sheet_l3", "sheet_l4", "hetero_slab"])
 def test_launch_shapes_do_not_change_results(wl_name):
     """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
-    programmatic dependent launch or plain launches, and graphs give
-    bit-identical states (l = 1, 3 and 4)."""
+    programmatic dependent launch or plain launches, graphs, and the
+    shared-memory diffusion kernels (diff_block = 0: 2D tiles, 3D z-march)
+    give bit-identical states (l = 1, 3 and 4)."""
     from parity_util import ensure_lib
 
     binding = ensure_lib()
@@ -315,6 +316,7 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 "sheet2d": (I.aniso_sheet_2d(n=41, length=1.0, model="tp06"), {}),
                 "sheet_l3": (I.aniso_sheet_2d(n=37, length=0.36, model="tp06"), {}),
                 "sheet_l4": (I.aniso_sheet_2d(n=45, length=0.44, model="tp06"), dict(l_rounding="ceil")),
+                "slab_wide": (I.tp06_slab_3d(45, 21, 7, t_end=12), {}),
                 "hetero_slab": (_heterogeneous(I.tp06_slab_3d(23, 19, 9, t_end=12)), {})}[wl_name]
     variants = [dict(),
                 dict(fuse_diffusion=0),
@@ -324,7 +326,10 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 dict(pdl=0, react_block=64, graph_steps=0),
                 dict(bucket_k=0, graph_steps=0),
                 dict(graph_steps=6, diff_block=128),
-                dict(diff_block=256, fuse_diffusion=0, graph_steps=0)]
+                dict(diff_block=256, fuse_diffusion=0, graph_steps=0),
+                dict(diff_block=0),
+                dict(diff_block=0, fuse_diffusion=0, graph_steps=0),
+                dict(diff_block=0, bucket_k=0, pdl=0)]
     ref = None
     for prec in ("fp32_kahan", "fp64"):
         ref = None
