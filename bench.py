@@ -794,15 +794,19 @@ def run_ours(args):
 
 
 def profile_run(args):
-    """A short plain run of the headline workload for external profilers."""
+    """A short plain run of the slab workload (101 x 101 x 26, or 401 x 401 x 26
+    with --workload slab_l) for external profilers."""
     import inputs
     from paper_2011_04747_gb300 import binding, build as _build
 
     if not os.path.exists(binding.LIB_PATH):
         _build.build()
-    wl = inputs.tp06_slab_3d(**SLAB, t_end=T_END)
+    wl = inputs.tp06_slab_3d(401, 401, 26, t_end=T_END) if args.workload == "slab_l" else \
+        inputs.tp06_slab_3d(**SLAB, t_end=T_END)
     s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=args.graph_steps,
                                      bucket_k=bool(args.bucket))
+    if args.diff_block >= 0:
+        s.daeti_set_tuning(diff_block=args.diff_block)
     if args.profile_from > 0:
         s.daeti_advance(args.profile_from)
     s.daeti_advance(args.profile_from + args.profile_run)
@@ -826,6 +830,9 @@ def main():
     ap.add_argument("--bucket", type=int, default=1, help="group nodes by k before step A (1) or not (0)")
     ap.add_argument("--profile-run", type=float, default=0.0,
                     help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
+    ap.add_argument("--diff-block", type=int, default=-1,
+                    help="with --profile-run: diffusion launch shape (0 = shared-memory z-march, 256 = one "
+                         "thread per node; default: the library's)")
     ap.add_argument("--profile-from", type=float, default=0.0,
                     help="with --profile-run: first advance to this time (ms), e.g. into the plateau "
                          "(60) or the resting phase (150)")

@@ -18,6 +18,7 @@
 // last sub-step of each step I is fused into the reaction launch
 // (reaction.cu).
 #include <algorithm>
+#include <type_traits>
 
 #include "diffops.cuh"
 
@@ -230,6 +231,168 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl
                   cout, sp);
 }
 
+// ------------------------------------------------- 3D z-march, node pairs
+// The float z-march with two x-adjacent nodes per thread in the packed FP32
+// instructions (fma/sub/add.rn.f32x2: each lane rounds exactly as the scalar
+// instruction).  A block owns 32 x 8 nodes (16 x 8 threads); a thread reads
+// its pair's 4 x 3 neighbourhood of each new plane with six 8-byte shared
+// loads and multiplies by rows of the negated pair table (two coefficients
+// per 16-byte load).  Accumulating -sum a_ij (V_j - V_i) with negated
+// coefficients from -0 gives exactly the negation of the scalar sum, so the
+// results equal the one-thread-per-node kernel's.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+constexpr int PZX = 32, PZT = PZX / 2, PZY = 8;
+
+template <bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(PZT * PZY) zpair_substep_kernel(OpView<float> op, const float* __restrict__ pair,
+                                                                 int n, int zrun, const float* __restrict__ vin,
+                                                                 float* vout, const float* __restrict__ cin,
+                                                                 float* cout, SyncParams<float> sp) {
+    constexpr int PX = PZX + 2, PY = PZY + 2, PLANE = PX * PY, NT = PZT * PZY;
+    __shared__ __align__(16) float vbuf[ZS][PLANE];
+    __shared__ __align__(16) float cbuf[KAHAN ? ZS : 1][2 * NT];
+    pdl_wait();
+    pdl_trigger();
+    const int tid = threadIdx.x;
+    const int tx = tid % PZT, ty = tid / PZT;
+    const int x0 = blockIdx.x * PZX, y0 = blockIdx.y * PZY;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const long long nxy = (long long)nx * ny;
+    const int z0 = blockIdx.z * zrun;
+    const int z1 = min(nz, z0 + zrun);
+    const int xa = x0 + 2 * tx, gy = y0 + ty;
+    const bool va = xa < nx && gy < ny, vb = xa + 1 < nx && gy < ny;
+    // cp.async group of plane p: V of plane p over the tile and its halo
+    // (p <= z1; halo nodes past the far faces are skipped), and the Kahan
+    // terms of plane p - 1; offsets stay inside the V buffers' ghost margins
+    auto issue = [&](int p) {
+        if (p <= z1) {
+            float* dst = vbuf[(p + ZS) % ZS];
+            for (int q = tid; q < PLANE; q += NT) {
+                const int hx = x0 - 1 + q % PX, hy = y0 - 1 + q / PX;
+                if (hx <= nx && hy <= ny) cp_async_elem(dst + q, vin + (hx + (long long)nx * hy + nxy * p));
+            }
+        }
+        if (KAHAN && p - 1 >= z0 && p - 1 < z1) {
+            const long long i = xa + (long long)nx * gy + nxy * (p - 1);
+            float* dst = &cbuf[(p - 1) % ZS][2 * tid];
+            if (va) cp_async_elem(dst, cin + i);
+            if (vb) cp_async_elem(dst + 1, cin + i + 1);
+        }
+        cp_async_commit();
+    };
+    // the pair's neighbourhood of plane p: w[r][0] = (x-1, x), w[r][1] =
+    // (x, x+1), w[r][2] = (x+1, x+2) for rows y-1, y, y+1 (x = xa)
+    auto load = [&](f32x2 (*w)[3], int p) {
+        const float* src = vbuf[(p + ZS) % ZS] + ty * PX + 2 * tx;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const f32x2 lft = *reinterpret_cast<const f32x2*>(src + r * PX);
+            const f32x2 rgt = *reinterpret_cast<const f32x2*>(src + r * PX + 2);
+            w[r][0] = lft;
+            w[r][1] = pk2(hi2(lft), lo2(rgt));
+            w[r][2] = rgt;
+        }
+    };
+    for (int p = z0 - 1; p < z0 + ZD; ++p) issue(p);
+    cp_async_wait<ZD - 1>();
+    __syncthreads();
+    f32x2 a[3][3], b[3][3], c[3][3];   // planes z - 1, z, z + 1
+    load(a, z0 - 1);
+    load(b, z0);
+    __syncthreads();
+    const int cxa = xa == 0 ? 0 : (xa == nx - 1 ? 2 : 1);
+    const int cxb = xa + 1 >= nx ? 2 : (xa + 1 == nx - 1 ? 2 : 1);
+    const int ptype = cxa == 0 ? (cxb == 1 ? 0 : 4) : (cxa == 1 ? (cxb == 1 ? 1 : 2) : 3);
+    const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
+    for (int z = z0; z < z1; ++z) {
+        issue(z + ZD);
+        cp_async_wait<ZD - 1>();
+        __syncthreads();
+        load(c, z + 1);
+        const float4* crow = reinterpret_cast<const float4*>(pair + ((size_t)((z * 3 + cy) * 5 + ptype)) * (2 * DAETI_ROW));
+        const f32x2 vi = b[1][1];
+        f32x2 nacc = pk2(-0.f, -0.f);
+#pragma unroll
+        for (int q = 0; q < DAETI_ROW / 2; ++q) {
+            const float4 cc = __ldg(crow + q);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * q + h;
+                if (j == 13 || j >= 27) continue;
+                const int dz = j / 9 - 1, dy = (j / 3) % 3 - 1, dx = j % 3 - 1;
+                const f32x2 xj = dz < 0 ? a[dy + 1][dx + 1] : (dz == 0 ? b[dy + 1][dx + 1] : c[dy + 1][dx + 1]);
+                nacc = fma2(h ? pk2(cc.z, cc.w) : pk2(cc.x, cc.y), sub2(xj, vi), nacc);
+            }
+        }
+        f32x2 v, cn = 0ull;
+        if (KAHAN) {
+            const f32x2 c0 = *reinterpret_cast<const f32x2*>(&cbuf[z % ZS][2 * tid]);
+            const f32x2 y = sub2(nacc, c0);
+            const f32x2 t = add2(vi, y);
+            cn = sub2(sub2(t, vi), y);
+            v = t;
+        } else {
+            v = add2(vi, nacc);
+        }
+        const long long ia = xa + (long long)nx * gy + nxy * z;
+        int ka = 1, kb = 1;
+        if (va) {
+            vout[ia] = lo2(v);
+            if (KAHAN) cout[ia] = lo2(cn);
+            if (SYNC) ka = sync_node<float, false>(sp, (int)ia, lo2(v));
+        }
+        if (vb) {
+            vout[ia + 1] = hi2(v);
+            if (KAHAN) cout[ia + 1] = hi2(cn);
+            if (SYNC) kb = sync_node<float, false>(sp, (int)ia + 1, hi2(v));
+        }
+        if (SYNC && sp.counts) {
+            bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, (int)ia, ka, va);
+            bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, (int)ia + 1, kb, vb);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                a[r][d] = b[r][d];
+                b[r][d] = c[r][d];
+            }
+    }
+    cp_async_wait<0>();
+}
+
 // Resident blocks per SM of a kernel at `threads` threads, and the SM count
 // (queried once per kernel instance; 4 and 152 if a query fails).
 template <typename K>
@@ -264,6 +427,24 @@ static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& 
         if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         return;
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        if (dop.pair) {
+            const long tiles = (long)((dop.nx + PZX - 1) / PZX) * ((dop.ny + PZY - 1) / PZY);
+            const int nb = sync ? resident_blocks(zpair_substep_kernel<KAHAN, true>, PZT * PZY)
+                                : resident_blocks(zpair_substep_kernel<KAHAN, false>, PZT * PZY);
+            const long slots = (long)sm_count() * nb;
+            const int nsplit = (int)std::max<long>(1, std::min<long>(dop.nz, (slots + tiles / 2) / tiles));
+            const int zrun = (dop.nz + nsplit - 1) / nsplit;
+            const dim3 grid((dop.nx + PZX - 1) / PZX, (dop.ny + PZY - 1) / PZY, (dop.nz + zrun - 1) / zrun);
+            if (sync)
+                launch_ex(zpair_substep_kernel<KAHAN, true>, grid, PZT * PZY, st, pdl, op, (const float*)dop.pair, n,
+                          zrun, vin, vout, cin, cout, sp);
+            else
+                launch_ex(zpair_substep_kernel<KAHAN, false>, grid, PZT * PZY, st, pdl, op, (const float*)dop.pair,
+                          n, zrun, vin, vout, cin, cout, sp);
+            return;
+        }
     }
     const long tiles = (long)((dop.nx + ZX - 1) / ZX) * ((dop.ny + ZY - 1) / ZY);
     const int nb = sync ? resident_blocks(zmarch_substep_kernel<R, KAHAN, true>, ZX * ZY)

@@ -61,6 +61,11 @@ struct DiffOp {
     void* coef = nullptr;    // table: [nz*9][28] off-diagonal dt_ad K_ij / m_i (centre entry and pad 0)
     uint16_t* cls = nullptr; // table row of each node (nullable)
     int per_node = 0;        // 1: coef holds one row per node (row i for node i), cls unused
+    // float tables only: rows of negated coefficients of two x-adjacent
+    // nodes interleaved, [nz*3 (z, y class)][5 pair types][28 pairs]
+    // (pair types by the x classes of (x, x+1), x even: (0,1) (1,1) (1,2)
+    // (2,-) (0,2)); read by the paired z-march diffusion kernel
+    float* pair = nullptr;
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
     int64_t* chunk_ptr = nullptr;   // start of chunk c in val/col
