@@ -237,7 +237,10 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
  * react_min_blocks: 6, 8 or 10 resident reaction blocks per SM the register
  * budget must allow (TP06 in float); diff_block: threads per block of the
  * one-thread-per-node diffusion kernel (32..256, multiple of 32; default
- * 256), or 0 for the shared-memory tiled kernel on structured grids;
+ * 256); 0: shared-memory kernels on structured grids (2D tiles; 3D z-march
+ * over planes staged by cp.async, two nodes per thread in float); 1: on 3D
+ * structured grids, a register z-march (one thread per (x, y) column over a
+ * run of planes; other meshes take 256);
  * fuse_diffusion: run the last diffusion sub-step of step I inside the
  * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
  * steps per captured CUDA graph (rounded up to even, 0 = plain launches);

@@ -1311,7 +1311,7 @@ int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
 int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
     if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block < 0 ||
-        t->diff_block > 256 || t->diff_block % 32 || t->graph_steps < 0 ||
+        t->diff_block > 256 || (t->diff_block > 1 && t->diff_block % 32) || t->graph_steps < 0 ||
         (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1))
         return fail(c, DAETI_EINVAL, "bad tuning values");
     int rc = daeti_synchronize(c);

@@ -393,6 +393,93 @@ __global__ void __launch_bounds__(PZT * PZY) zpair_substep_kernel(OpView<float> 
     cp_async_wait<0>();
 }
 
+// ------------------------------------------------- 3D register z-march
+// 3D structured grids with ghost-padded V buffers and the per-class table,
+// one thread per (x, y) column over a run of z planes and no barriers (but
+// the synchronisation's bucketing): a thread keeps the 3 x 3 neighbourhoods
+// of planes z - 1, z and z + 1 in registers and loads only the 9 values of
+// the new plane per node (instead of 26 neighbours); the loop is unrolled by
+// three so the planes change roles instead of being copied.  Same
+// stencil_update, same term order: results equal the one-thread-per-node
+// kernel's.
+constexpr int RZX = 32, RZY = 8;
+
+template <typename R, bool KAHAN, bool SYNC>
+struct ZColumn {
+    const OpView<R>& op;
+    const R* base;        // V of this column at plane 0 (a column of the grid; column 0 off the grid)
+    long long nxy;
+    int nx, cx, cy, i0;   // i0: node index of the column at plane 0
+    bool col_in;
+    R* vout;
+    const float* cin;
+    float* cout;
+    const SyncParams<R>& sp;
+
+    __device__ __forceinline__ void load(R (&r)[9], int p) const {
+        const R* q = base + nxy * p;
+        r[0] = q[-nx - 1];
+        r[1] = q[-nx];
+        r[2] = q[-nx + 1];
+        r[3] = q[-1];
+        r[4] = q[0];
+        r[5] = q[1];
+        r[6] = q[nx - 1];
+        r[7] = q[nx];
+        r[8] = q[nx + 1];
+    }
+    // node at plane z from planes z - 1 (A), z (B), z + 1 (C, loaded here)
+    __device__ __forceinline__ void step(const R (&A)[9], const R (&B)[9], R (&C)[9], int z) const {
+        load(C, z + 1);
+        int k = 1;
+        const int i = i0 + (int)(nxy * z);
+        if (col_in) {
+            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
+            auto fetch = [&](int dx, int dy, int dz) {
+                const int j = (dy + 1) * 3 + (dx + 1);
+                return dz < 0 ? A[j] : (dz == 0 ? B[j] : C[j]);
+            };
+            R v;
+            float cc;
+            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, B[4], KAHAN ? cin[i] : 0.f, fetch, v, cc);
+            vout[i] = v;
+            if (KAHAN) cout[i] = cc;
+            if (SYNC) k = sync_node<R, false>(sp, i, v);
+        }
+        if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
+    }
+};
+
+template <typename R, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 4 : 2) zreg_substep_kernel(OpView<R> op, int n, int zrun,
+                                                                const R* __restrict__ vin, R* vout,
+                                                                const float* __restrict__ cin, float* cout,
+                                                                SyncParams<R> sp) {
+    pdl_wait();
+    pdl_trigger();
+    const int gx = blockIdx.x * RZX + threadIdx.x % RZX, gy = blockIdx.y * RZY + threadIdx.x / RZX;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const int z0 = blockIdx.z * zrun, z1 = min(nz, z0 + zrun);
+    const bool col_in = gx < nx && gy < ny;
+    // offsets reach one plane, row and node beyond the column, inside the
+    // ghost margins; columns off the grid read column 0 and store nothing
+    const int col = col_in ? gx + nx * gy : 0;
+    const ZColumn<R, KAHAN, SYNC> zc{op, vin + col, (long long)nx * ny, nx,
+                                     gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1), gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1),
+                                     col, col_in, vout, cin, cout, sp};
+    R P0[9], P1[9], P2[9];
+    zc.load(P0, z0 - 1);
+    zc.load(P1, z0);
+    int z = z0;
+    for (; z + 3 <= z1; z += 3) {
+        zc.step(P0, P1, P2, z);
+        zc.step(P1, P2, P0, z + 1);
+        zc.step(P2, P0, P1, z + 2);
+    }
+    if (z < z1) zc.step(P0, P1, P2, z);
+    if (z + 1 < z1) zc.step(P1, P2, P0, z + 1);
+}
+
 // Resident blocks per SM of a kernel at `threads` threads, and the SM count
 // (queried once per kernel instance; 4 and 152 if a query fails).
 template <typename K>
@@ -421,12 +508,43 @@ static int sm_count() {
 // the GPU's resident slots about once.
 template <typename R, bool KAHAN>
 static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
-                         const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
+                         const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp,
+                         bool zreg_shape) {
     if (dop.dim == 2) {
         const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
         if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         return;
+    }
+    {
+        // register z-march (default shared-free shape): columns x run, the
+        // z range split so the grid covers the resident slots about once
+        const long cols = (long)((dop.nx + RZX - 1) / RZX) * ((dop.ny + RZY - 1) / RZY);
+        const int nb = sync ? resident_blocks(zreg_substep_kernel<R, KAHAN, true>, RZX * RZY)
+                            : resident_blocks(zreg_substep_kernel<R, KAHAN, false>, RZX * RZY);
+        const long slots = (long)sm_count() * nb;
+        int best = 1;
+        double best_cost = 1e300;
+        for (int ns = 1; ns <= dop.nz; ++ns) {   // waves x (planes per run + prologue)
+            const int zr = (dop.nz + ns - 1) / ns;
+            const long blocks = cols * ((dop.nz + zr - 1) / zr);
+            const double cost = (double)((blocks + slots - 1) / slots) * (zr + 1.0);
+            if (cost < best_cost - 1e-9) {
+                best_cost = cost;
+                best = ns;
+            }
+        }
+        const int zrun = (dop.nz + best - 1) / best;
+        const dim3 grid((dop.nx + RZX - 1) / RZX, (dop.ny + RZY - 1) / RZY, (dop.nz + zrun - 1) / zrun);
+        if (zreg_shape) {
+            if (sync)
+                launch_ex(zreg_substep_kernel<R, KAHAN, true>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin,
+                          cout, sp);
+            else
+                launch_ex(zreg_substep_kernel<R, KAHAN, false>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin,
+                          cout, sp);
+            return;
+        }
     }
     if constexpr (std::is_same<R, float>::value) {
         if (dop.pair) {
@@ -464,7 +582,8 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
                        StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
     const bool padded = s.vpad >= stencil_reach(dop);
-    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
+    const bool zreg = block == 1 && dop.dim == 3;   // register z-march
+    if (dop.kind == 0 && (block == 0 || zreg) && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
         // structured grid, shared-memory tiles (3D: the z-march, which reads
         // the ghost margins of padded V buffers)
         const OpView<R> op = op_view<R>(dop);
@@ -472,10 +591,10 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zreg);
         return;
     }
-    if (block <= 0) block = 256;
+    if (block <= 1) block = 256;
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
     const OpView<R> op = op_view<R>(dop);
