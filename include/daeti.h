@@ -246,8 +246,10 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
  * steps per captured CUDA graph (rounded up to even, 0 = plain launches);
  * pdl: 1 = launch the per-step kernels with
  * programmatic dependent launch, so each one's blocks are resident when its
- * predecessor ends (default), 0 = plain launches.  set waits for enqueued
- * work and drops captured graphs. */
+ * predecessor ends (default), 0 = plain launches; diff_zrun: z planes per
+ * thread of the register z-march (diff_block = 1), 0 = chosen from the grid
+ * and the GPU's resident slots.  set waits for enqueued work and drops
+ * captured graphs. */
 typedef struct daeti_tuning {
     int32_t struct_size;       /* sizeof(daeti_tuning) */
     int32_t react_block;
@@ -257,6 +259,7 @@ typedef struct daeti_tuning {
     int32_t bucket_k;
     int32_t graph_steps;
     int32_t pdl;
+    int32_t diff_zrun;
 } daeti_tuning;
 int daeti_get_tuning(daeti_ctx* ctx, daeti_tuning* tuning);
 int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);

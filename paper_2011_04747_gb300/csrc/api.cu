@@ -186,7 +186,7 @@ void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bo
 void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
     Timer t(c, st, timed, 1);
     launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st,
-                     c->rtune.pdl != 0);
+                     c->rtune.pdl != 0, c->diff_zrun);
 }
 
 // One Strang step from a synchronisation to the next: step I (l sub-steps,
@@ -1305,6 +1305,7 @@ int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
     t->bucket_k = c->lists ? 1 : 0;
     t->graph_steps = c->graph_steps;
     t->pdl = c->rtune.pdl;
+    t->diff_zrun = c->diff_zrun;
     return DAETI_OK;
 }
 
@@ -1312,7 +1313,7 @@ int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
     if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block < 0 ||
         t->diff_block > 256 || (t->diff_block > 1 && t->diff_block % 32) || t->graph_steps < 0 ||
-        (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1))
+        (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1) || t->diff_zrun < 0)
         return fail(c, DAETI_EINVAL, "bad tuning values");
     int rc = daeti_synchronize(c);
     if (rc) return rc;
@@ -1321,6 +1322,7 @@ int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     c->rtune.min_blocks = t->react_min_blocks;
     c->rtune.pdl = t->pdl;
     c->diff_block = t->diff_block;
+    c->diff_zrun = t->diff_zrun;
     c->fused = t->fuse_diffusion != 0;
     const bool new_lists = t->bucket_k != 0;
     if (new_lists != c->lists && c->prepared) {

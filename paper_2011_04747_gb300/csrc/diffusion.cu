@@ -411,9 +411,9 @@ struct ZColumn {
     long long nxy;
     int nx, cx, cy, i0;   // i0: node index of the column at plane 0
     bool col_in;
-    R* vout;
-    const float* cin;
-    float* cout;
+    R* __restrict__ vout;
+    const float* __restrict__ cin;
+    float* __restrict__ cout;
     const SyncParams<R>& sp;
 
     __device__ __forceinline__ void load(R (&r)[9], int p) const {
@@ -452,9 +452,9 @@ struct ZColumn {
 
 template <typename R, bool KAHAN, bool SYNC>
 __global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 4 : 2) zreg_substep_kernel(OpView<R> op, int n, int zrun,
-                                                                const R* __restrict__ vin, R* vout,
-                                                                const float* __restrict__ cin, float* cout,
-                                                                SyncParams<R> sp) {
+                                                                const R* __restrict__ vin, R* __restrict__ vout,
+                                                                const float* __restrict__ cin,
+                                                                float* __restrict__ cout, SyncParams<R> sp) {
     pdl_wait();
     pdl_trigger();
     const int gx = blockIdx.x * RZX + threadIdx.x % RZX, gy = blockIdx.y * RZY + threadIdx.x / RZX;
@@ -509,7 +509,7 @@ static int sm_count() {
 template <typename R, bool KAHAN>
 static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
                          const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp,
-                         bool zreg_shape) {
+                         bool zreg_shape, int zrun_req) {
     if (dop.dim == 2) {
         const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
         if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
@@ -534,7 +534,7 @@ static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& 
                 best = ns;
             }
         }
-        const int zrun = (dop.nz + best - 1) / best;
+        const int zrun = zrun_req > 0 ? std::min(zrun_req, dop.nz) : (dop.nz + best - 1) / best;
         const dim3 grid((dop.nx + RZX - 1) / RZX, (dop.ny + RZY - 1) / RZY, (dop.nz + zrun - 1) / zrun);
         if (zreg_shape) {
             if (sync)
@@ -579,7 +579,7 @@ static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& 
 
 template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
-                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
+                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int zrun) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
     const bool padded = s.vpad >= stencil_reach(dop);
     const bool zreg = block == 1 && dop.dim == 3;   // register z-march
@@ -591,7 +591,7 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zreg);
+        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zreg, zrun);
         return;
     }
     if (block <= 1) block = 256;
@@ -612,13 +612,13 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
 }
 
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl) {
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int zrun) {
     if (s.prec == P_F64)
-        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
+        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
     else if (s.kahan)
-        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
+        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
     else
-        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl);
+        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
 }
 
 // ---------------------------------------------------------- per-k node lists

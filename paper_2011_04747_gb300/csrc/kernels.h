@@ -140,8 +140,10 @@ void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef s
 // synchronisation epilogue runs on the result (lists of parity `par`).
 // pdl: launch with programmatic dependent launch (the kernels wait for their
 // predecessor before touching memory either way).
+// block: 32..256 one thread per node; 0 shared-memory tiles / z-march; 1 the
+// register z-march on 3D grids, zrun planes per thread (0: automatic).
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false);
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false, int zrun = 0);
 void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st);
 void launch_tick(long long* ctr, long long inc, cudaStream_t st);
 void launch_set_counter(long long* ctr, long long value, cudaStream_t st);
