@@ -397,9 +397,10 @@ __global__ void __launch_bounds__(PZT * PZY) zpair_substep_kernel(OpView<float> 
 // 3D structured grids with ghost-padded V buffers and the per-class table,
 // one thread per (x, y) column over a run of z planes and no barriers (but
 // the synchronisation's bucketing): a thread keeps the 3 x 3 neighbourhoods
-// of planes z - 1, z and z + 1 in registers and loads only the 9 values of
-// the new plane per node (instead of 26 neighbours); the loop is unrolled by
-// three so the planes change roles instead of being copied.  Same
+// of planes z - 1, z, z + 1 and z + 2 in registers and loads only the 9
+// values of one new plane per node (instead of 26 neighbours), two planes
+// ahead; the loop is unrolled by four so the planes change roles instead of
+// being copied.  Same
 // stencil_update, same term order: results equal the one-thread-per-node
 // kernel's.
 constexpr int RZX = 32, RZY = 8;
@@ -428,9 +429,12 @@ struct ZColumn {
         r[7] = q[nx];
         r[8] = q[nx + 1];
     }
-    // node at plane z from planes z - 1 (A), z (B), z + 1 (C, loaded here)
-    __device__ __forceinline__ void step(const R (&A)[9], const R (&B)[9], R (&C)[9], int z) const {
-        load(C, z + 1);
+    // node at plane z from planes z - 1 (A), z (B) and z + 1 (C, loaded a
+    // step earlier); the load of plane z + 2 into D is issued first, so two
+    // planes of loads are in flight while the node is computed
+    __device__ __forceinline__ void step(const R (&A)[9], const R (&B)[9], const R (&C)[9], R (&D)[9], int z,
+                                         int z1) const {
+        if (z + 2 <= z1) load(D, z + 2);
         int k = 1;
         const int i = i0 + (int)(nxy * z);
         if (col_in) {
@@ -451,7 +455,7 @@ struct ZColumn {
 };
 
 template <typename R, bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 4 : 2) zreg_substep_kernel(OpView<R> op, int n, int zrun,
+__global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 3 : 2) zreg_substep_kernel(OpView<R> op, int n, int zrun,
                                                                 const R* __restrict__ vin, R* __restrict__ vout,
                                                                 const float* __restrict__ cin,
                                                                 float* __restrict__ cout, SyncParams<R> sp) {
@@ -467,17 +471,20 @@ __global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 4 : 2) zreg_subste
     const ZColumn<R, KAHAN, SYNC> zc{op, vin + col, (long long)nx * ny, nx,
                                      gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1), gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1),
                                      col, col_in, vout, cin, cout, sp};
-    R P0[9], P1[9], P2[9];
+    R P0[9], P1[9], P2[9], P3[9];
     zc.load(P0, z0 - 1);
     zc.load(P1, z0);
+    zc.load(P2, z0 + 1);
     int z = z0;
-    for (; z + 3 <= z1; z += 3) {
-        zc.step(P0, P1, P2, z);
-        zc.step(P1, P2, P0, z + 1);
-        zc.step(P2, P0, P1, z + 2);
+    for (; z + 4 <= z1; z += 4) {
+        zc.step(P0, P1, P2, P3, z, z1);
+        zc.step(P1, P2, P3, P0, z + 1, z1);
+        zc.step(P2, P3, P0, P1, z + 2, z1);
+        zc.step(P3, P0, P1, P2, z + 3, z1);
     }
-    if (z < z1) zc.step(P0, P1, P2, z);
-    if (z + 1 < z1) zc.step(P1, P2, P0, z + 1);
+    if (z < z1) zc.step(P0, P1, P2, P3, z, z1);
+    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, z1);
+    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, z1);
 }
 
 // Resident blocks per SM of a kernel at `threads` threads, and the SM count
