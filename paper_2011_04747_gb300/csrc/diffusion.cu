@@ -432,8 +432,11 @@ struct ZColumn {
     // node at plane z from planes z - 1 (A), z (B) and z + 1 (C, loaded a
     // step earlier); the load of plane z + 2 into D is issued first, so two
     // planes of loads are in flight while the node is computed
+    // mode: the bucketing mode of this synchronisation (counts[0]); in the
+    // uniform-k mode (< 0) a node whose k differs only sets `differs`, voted
+    // on once per block at the end, instead of a block barrier per plane
     __device__ __forceinline__ void step(const R (&A)[9], const R (&B)[9], const R (&C)[9], R (&D)[9], int z,
-                                         int z1) const {
+                                         int z1, int mode, int& differs) const {
         if (z + 2 <= z1) load(D, z + 2);
         int k = 1;
         const int i = i0 + (int)(nxy * z);
@@ -450,7 +453,10 @@ struct ZColumn {
             if (KAHAN) cout[i] = cc;
             if (SYNC) k = sync_node<R, false>(sp, i, v);
         }
-        if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
+        if (SYNC && sp.counts) {
+            if (mode < 0) differs |= col_in && k != -mode;
+            else block_append(sp.counts, sp.lists, sp.n, i, k, col_in);
+        }
     }
 };
 
@@ -471,20 +477,25 @@ __global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 3 : 2) zreg_subste
     const ZColumn<R, KAHAN, SYNC> zc{op, vin + col, (long long)nx * ny, nx,
                                      gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1), gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1),
                                      col, col_in, vout, cin, cout, sp};
+    const int mode = SYNC && sp.counts ? sp.counts[0] : 1;
+    int differs = 0;
     R P0[9], P1[9], P2[9], P3[9];
     zc.load(P0, z0 - 1);
     zc.load(P1, z0);
     zc.load(P2, z0 + 1);
     int z = z0;
     for (; z + 4 <= z1; z += 4) {
-        zc.step(P0, P1, P2, P3, z, z1);
-        zc.step(P1, P2, P3, P0, z + 1, z1);
-        zc.step(P2, P3, P0, P1, z + 2, z1);
-        zc.step(P3, P0, P1, P2, z + 3, z1);
+        zc.step(P0, P1, P2, P3, z, z1, mode, differs);
+        zc.step(P1, P2, P3, P0, z + 1, z1, mode, differs);
+        zc.step(P2, P3, P0, P1, z + 2, z1, mode, differs);
+        zc.step(P3, P0, P1, P2, z + 3, z1, mode, differs);
     }
-    if (z < z1) zc.step(P0, P1, P2, P3, z, z1);
-    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, z1);
-    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, z1);
+    if (z < z1) zc.step(P0, P1, P2, P3, z, z1, mode, differs);
+    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, z1, mode, differs);
+    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, z1, mode, differs);
+    if (SYNC && sp.counts && mode < 0) {
+        if (__syncthreads_or(differs) && threadIdx.x == 0) atomicOr(sp.uflag, 1);
+    }
 }
 
 // Resident blocks per SM of a kernel at `threads` threads, and the SM count
