@@ -163,9 +163,10 @@ struct SyncParams {
 // (reading R-k; with rrate, the reaction's rate at its last sub-step, reading
 // R-k2) and the first-upward-crossing activation time (R-LAT).
 // EXT: p.rrate may be set (compiled out otherwise).
+// The same with V at the last synchronisation (vold) and the activation
+// time (a0) of node i already loaded by the caller.
 template <typename R, bool EXT>
-__device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) {
-    R vold = p.vsync[i];
+__device__ __forceinline__ int sync_node_loaded(const SyncParams<R>& p, int i, R vnew, R vold, R a0) {
     int k = 1;
     if (p.adaptive) {
         R rate = (EXT && p.rrate) ? p.rrate[i] * p.rrate_scale : (vnew - vold) * p.rate_scale;
@@ -176,7 +177,6 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
         k = k < p.kmax ? k : p.kmax;
     }
     p.kk[i] = (uint8_t)k;
-    R a0 = p.act[i];
     if (a0 < (R)0 && vold < p.vth && vnew >= p.vth) {
         double tprev = (double)step_index(p.step) * p.dt;
         p.act[i] = (R)(tprev + p.dt * (double)((p.vth - vold) / (vnew - vold)));
@@ -184,6 +184,11 @@ __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) 
     p.vsync[i] = vnew;
     if (!isfinite(vnew)) atomicOr(p.flags, 1);
     return k;
+}
+
+template <typename R, bool EXT>
+__device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) {
+    return sync_node_loaded<R, EXT>(p, i, vnew, p.vsync[i], p.act[i]);
 }
 
 // Block-cooperative append of node i (valid lanes) to the list of its k

@@ -405,6 +405,16 @@ __global__ void __launch_bounds__(PZT * PZY) zpair_substep_kernel(OpView<float> 
 // kernel's.
 constexpr int RZX = 32, RZY = 8;
 
+// One plane of a column: the 3 x 3 neighbourhood of V and, for planes the
+// thread computes, the node's Kahan term, V at the last synchronisation and
+// activation time (loaded with the plane, ahead of their use).
+template <typename R>
+struct ZPlane {
+    R v[9];
+    float c;
+    R vs, ac;
+};
+
 template <typename R, bool KAHAN, bool SYNC>
 struct ZColumn {
     const OpView<R>& op;
@@ -412,31 +422,40 @@ struct ZColumn {
     long long nxy;
     int nx, cx, cy, i0;   // i0: node index of the column at plane 0
     bool col_in;
+    int z0, z1;
     R* __restrict__ vout;
     const float* __restrict__ cin;
     float* __restrict__ cout;
     const SyncParams<R>& sp;
 
-    __device__ __forceinline__ void load(R (&r)[9], int p) const {
+    __device__ __forceinline__ void load(ZPlane<R>& P, int p) const {
         const R* q = base + nxy * p;
-        r[0] = q[-nx - 1];
-        r[1] = q[-nx];
-        r[2] = q[-nx + 1];
-        r[3] = q[-1];
-        r[4] = q[0];
-        r[5] = q[1];
-        r[6] = q[nx - 1];
-        r[7] = q[nx];
-        r[8] = q[nx + 1];
+        P.v[0] = q[-nx - 1];
+        P.v[1] = q[-nx];
+        P.v[2] = q[-nx + 1];
+        P.v[3] = q[-1];
+        P.v[4] = q[0];
+        P.v[5] = q[1];
+        P.v[6] = q[nx - 1];
+        P.v[7] = q[nx];
+        P.v[8] = q[nx + 1];
+        if (p >= z0 && p < z1) {
+            const int i = i0 + (int)(nxy * p);
+            if (KAHAN) P.c = __ldg(cin + i);
+            if (SYNC) {
+                P.vs = sp.vsync[i];
+                P.ac = sp.act[i];
+            }
+        }
     }
     // node at plane z from planes z - 1 (A), z (B) and z + 1 (C, loaded a
     // step earlier); the load of plane z + 2 into D is issued first, so two
-    // planes of loads are in flight while the node is computed
-    // mode: the bucketing mode of this synchronisation (counts[0]); in the
-    // uniform-k mode (< 0) a node whose k differs only sets `differs`, voted
-    // on once per block at the end, instead of a block barrier per plane
-    __device__ __forceinline__ void step(const R (&A)[9], const R (&B)[9], const R (&C)[9], R (&D)[9], int z,
-                                         int z1, int mode, int& differs) const {
+    // planes of loads are in flight while the node is computed.  mode: the
+    // bucketing mode of this synchronisation (counts[0]); in the uniform-k
+    // mode (< 0) a node whose k differs only sets `differs`, voted on once
+    // per block at the end, instead of a block barrier per plane
+    __device__ __forceinline__ void step(const ZPlane<R>& A, const ZPlane<R>& B, const ZPlane<R>& C, ZPlane<R>& D,
+                                         int z, int mode, int& differs) const {
         if (z + 2 <= z1) load(D, z + 2);
         int k = 1;
         const int i = i0 + (int)(nxy * z);
@@ -444,14 +463,14 @@ struct ZColumn {
             const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
             auto fetch = [&](int dx, int dy, int dz) {
                 const int j = (dy + 1) * 3 + (dx + 1);
-                return dz < 0 ? A[j] : (dz == 0 ? B[j] : C[j]);
+                return dz < 0 ? A.v[j] : (dz == 0 ? B.v[j] : C.v[j]);
             };
             R v;
             float cc;
-            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, B[4], KAHAN ? cin[i] : 0.f, fetch, v, cc);
+            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, B.v[4], KAHAN ? B.c : 0.f, fetch, v, cc);
             vout[i] = v;
             if (KAHAN) cout[i] = cc;
-            if (SYNC) k = sync_node<R, false>(sp, i, v);
+            if (SYNC) k = sync_node_loaded<R, false>(sp, i, v, B.vs, B.ac);
         }
         if (SYNC && sp.counts) {
             if (mode < 0) differs |= col_in && k != -mode;
@@ -476,23 +495,23 @@ __global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 3 : 2) zreg_subste
     const int col = col_in ? gx + nx * gy : 0;
     const ZColumn<R, KAHAN, SYNC> zc{op, vin + col, (long long)nx * ny, nx,
                                      gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1), gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1),
-                                     col, col_in, vout, cin, cout, sp};
+                                     col, col_in, z0, z1, vout, cin, cout, sp};
     const int mode = SYNC && sp.counts ? sp.counts[0] : 1;
     int differs = 0;
-    R P0[9], P1[9], P2[9], P3[9];
+    ZPlane<R> P0, P1, P2, P3;
     zc.load(P0, z0 - 1);
     zc.load(P1, z0);
     zc.load(P2, z0 + 1);
     int z = z0;
     for (; z + 4 <= z1; z += 4) {
-        zc.step(P0, P1, P2, P3, z, z1, mode, differs);
-        zc.step(P1, P2, P3, P0, z + 1, z1, mode, differs);
-        zc.step(P2, P3, P0, P1, z + 2, z1, mode, differs);
-        zc.step(P3, P0, P1, P2, z + 3, z1, mode, differs);
+        zc.step(P0, P1, P2, P3, z, mode, differs);
+        zc.step(P1, P2, P3, P0, z + 1, mode, differs);
+        zc.step(P2, P3, P0, P1, z + 2, mode, differs);
+        zc.step(P3, P0, P1, P2, z + 3, mode, differs);
     }
-    if (z < z1) zc.step(P0, P1, P2, P3, z, z1, mode, differs);
-    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, z1, mode, differs);
-    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, z1, mode, differs);
+    if (z < z1) zc.step(P0, P1, P2, P3, z, mode, differs);
+    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, mode, differs);
+    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, mode, differs);
     if (SYNC && sp.counts && mode < 0) {
         if (__syncthreads_or(differs) && threadIdx.x == 0) atomicOr(sp.uflag, 1);
     }
