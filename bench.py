@@ -831,8 +831,8 @@ def main():
     ap.add_argument("--profile-run", type=float, default=0.0,
                     help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
     ap.add_argument("--diff-block", type=int, default=-1,
-                    help="with --profile-run: diffusion launch shape (0 = shared-memory z-march, 256 = one "
-                         "thread per node; default: the library's)")
+                    help="with --profile-run: diffusion launch shape (0 = 2D tiles / 3D register z-march, "
+                         "256 = one thread per node; default: the library's)")
     ap.add_argument("--profile-from", type=float, default=0.0,
                     help="with --profile-run: first advance to this time (ms), e.g. into the plateau "
                          "(60) or the resting phase (150)")

@@ -24,7 +24,7 @@ DEFAULT_SPACE = {
     "react_min_blocks": (6, 8, 10),
     "fuse_diffusion": (1, 0),
     "bucket_k": (1, 0),
-    "diff_block": (0, 1, 256),
+    "diff_block": (0, 256),
     "graph_steps": (20, 100),
     "pdl": (1, 0),
 }

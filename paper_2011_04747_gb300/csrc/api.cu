@@ -653,21 +653,6 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
                 if (j != self) A[cls * DAETI_ROW + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
         if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
-        if (c->s.prec == P_F32) {
-            // negated coefficients of node pairs (x, x+1), x even, interleaved
-            static const int pair_cls[5][2] = {{0, 1}, {1, 1}, {1, 2}, {2, 2}, {0, 2}};
-            const size_t rows = tab.m.size() / 3;   // (z, y class)
-            std::vector<double> P(rows * 5 * 2 * DAETI_ROW, 0.0);
-            for (size_t r = 0; r < rows; ++r)
-                for (int t = 0; t < 5; ++t)
-                    for (int j = 0; j < DAETI_ROW; ++j)
-                        for (int h = 0; h < 2; ++h)
-                            P[((r * 5 + t) * DAETI_ROW + j) * 2 + h] = -A[(r * 3 + pair_cls[t][h]) * DAETI_ROW + j];
-            void* pp = c->op.pair;
-            if (fresh && (rc = dalloc(c, &pp, R * P.size()))) return rc;
-            c->op.pair = (float*)pp;
-            if ((rc = upload_real(c, c->op.pair, P.data(), (int64_t)P.size()))) return rc;
-        }
         // per-node table row (z * 3 + y class) * 3 + x class, when it fits 16 bits
         if (fresh && (int64_t)tab.nz * 9 <= 65535) {
             std::vector<uint16_t> cls(N);
@@ -1312,7 +1297,7 @@ int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
 int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
     if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block < 0 ||
-        t->diff_block > 256 || (t->diff_block > 1 && t->diff_block % 32) || t->graph_steps < 0 ||
+        t->diff_block > 256 || t->diff_block % 32 || t->graph_steps < 0 ||
         (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1) || t->diff_zrun < 0)
         return fail(c, DAETI_EINVAL, "bad tuning values");
     int rc = daeti_synchronize(c);

@@ -18,7 +18,6 @@
 // last sub-step of each step I is fused into the reaction launch
 // (reaction.cu).
 #include <algorithm>
-#include <type_traits>
 
 #include "diffops.cuh"
 
@@ -86,112 +85,6 @@ __global__ void __launch_bounds__(TX * TY) tiled2d_substep_kernel(OpView<R> op, 
     if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
 }
 
-// ---------------------------------------------------------------- 3D z-march
-// 3D structured grids with ghost-padded V buffers and the per-class table:
-// a block owns a ZX x ZY column of nodes and marches through a run of z
-// planes.  V planes (tile plus a one-node halo) and the Kahan terms are
-// copied into a ring of ZS shared-memory slots by cp.async, ZD planes ahead
-// of the plane being computed, so each block keeps several KB of loads in
-// flight; every thread keeps the 3 x 3 neighbourhoods of planes z-1, z and
-// z+1 in registers and reads only the new plane's 9 values per step.  The
-// terms are added in the table's order, as in stencil_update everywhere, so
-// the results equal the one-thread-per-node kernel's bit for bit.
-constexpr int ZX = 32, ZY = 8, ZD = 6, ZS = ZD + 1;
-
-template <typename R>
-__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (sizeof(R) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-template <typename R, bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(ZX * ZY) zmarch_substep_kernel(OpView<R> op, int n, int zrun,
-                                                                const R* __restrict__ vin, R* vout,
-                                                                const float* __restrict__ cin, float* cout,
-                                                                SyncParams<R> sp) {
-    constexpr int PX = ZX + 2, PY = ZY + 2, PLANE = PX * PY, NT = ZX * ZY;
-    __shared__ R vbuf[ZS][PLANE];
-    __shared__ float cbuf[KAHAN ? ZS : 1][NT];
-    pdl_wait();
-    pdl_trigger();
-    const int tid = threadIdx.x;
-    const int tx = tid % ZX, ty = tid / ZX;
-    const int x0 = blockIdx.x * ZX, y0 = blockIdx.y * ZY;
-    const int nx = op.nx, ny = op.ny, nz = op.nz;
-    const long long nxy = (long long)nx * ny;
-    const int z0 = blockIdx.z * zrun;
-    const int z1 = min(nz, z0 + zrun);
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool col_in = gx < nx && gy < ny;
-    // One cp.async group per plane p (z0 - 1 <= p): V of plane p over the tile
-    // and its halo (p <= z1; halo nodes past the far faces are never read by a
-    // node of the grid and are skipped), and the Kahan terms of plane p - 1.
-    // Offsets reach at most one plane, row and node beyond the grid, inside the
-    // buffers' ghost margins.
-    auto issue = [&](int p) {
-        if (p <= z1) {
-            R* dst = vbuf[(p + ZS) % ZS];
-            for (int q = tid; q < PLANE; q += NT) {
-                const int hx = x0 - 1 + q % PX, hy = y0 - 1 + q / PX;
-                if (hx <= nx && hy <= ny) cp_async_elem(dst + q, vin + (hx + (long long)nx * hy + nxy * p));
-            }
-        }
-        if (KAHAN && p - 1 >= z0 && p - 1 < z1 && col_in)
-            cp_async_elem(&cbuf[(p - 1) % ZS][tid], cin + (gx + (long long)nx * gy + nxy * (p - 1)));
-        cp_async_commit();
-    };
-    auto load9 = [&](R* r, int p) {
-        const R* src = vbuf[(p + ZS) % ZS] + ty * PX + tx;
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) r[dy * 3 + dx] = src[dy * PX + dx];
-    };
-    for (int p = z0 - 1; p < z0 + ZD; ++p) issue(p);   // ZD + 1 groups: planes z0 - 1 .. z0 + ZD - 1
-    cp_async_wait<ZD - 1>();                          // planes z0 - 1 and z0 have landed
-    __syncthreads();
-    R a[9], b[9], c[9];                               // planes z - 1, z, z + 1
-    load9(a, z0 - 1);
-    load9(b, z0);
-    __syncthreads();                                  // slot of plane z0 - 1 is refilled next
-    const int cx = gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1);
-    const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
-    for (int z = z0; z < z1; ++z) {
-        issue(z + ZD);
-        cp_async_wait<ZD - 1>();                      // plane z + 1 and the Kahan terms of plane z
-        __syncthreads();
-        load9(c, z + 1);
-        int k = 1, i = 0;
-        if (col_in) {
-            i = (int)(gx + (long long)nx * gy + nxy * z);
-            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
-            auto fetch = [&](int dx, int dy, int dz) {
-                const int j = (dy + 1) * 3 + (dx + 1);
-                return dz < 0 ? a[j] : (dz == 0 ? b[j] : c[j]);
-            };
-            R v;
-            float cc;
-            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, b[4], KAHAN ? cbuf[z % ZS][tid] : 0.f, fetch, v, cc);
-            vout[i] = v;
-            if (KAHAN) cout[i] = cc;
-            if (SYNC) k = sync_node<R, false>(sp, i, v);
-        }
-        if (SYNC && sp.counts) bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, i, k, col_in);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            a[j] = b[j];
-            b[j] = c[j];
-        }
-    }
-    cp_async_wait<0>();
-}
-
 template <typename R>
 static SyncParams<R> make_sync(const DevState& s, const SyncArgs& sa, StepRef step, int par, bool lists) {
     SyncParams<R> sp;
@@ -229,168 +122,6 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl
     else
         launch_ex(substep_kernel<R, DIM, KAHAN, false, PAD, false>, grid, block, st, pdl, op, n, vin, vout, cin,
                   cout, sp);
-}
-
-// ------------------------------------------------- 3D z-march, node pairs
-// The float z-march with two x-adjacent nodes per thread in the packed FP32
-// instructions (fma/sub/add.rn.f32x2: each lane rounds exactly as the scalar
-// instruction).  A block owns 32 x 8 nodes (16 x 8 threads); a thread reads
-// its pair's 4 x 3 neighbourhood of each new plane with six 8-byte shared
-// loads and multiplies by rows of the negated pair table (two coefficients
-// per 16-byte load).  Accumulating -sum a_ij (V_j - V_i) with negated
-// coefficients from -0 gives exactly the negation of the scalar sum, so the
-// results equal the one-thread-per-node kernel's.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float lo2(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi2(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-constexpr int PZX = 32, PZT = PZX / 2, PZY = 8;
-
-template <bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(PZT * PZY) zpair_substep_kernel(OpView<float> op, const float* __restrict__ pair,
-                                                                 int n, int zrun, const float* __restrict__ vin,
-                                                                 float* vout, const float* __restrict__ cin,
-                                                                 float* cout, SyncParams<float> sp) {
-    constexpr int PX = PZX + 2, PY = PZY + 2, PLANE = PX * PY, NT = PZT * PZY;
-    __shared__ __align__(16) float vbuf[ZS][PLANE];
-    __shared__ __align__(16) float cbuf[KAHAN ? ZS : 1][2 * NT];
-    pdl_wait();
-    pdl_trigger();
-    const int tid = threadIdx.x;
-    const int tx = tid % PZT, ty = tid / PZT;
-    const int x0 = blockIdx.x * PZX, y0 = blockIdx.y * PZY;
-    const int nx = op.nx, ny = op.ny, nz = op.nz;
-    const long long nxy = (long long)nx * ny;
-    const int z0 = blockIdx.z * zrun;
-    const int z1 = min(nz, z0 + zrun);
-    const int xa = x0 + 2 * tx, gy = y0 + ty;
-    const bool va = xa < nx && gy < ny, vb = xa + 1 < nx && gy < ny;
-    // cp.async group of plane p: V of plane p over the tile and its halo
-    // (p <= z1; halo nodes past the far faces are skipped), and the Kahan
-    // terms of plane p - 1; offsets stay inside the V buffers' ghost margins
-    auto issue = [&](int p) {
-        if (p <= z1) {
-            float* dst = vbuf[(p + ZS) % ZS];
-            for (int q = tid; q < PLANE; q += NT) {
-                const int hx = x0 - 1 + q % PX, hy = y0 - 1 + q / PX;
-                if (hx <= nx && hy <= ny) cp_async_elem(dst + q, vin + (hx + (long long)nx * hy + nxy * p));
-            }
-        }
-        if (KAHAN && p - 1 >= z0 && p - 1 < z1) {
-            const long long i = xa + (long long)nx * gy + nxy * (p - 1);
-            float* dst = &cbuf[(p - 1) % ZS][2 * tid];
-            if (va) cp_async_elem(dst, cin + i);
-            if (vb) cp_async_elem(dst + 1, cin + i + 1);
-        }
-        cp_async_commit();
-    };
-    // the pair's neighbourhood of plane p: w[r][0] = (x-1, x), w[r][1] =
-    // (x, x+1), w[r][2] = (x+1, x+2) for rows y-1, y, y+1 (x = xa)
-    auto load = [&](f32x2 (*w)[3], int p) {
-        const float* src = vbuf[(p + ZS) % ZS] + ty * PX + 2 * tx;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const f32x2 lft = *reinterpret_cast<const f32x2*>(src + r * PX);
-            const f32x2 rgt = *reinterpret_cast<const f32x2*>(src + r * PX + 2);
-            w[r][0] = lft;
-            w[r][1] = pk2(hi2(lft), lo2(rgt));
-            w[r][2] = rgt;
-        }
-    };
-    for (int p = z0 - 1; p < z0 + ZD; ++p) issue(p);
-    cp_async_wait<ZD - 1>();
-    __syncthreads();
-    f32x2 a[3][3], b[3][3], c[3][3];   // planes z - 1, z, z + 1
-    load(a, z0 - 1);
-    load(b, z0);
-    __syncthreads();
-    const int cxa = xa == 0 ? 0 : (xa == nx - 1 ? 2 : 1);
-    const int cxb = xa + 1 >= nx ? 2 : (xa + 1 == nx - 1 ? 2 : 1);
-    const int ptype = cxa == 0 ? (cxb == 1 ? 0 : 4) : (cxa == 1 ? (cxb == 1 ? 1 : 2) : 3);
-    const int cy = gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1);
-    for (int z = z0; z < z1; ++z) {
-        issue(z + ZD);
-        cp_async_wait<ZD - 1>();
-        __syncthreads();
-        load(c, z + 1);
-        const float4* crow = reinterpret_cast<const float4*>(pair + ((size_t)((z * 3 + cy) * 5 + ptype)) * (2 * DAETI_ROW));
-        const f32x2 vi = b[1][1];
-        f32x2 nacc = pk2(-0.f, -0.f);
-#pragma unroll
-        for (int q = 0; q < DAETI_ROW / 2; ++q) {
-            const float4 cc = __ldg(crow + q);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = 2 * q + h;
-                if (j == 13 || j >= 27) continue;
-                const int dz = j / 9 - 1, dy = (j / 3) % 3 - 1, dx = j % 3 - 1;
-                const f32x2 xj = dz < 0 ? a[dy + 1][dx + 1] : (dz == 0 ? b[dy + 1][dx + 1] : c[dy + 1][dx + 1]);
-                nacc = fma2(h ? pk2(cc.z, cc.w) : pk2(cc.x, cc.y), sub2(xj, vi), nacc);
-            }
-        }
-        f32x2 v, cn = 0ull;
-        if (KAHAN) {
-            const f32x2 c0 = *reinterpret_cast<const f32x2*>(&cbuf[z % ZS][2 * tid]);
-            const f32x2 y = sub2(nacc, c0);
-            const f32x2 t = add2(vi, y);
-            cn = sub2(sub2(t, vi), y);
-            v = t;
-        } else {
-            v = add2(vi, nacc);
-        }
-        const long long ia = xa + (long long)nx * gy + nxy * z;
-        int ka = 1, kb = 1;
-        if (va) {
-            vout[ia] = lo2(v);
-            if (KAHAN) cout[ia] = lo2(cn);
-            if (SYNC) ka = sync_node<float, false>(sp, (int)ia, lo2(v));
-        }
-        if (vb) {
-            vout[ia + 1] = hi2(v);
-            if (KAHAN) cout[ia + 1] = hi2(cn);
-            if (SYNC) kb = sync_node<float, false>(sp, (int)ia + 1, hi2(v));
-        }
-        if (SYNC && sp.counts) {
-            bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, (int)ia, ka, va);
-            bucket_nodes(sp.counts, sp.lists, sp.uflag, sp.n, (int)ia + 1, kb, vb);
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                a[r][d] = b[r][d];
-                b[r][d] = c[r][d];
-            }
-    }
-    cp_async_wait<0>();
 }
 
 // ------------------------------------------------- 3D register z-march
@@ -540,78 +271,40 @@ static int sm_count() {
     return cached;
 }
 
-// Shared-memory launch shapes of structured grids (diff_block = 0): 2D tiles,
-// or the 3D z-march with the z range split into runs so that the blocks fill
-// the GPU's resident slots about once.
+// diff_block = 0 on structured grids: 2D shared-memory tiles, or the 3D
+// register z-march with its z range split into runs (zrun_req planes, or
+// chosen so that the blocks cover the GPU's resident slots in few waves).
 template <typename R, bool KAHAN>
 static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
                          const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp,
-                         bool zreg_shape, int zrun_req) {
+                         int zrun_req) {
     if (dop.dim == 2) {
         const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
         if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
         return;
     }
-    {
-        // register z-march (default shared-free shape): columns x run, the
-        // z range split so the grid covers the resident slots about once
-        const long cols = (long)((dop.nx + RZX - 1) / RZX) * ((dop.ny + RZY - 1) / RZY);
-        const int nb = sync ? resident_blocks(zreg_substep_kernel<R, KAHAN, true>, RZX * RZY)
-                            : resident_blocks(zreg_substep_kernel<R, KAHAN, false>, RZX * RZY);
-        const long slots = (long)sm_count() * nb;
-        int best = 1;
-        double best_cost = 1e300;
-        for (int ns = 1; ns <= dop.nz; ++ns) {   // waves x (planes per run + prologue)
-            const int zr = (dop.nz + ns - 1) / ns;
-            const long blocks = cols * ((dop.nz + zr - 1) / zr);
-            const double cost = (double)((blocks + slots - 1) / slots) * (zr + 1.0);
-            if (cost < best_cost - 1e-9) {
-                best_cost = cost;
-                best = ns;
-            }
-        }
-        const int zrun = zrun_req > 0 ? std::min(zrun_req, dop.nz) : (dop.nz + best - 1) / best;
-        const dim3 grid((dop.nx + RZX - 1) / RZX, (dop.ny + RZY - 1) / RZY, (dop.nz + zrun - 1) / zrun);
-        if (zreg_shape) {
-            if (sync)
-                launch_ex(zreg_substep_kernel<R, KAHAN, true>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin,
-                          cout, sp);
-            else
-                launch_ex(zreg_substep_kernel<R, KAHAN, false>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin,
-                          cout, sp);
-            return;
-        }
-    }
-    if constexpr (std::is_same<R, float>::value) {
-        if (dop.pair) {
-            const long tiles = (long)((dop.nx + PZX - 1) / PZX) * ((dop.ny + PZY - 1) / PZY);
-            const int nb = sync ? resident_blocks(zpair_substep_kernel<KAHAN, true>, PZT * PZY)
-                                : resident_blocks(zpair_substep_kernel<KAHAN, false>, PZT * PZY);
-            const long slots = (long)sm_count() * nb;
-            const int nsplit = (int)std::max<long>(1, std::min<long>(dop.nz, (slots + tiles / 2) / tiles));
-            const int zrun = (dop.nz + nsplit - 1) / nsplit;
-            const dim3 grid((dop.nx + PZX - 1) / PZX, (dop.ny + PZY - 1) / PZY, (dop.nz + zrun - 1) / zrun);
-            if (sync)
-                launch_ex(zpair_substep_kernel<KAHAN, true>, grid, PZT * PZY, st, pdl, op, (const float*)dop.pair, n,
-                          zrun, vin, vout, cin, cout, sp);
-            else
-                launch_ex(zpair_substep_kernel<KAHAN, false>, grid, PZT * PZY, st, pdl, op, (const float*)dop.pair,
-                          n, zrun, vin, vout, cin, cout, sp);
-            return;
-        }
-    }
-    const long tiles = (long)((dop.nx + ZX - 1) / ZX) * ((dop.ny + ZY - 1) / ZY);
-    const int nb = sync ? resident_blocks(zmarch_substep_kernel<R, KAHAN, true>, ZX * ZY)
-                        : resident_blocks(zmarch_substep_kernel<R, KAHAN, false>, ZX * ZY);
+    const long cols = (long)((dop.nx + RZX - 1) / RZX) * ((dop.ny + RZY - 1) / RZY);
+    const int nb = sync ? resident_blocks(zreg_substep_kernel<R, KAHAN, true>, RZX * RZY)
+                        : resident_blocks(zreg_substep_kernel<R, KAHAN, false>, RZX * RZY);
     const long slots = (long)sm_count() * nb;
-    const int nsplit = (int)std::max<long>(1, std::min<long>(dop.nz, (slots + tiles / 2) / tiles));
-    const int zrun = (dop.nz + nsplit - 1) / nsplit;
-    const dim3 grid((dop.nx + ZX - 1) / ZX, (dop.ny + ZY - 1) / ZY, (dop.nz + zrun - 1) / zrun);
+    int best = 1;
+    double best_cost = 1e300;
+    for (int ns = 1; ns <= dop.nz; ++ns) {   // waves x (planes per run + prologue)
+        const int zr = (dop.nz + ns - 1) / ns;
+        const long blocks = cols * ((dop.nz + zr - 1) / zr);
+        const double cost = (double)((blocks + slots - 1) / slots) * (zr + 1.0);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = ns;
+        }
+    }
+    const int zrun = zrun_req > 0 ? std::min(zrun_req, dop.nz) : (dop.nz + best - 1) / best;
+    const dim3 grid((dop.nx + RZX - 1) / RZX, (dop.ny + RZY - 1) / RZY, (dop.nz + zrun - 1) / zrun);
     if (sync)
-        launch_ex(zmarch_substep_kernel<R, KAHAN, true>, grid, ZX * ZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
+        launch_ex(zreg_substep_kernel<R, KAHAN, true>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
     else
-        launch_ex(zmarch_substep_kernel<R, KAHAN, false>, grid, ZX * ZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
+        launch_ex(zreg_substep_kernel<R, KAHAN, false>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
 }
 
 template <typename R, bool KAHAN>
@@ -619,19 +312,18 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
                        StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int zrun) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
     const bool padded = s.vpad >= stencil_reach(dop);
-    const bool zreg = block == 1 && dop.dim == 3;   // register z-march
-    if (dop.kind == 0 && (block == 0 || zreg) && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
-        // structured grid, shared-memory tiles (3D: the z-march, which reads
-        // the ghost margins of padded V buffers)
+    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
+        // structured grid: 2D shared-memory tiles, or the 3D register
+        // z-march (which reads the ghost margins of padded V buffers)
         const OpView<R> op = op_view<R>(dop);
         const R* vin = (const R*)s.V[src];
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zreg, zrun);
+        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zrun);
         return;
     }
-    if (block <= 1) block = 256;
+    if (block <= 0) block = 256;
     const int grid = (int)((s.n + block - 1) / block);
     if (grid == 0) return;
     const OpView<R> op = op_view<R>(dop);

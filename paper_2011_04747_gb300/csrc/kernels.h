@@ -61,11 +61,6 @@ struct DiffOp {
     void* coef = nullptr;    // table: [nz*9][28] off-diagonal dt_ad K_ij / m_i (centre entry and pad 0)
     uint16_t* cls = nullptr; // table row of each node (nullable)
     int per_node = 0;        // 1: coef holds one row per node (row i for node i), cls unused
-    // float tables only: rows of negated coefficients of two x-adjacent
-    // nodes interleaved, [nz*3 (z, y class)][5 pair types][28 pairs]
-    // (pair types by the x classes of (x, x+1), x even: (0,1) (1,1) (1,2)
-    // (2,-) (0,2)); read by the paired z-march diffusion kernel
-    float* pair = nullptr;
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
     int64_t* chunk_ptr = nullptr;   // start of chunk c in val/col
@@ -140,8 +135,8 @@ void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef s
 // synchronisation epilogue runs on the result (lists of parity `par`).
 // pdl: launch with programmatic dependent launch (the kernels wait for their
 // predecessor before touching memory either way).
-// block: 32..256 one thread per node; 0 shared-memory tiles / z-march; 1 the
-// register z-march on 3D grids, zrun planes per thread (0: automatic).
+// block: 32..256 one thread per node; 0 on structured grids: 2D shared-memory
+// tiles or the 3D register z-march with zrun planes per thread (0: automatic).
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false, int zrun = 0);
 void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st);

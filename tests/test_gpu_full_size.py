@@ -67,15 +67,14 @@ def test_full_batch_sampled_tissues():
 
 @pytest.mark.parametrize("dims", [(101, 101, 26), (401, 401, 26)])
 def test_zmarch_diffusion_bit_identical_at_bench_sizes(dims):
-    """The z-march diffusion kernels (diff_block = 0: shared-memory planes, two
-    nodes per thread; 1: register columns) against the one-thread-per-node
-    kernel on the bench slab and the 4.18 M-node slab,
+    """The register z-march diffusion kernel (diff_block = 0) against the
+    one-thread-per-node kernel on the bench slab and the 4.18 M-node slab,
     over the stimulus and upstroke (lists, uniform-k votes and plain
     sub-steps), FP32 with compensated V: identical states."""
     binding = ensure_lib()
     wl = I.tp06_slab_3d(*dims, t_end=6.0)
     out = []
-    for diff_block in (256, 0, 1):
+    for diff_block in (256, 0):
         s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=20)
         s.daeti_set_tuning(diff_block=diff_block)
         s.daeti_advance(3.0)
