@@ -7,6 +7,9 @@
 * ``aligned_max_dv``: largest |V_a - V_b| between two voltage traces after
   shifting one by the difference of their activation times (the comparison of
   "aligned APs" in Sections 3.1 and 3.2), by linear interpolation in time.
+* ``apd90``: action potential duration at 90 % repolarisation measured from
+  the instant of largest dV/dt (the APD90 of Section 3.1 and e_APD of
+  Eq. 4, Section 3.3).
 """
 from __future__ import annotations
 
@@ -38,3 +41,27 @@ def aligned_max_dv(times, va, vb, act_a, act_b):
     ok = (tb >= times[0]) & (tb <= times[-1])
     vb_shift = np.interp(tb[ok], times, vb)
     return float(np.max(np.abs(np.asarray(va)[ok] - vb_shift))) if ok.any() else float("nan")
+
+
+def apd90(times, v):
+    """APD90 of the first action potential in a uniformly sampled trace.
+
+    Start: the midpoint of the sample interval with the largest rise of V
+    (the maximum of dV/dt, resolved to the sampling).  End: the first time
+    after the peak at which V has fallen by 90 % of its amplitude (peak minus
+    the trace's first value), interpolated linearly between samples.  NaN if
+    V does not come back down that far.
+    """
+    times = np.asarray(times, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    jump = v[1:] - v[:-1]
+    j = int(np.argmax(jump))
+    t_start = 0.5 * (times[j] + times[j + 1])
+    k = j + int(np.argmax(v[j:]))
+    v90 = v[k] - 0.9 * (v[k] - v[0])
+    after = np.nonzero(v[k:] < v90)[0]
+    if after.size == 0:
+        return float("nan")
+    m = k + int(after[0])
+    frac = (v[m - 1] - v90) / (v[m - 1] - v[m])
+    return float(times[m - 1] + frac * (times[m] - times[m - 1]) - t_start)

@@ -62,7 +62,14 @@ struct daeti_batch {
     ReactTuning rtune;
     int64_t nstep = 0;
     int cur = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // steps with / without an open stimulus window
+    // per-k node lists of each model pool (0 MS, 1 TP06), as for a single
+    // tissue: list k of pool p at plists[p] + k * n_p (pool-local indices),
+    // lengths [2 parities][DAETI_MAX_K], uniform-k flags at pflags[p] + 2 + parity
+    int* plists[2] = {nullptr, nullptr};
+    int* pcounts[2] = {nullptr, nullptr};
+    int* pflags[2] = {nullptr, nullptr};
+    int par = 0;
+    cudaGraphExec_t graph[2][2] = {};   // [list parity][steps with / without an open stimulus window]
     std::vector<StimDev> stim_dev;                     // host copy of the stimulus slots
     int graph_steps = 20;
     std::vector<void*> allocs;
@@ -83,19 +90,12 @@ int bfail(daeti_batch* b, int code, const std::string& msg) {
                          std::string(#call) + ": " + cudaGetErrorString(e_));                      \
     } while (0)
 
-// One diffusion sub-step of every tissue.  V buffers carry a zeroed ghost
-// margin wider than the largest tissue's stencil reach, and out-of-tissue
-// offsets have coefficient 0 in each tissue's table, so a neighbour read past
-// a tissue's edge (the next tissue or the margin) adds exactly 0 and no
-// boundary test is needed; the node's table row is precomputed.
+// One node's sub-step (and synchronisation): returns k of the next step A.
 template <typename R, bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev* __restrict__ info,
-                                                           const int* __restrict__ tid,
-                                                           const uint32_t* __restrict__ rows, int n,
-                                                           const R* __restrict__ vin, R* vout, const float* cin,
-                                                           float* cout, const R* __restrict__ coef, SyncParams<R> sp) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ int batch_node(const TissueInfoDev* __restrict__ info, const int* __restrict__ tid,
+                                          const uint32_t* __restrict__ rows, int i, const R* __restrict__ vin,
+                                          R* vout, const float* cin, float* cout, const R* __restrict__ coef,
+                                          const SyncParams<R>& sp) {
     const TissueInfoDev t = info[tid[i]];
     const R* crow = coef + (size_t)rows[i] * DAETI_ROW;
     const int nx = t.nx, nxy = t.nx * t.ny;
@@ -112,12 +112,49 @@ __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev*
         SyncParams<R> p = sp;
         p.rate_scale = (R)t.rate_scale;
         p.vth = (R)t.vth;
-        sync_node<R, false>(p, i, v);
+        return sync_node<R, false>(p, i, v);
+    }
+    return 1;
+}
+
+// Bucketing of one model pool at a synchronisation (pool-local node indices).
+struct PoolBuckets {
+    int* counts;   // lengths of the next step A's lists (null: no lists)
+    int* lists;
+    int* uflag;
+    int n;         // nodes in the pool
+    int off;       // first node of the pool in the batch index space
+};
+
+// One diffusion sub-step of every tissue.  V buffers carry a zeroed ghost
+// margin wider than the largest tissue's stencil reach, and out-of-tissue
+// offsets have coefficient 0 in each tissue's table, so a neighbour read past
+// a tissue's edge (the next tissue or the margin) adds exactly 0 and no
+// boundary test is needed; the node's table row is precomputed.  The
+// synchronising sub-step also files each node into its model pool's per-k
+// lists for the next step A (or votes that k is still uniform).
+template <typename R, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev* __restrict__ info,
+                                                           const int* __restrict__ tid,
+                                                           const uint32_t* __restrict__ rows, int n,
+                                                           const R* __restrict__ vin, R* vout, const float* cin,
+                                                           float* cout, const R* __restrict__ coef, SyncParams<R> sp,
+                                                           PoolBuckets pb0, PoolBuckets pb1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    int k = 1;
+    if (valid) k = batch_node<R, KAHAN, SYNC>(info, tid, rows, i, vin, vout, cin, cout, coef, sp);
+    // every thread of the block takes part in both pools' bucketing
+    if (SYNC && pb0.counts) {
+        bucket_nodes(pb0.counts, pb0.lists, pb0.uflag, pb0.n, i - pb0.off, k, valid && i < pb1.off);
+        bucket_nodes(pb1.counts, pb1.lists, pb1.uflag, pb1.n, i - pb1.off, k, valid && i >= pb1.off);
     }
 }
 
+// par: list parity of the step whose synchronisation this is (the lists
+// filed are those of parity par ^ 1, the next step's).
 template <typename R, bool KAHAN>
-void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t st) {
+void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t st, int par) {
     SyncParams<R> sp;
     sp.vsync = (R*)b->s_all.vsync;
     sp.kk = b->s_all.kk;
@@ -139,18 +176,27 @@ void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t
     R* vout = (R*)b->s_all.V[1 - src];
     const float* cin = KAHAN ? b->s_all.C[src] : nullptr;
     float* cout = KAHAN ? b->s_all.C[1 - src] : nullptr;
+    PoolBuckets pb[2];
+    const int nxt = par ^ 1;
+    for (int q = 0; q < 2; ++q) {
+        pb[q].counts = b->pcounts[q] + nxt * DAETI_MAX_K;
+        pb[q].lists = b->plists[q];
+        pb[q].uflag = b->pflags[q] + 2 + nxt;
+        pb[q].n = (int)(q ? b->n_tp : b->n_ms);
+        pb[q].off = q ? (int)b->n_ms : 0;
+    }
     if (sync)
         batch_substep_kernel<R, KAHAN, true><<<grid, 256, 0, st>>>(b->info, b->tid, b->rows, n, vin, vout, cin,
-                                                                  cout, (const R*)b->coef, sp);
+                                                                  cout, (const R*)b->coef, sp, pb[0], pb[1]);
     else
         batch_substep_kernel<R, KAHAN, false><<<grid, 256, 0, st>>>(b->info, b->tid, b->rows, n, vin, vout, cin,
-                                                                   cout, (const R*)b->coef, sp);
+                                                                   cout, (const R*)b->coef, sp, pb[0], pb[1]);
 }
 
-void batch_diffuse_any(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t st) {
-    if (b->s_all.prec == P_F64) batch_diffuse<double, false>(b, src, sync, ref, st);
-    else if (b->s_all.kahan) batch_diffuse<float, true>(b, src, sync, ref, st);
-    else batch_diffuse<float, false>(b, src, sync, ref, st);
+void batch_diffuse_any(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t st, int par) {
+    if (b->s_all.prec == P_F64) batch_diffuse<double, false>(b, src, sync, ref, st, par);
+    else if (b->s_all.kahan) batch_diffuse<float, true>(b, src, sync, ref, st, par);
+    else batch_diffuse<float, false>(b, src, sync, ref, st, par);
 }
 
 // View of one model's contiguous node range as a single-tissue state.
@@ -169,27 +215,32 @@ DevState pool_view(daeti_batch* b, bool ms) {
     v.act = (char*)b->s_all.act + o * r;
     v.kk = b->s_all.kk + o;
     v.stim_mask = b->s_all.stim_mask ? b->s_all.stim_mask + o : nullptr;
-    v.lists = nullptr;
+    v.lists = b->plists[ms ? 0 : 1];
+    v.counts = b->pcounts[ms ? 0 : 1];
+    v.flags = b->pflags[ms ? 0 : 1];
+    v.substeps = nullptr;
     return v;
 }
 
 // One step of every tissue (quiet: no stimulus window is open during it, so
-// the reaction launches are told there are no stimuli).
-void batch_step(daeti_batch* b, StepRef ref, cudaStream_t st, bool quiet = false) {
+// the reaction launches are told there are no stimuli) with the lists of
+// parity par; returns the parity of the next step.
+int batch_step(daeti_batch* b, StepRef ref, cudaStream_t st, int par, bool quiet = false) {
     int buf = b->cur;
     for (int i = 0; i < b->l; ++i) {
-        batch_diffuse_any(b, buf, false, ref, st);
+        batch_diffuse_any(b, buf, false, ref, st, par);
         buf ^= 1;
     }
     DiffOp none;
     DevState ms = pool_view(b, true), tp = pool_view(b, false);
     if (quiet) ms.n_stims = tp.n_stims = 0;
-    if (b->n_ms) launch_reaction(ms, b->ms_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
-    if (b->n_tp) launch_reaction(tp, b->tp_args, b->dt, ref, false, 0, buf, false, none, b->rtune, st);
+    if (b->n_ms) launch_reaction(ms, b->ms_args, b->dt, ref, true, par, buf, false, none, b->rtune, st);
+    if (b->n_tp) launch_reaction(tp, b->tp_args, b->dt, ref, true, par, buf, false, none, b->rtune, st);
     for (int i = 0; i < b->l; ++i) {
-        batch_diffuse_any(b, buf, i == b->l - 1, ref, st);
+        batch_diffuse_any(b, buf, i == b->l - 1, ref, st, par);
         buf ^= 1;
     }
+    return par ^ 1;
 }
 
 int balloc(daeti_batch* b, void** p, size_t bytes) {
@@ -250,8 +301,8 @@ int daeti_batch_create(daeti_batch** out, const daeti_options* opt) {
 int daeti_batch_destroy(daeti_batch* b) {
     if (!b) return DAETI_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (int q = 0; q < 2; ++q)
-        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
+    for (int q = 0; q < 4; ++q)
+        if (b->graph[q / 2][q % 2]) cudaGraphExecDestroy(b->graph[q / 2][q % 2]);
     for (void* p : b->allocs) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -431,6 +482,15 @@ int daeti_batch_prepare(daeti_batch* b) {
     s.flags = (int*)p;
     if ((rc = balloc(b, &p, 8))) return rc;
     s.step_ctr = (long long*)p;
+    for (int q = 0; q < 2; ++q) {
+        const int64_t np = q ? b->n_tp : b->n_ms;
+        if ((rc = balloc(b, &p, sizeof(int) * (size_t)(b->kmax + 1) * (size_t)std::max<int64_t>(1, np)))) return rc;
+        b->plists[q] = (int*)p;
+        if ((rc = balloc(b, &p, sizeof(int) * 2 * DAETI_MAX_K))) return rc;
+        b->pcounts[q] = (int*)p;
+        if ((rc = balloc(b, &p, 16))) return rc;
+        b->pflags[q] = (int*)p;
+    }
     if ((rc = balloc(b, &b->S_ms, R * std::max<int64_t>(1, b->n_ms)))) return rc;
     if ((rc = balloc(b, &b->S_tp, R * state_elems(std::max<int64_t>(1, b->n_tp), 18)))) return rc;
     if (!sd.empty()) {
@@ -499,9 +559,17 @@ int daeti_batch_prepare(daeti_batch* b) {
     }
     BCK(cudaMemsetAsync(s.kk, 1, N, b->stream));
     BCK(cudaMemsetAsync(s.flags, 0, 16, b->stream));
+    // every node of a pool in the k = 1 list of parity 0
+    for (int q = 0; q < 2; ++q) {
+        BCK(cudaMemsetAsync(b->pcounts[q], 0, sizeof(int) * 2 * DAETI_MAX_K, b->stream));
+        BCK(cudaMemsetAsync(b->pflags[q], 0, 16, b->stream));
+        if (q ? b->n_tp : b->n_ms) launch_rebuild_lists(pool_view(b, q == 0), 0, b->stream);
+    }
+    BCK(cudaGetLastError());
     BCK(cudaStreamSynchronize(b->stream));
     b->nstep = 0;
     b->cur = 0;
+    b->par = 0;
     return DAETI_OK;
 }
 
@@ -519,27 +587,30 @@ int daeti_batch_advance(daeti_batch* b, double t_end) {
         while (remaining >= G) {
             const int quiet =
                 !stimulus_in_steps(b->stim_dev.data(), (int)b->stim_dev.size(), b->dt, b->nstep, G) ? 1 : 0;
-            if (!b->graph[quiet]) {
+            cudaGraphExec_t& ge = b->graph[b->par][quiet];
+            int par = b->par;
+            if (!ge) {
                 cudaGraph_t g = nullptr;
                 BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
                 for (int j = 0; j < G; ++j)
-                    batch_step(b, StepRef{b->s_all.step_ctr, (long long)j}, b->cap_stream, quiet != 0);
+                    par = batch_step(b, StepRef{b->s_all.step_ctr, (long long)j}, b->cap_stream, par, quiet != 0);
                 launch_tick(b->s_all.step_ctr, G, b->cap_stream);
                 BCK(cudaStreamEndCapture(b->cap_stream, &g));
-                cudaError_t e = cudaGraphInstantiate(&b->graph[quiet], g, 0);
+                cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) {
-                    b->graph[quiet] = nullptr;
+                    ge = nullptr;
                     return bfail(b, DAETI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
                 }
             }
-            BCK(cudaGraphLaunch(b->graph[quiet], b->stream));
+            BCK(cudaGraphLaunch(ge, b->stream));
+            b->par ^= G & 1;
             b->nstep += G;
             remaining -= G;
         }
     }
     while (remaining > 0) {
-        batch_step(b, StepRef{nullptr, (long long)b->nstep}, b->stream);
+        b->par = batch_step(b, StepRef{nullptr, (long long)b->nstep}, b->stream, b->par);
         b->nstep++;
         remaining--;
     }

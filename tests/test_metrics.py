@@ -80,3 +80,20 @@ def test_package_and_oracle_measures_agree():
     a, b = _ap(t, 30.0), _ap(t, 42.0) + rng.normal(scale=0.01, size=t.size)
     assert pm.aligned_max_dv(t, a, b, 30.0, 41.9) == pytest.approx(om.aligned_max_dv(t, a, b, 30.0, 41.9),
                                                                    rel=1e-12)
+
+
+def test_oracle_apd90_of_a_synthetic_ap():
+    """The oracle's APD90 (start at the sample interval of largest rise, no
+    sub-sample refinement) against the closed form of the synthetic AP: within
+    half a sampling step, and exact when the steepest point is an interval
+    midpoint."""
+    for dt in (0.05, 0.1):
+        t = np.arange(int(600 / dt)) * dt
+        for t_mid in (40.0 + dt / 2, 40.0123, 40.031):
+            got = om.apd90(t, _smooth_ap(t, t_mid))
+            assert got == pytest.approx(275.0, abs=0.5 * dt + 0.005)
+        assert om.apd90(t, _smooth_ap(t, 40.0 + dt / 2)) == pytest.approx(275.0, abs=0.005)
+    t = np.arange(6000) * 0.1
+    assert np.isnan(om.apd90(t[:1000], _smooth_ap(t, 50.0)[:1000]))
+    # the package's refined value and the oracle's agree to the sampling step
+    assert abs(om.apd90(t, _smooth_ap(t, 50.037)) - pm.apd90(t, _smooth_ap(t, 50.037))) <= 0.1
