@@ -673,18 +673,25 @@ def bench_batch(args, env):
     wls = inputs.batch_tissues()
     t_end = 300.0
     n_nodes = sum(w.n_nodes for w in wls)
-    n_steps = int(round(t_end / 0.1))
-    batch = binding.Batch(precision="fp32_kahan", graph_steps=args.graph_steps, stream=env.stream)
-    for w in wls:
-        d = binding.describe_workload(w)
-        batch.daeti_batch_add(d)
-        d.close()
-    batch.daeti_batch_prepare()
-    sec_b = env.timed(lambda: batch.daeti_batch_advance(t_end), 1, 0)
-    batch.close()
+    n_steps = int(round((t_end - 1.0) / 0.1))    # timed: 1 ms .. 300 ms
+    secs = {}
+    for bucket in (1, 0):
+        # bucket_k = 1: the TP06 tissues' nodes grouped by k (warp-uniform sub-step counts)
+        batch = binding.Batch(precision="fp32_kahan", graph_steps=args.graph_steps, stream=env.stream,
+                              bucket_k=bool(bucket))
+        for w in wls:
+            d = binding.describe_workload(w)
+            batch.daeti_batch_add(d)
+            d.close()
+        batch.daeti_batch_prepare()
+        batch.daeti_batch_advance(1.0)        # graphs captured, caches warm; 1 ms of the run
+        secs[bucket] = env.timed(lambda: batch.daeti_batch_advance(t_end), 1, 0)
+        batch.close()
+    sec_b = secs[1]
     solvers = [binding.solver_from_workload(w, precision="fp32_kahan", graph_steps=args.graph_steps) for w in wls]
     for s in solvers:
         s.daeti_set_stream(env.stream)
+        s.daeti_advance(1.0)                  # as the batch: graphs captured, first 1 ms untimed
 
     def seq():
         for s in solvers:
@@ -697,8 +704,10 @@ def bench_batch(args, env):
             "value": env.world * n_nodes * n_steps / sec_b, "unit": UNIT, "n_gpus": env.world,
             "steps": 1, "warmup": 0, "ms_per_step": sec_b * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch_512_tissues_300ms", "nodes": n_nodes, "strang_steps": n_steps},
+            "config": {"workload": "batch_512_tissues_300ms", "nodes": n_nodes, "strang_steps": n_steps,
+                       "timed": "1 ms .. 300 ms of each run (the first 1 ms captures the graphs)"},
             "sequential": {"value": n_nodes * n_steps / sec_s, "ms": sec_s * 1e3},
+            "without_k_lists": {"value": env.world * n_nodes * n_steps / secs[0], "ms": secs[0] * 1e3},
             "batched_over_sequential": sec_s / sec_b}
 
 

@@ -69,6 +69,10 @@ struct daeti_batch {
     int* pcounts[2] = {nullptr, nullptr};
     int* pflags[2] = {nullptr, nullptr};
     int par = 0;
+    // lists in use per pool: the TP06 pool with bucket_k (its sub-steps are
+    // long enough for warp-uniform k to pay for the bucketing); the
+    // Mitchell-Schaeffer pool takes each node's own k
+    bool listed[2] = {false, false};
     cudaGraphExec_t graph[2][2] = {};   // [list parity][steps with / without an open stimulus window]
     std::vector<StimDev> stim_dev;                     // host copy of the stimulus slots
     int graph_steps = 20;
@@ -144,11 +148,9 @@ __global__ void __launch_bounds__(256) batch_substep_kernel(const TissueInfoDev*
     const bool valid = i < n;
     int k = 1;
     if (valid) k = batch_node<R, KAHAN, SYNC>(info, tid, rows, i, vin, vout, cin, cout, coef, sp);
-    // every thread of the block takes part in both pools' bucketing
-    if (SYNC && pb0.counts) {
-        bucket_nodes(pb0.counts, pb0.lists, pb0.uflag, pb0.n, i - pb0.off, k, valid && i < pb1.off);
-        bucket_nodes(pb1.counts, pb1.lists, pb1.uflag, pb1.n, i - pb1.off, k, valid && i >= pb1.off);
-    }
+    // every thread of the block takes part in each listed pool's bucketing
+    if (SYNC && pb0.counts) bucket_nodes(pb0.counts, pb0.lists, pb0.uflag, pb0.n, i - pb0.off, k, valid && i < pb1.off);
+    if (SYNC && pb1.counts) bucket_nodes(pb1.counts, pb1.lists, pb1.uflag, pb1.n, i - pb1.off, k, valid && i >= pb1.off);
 }
 
 // par: list parity of the step whose synchronisation this is (the lists
@@ -179,7 +181,7 @@ void batch_diffuse(daeti_batch* b, int src, bool sync, StepRef ref, cudaStream_t
     PoolBuckets pb[2];
     const int nxt = par ^ 1;
     for (int q = 0; q < 2; ++q) {
-        pb[q].counts = b->pcounts[q] + nxt * DAETI_MAX_K;
+        pb[q].counts = b->listed[q] ? b->pcounts[q] + nxt * DAETI_MAX_K : nullptr;
         pb[q].lists = b->plists[q];
         pb[q].uflag = b->pflags[q] + 2 + nxt;
         pb[q].n = (int)(q ? b->n_tp : b->n_ms);
@@ -234,8 +236,8 @@ int batch_step(daeti_batch* b, StepRef ref, cudaStream_t st, int par, bool quiet
     DiffOp none;
     DevState ms = pool_view(b, true), tp = pool_view(b, false);
     if (quiet) ms.n_stims = tp.n_stims = 0;
-    if (b->n_ms) launch_reaction(ms, b->ms_args, b->dt, ref, true, par, buf, false, none, b->rtune, st);
-    if (b->n_tp) launch_reaction(tp, b->tp_args, b->dt, ref, true, par, buf, false, none, b->rtune, st);
+    if (b->n_ms) launch_reaction(ms, b->ms_args, b->dt, ref, b->listed[0], par, buf, false, none, b->rtune, st);
+    if (b->n_tp) launch_reaction(tp, b->tp_args, b->dt, ref, b->listed[1], par, buf, false, none, b->rtune, st);
     for (int i = 0; i < b->l; ++i) {
         batch_diffuse_any(b, buf, i == b->l - 1, ref, st, par);
         buf ^= 1;
@@ -559,11 +561,13 @@ int daeti_batch_prepare(daeti_batch* b) {
     }
     BCK(cudaMemsetAsync(s.kk, 1, N, b->stream));
     BCK(cudaMemsetAsync(s.flags, 0, 16, b->stream));
-    // every node of a pool in the k = 1 list of parity 0
+    // every node of a listed pool in the k = 1 list of parity 0
+    b->listed[0] = false;
+    b->listed[1] = b->opt.bucket_k != 0 && b->n_tp > 0;
     for (int q = 0; q < 2; ++q) {
         BCK(cudaMemsetAsync(b->pcounts[q], 0, sizeof(int) * 2 * DAETI_MAX_K, b->stream));
         BCK(cudaMemsetAsync(b->pflags[q], 0, 16, b->stream));
-        if (q ? b->n_tp : b->n_ms) launch_rebuild_lists(pool_view(b, q == 0), 0, b->stream);
+        if (b->listed[q]) launch_rebuild_lists(pool_view(b, q == 0), 0, b->stream);
     }
     BCK(cudaGetLastError());
     BCK(cudaStreamSynchronize(b->stream));
