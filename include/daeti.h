@@ -182,6 +182,15 @@ int daeti_update_conductivity(daeti_ctx* ctx, int64_t n_elem, const double* d_lo
 int daeti_update_conductivity_nodal(daeti_ctx* ctx, int64_t n_nodes, const double* d_long,
                                     const double* d_trans, const double* fibre);
 
+/* Replace the cell model's parameters after prepare (same model, same count
+ * as daeti_set_cell_model: Mitchell-Schaeffer {tau_in, tau_out, tau_open,
+ * tau_close, v_gate}, TP06 {celltype} unless types are given per node).  The
+ * state and the schedule are kept; captured graphs (also the adjoint's) are
+ * dropped, since they hold the model's rates.  Used with
+ * daeti_update_conductivity to re-evaluate a misfit and its gradient without
+ * a new prepare.  Errors: EINVAL, ESTATE. */
+int daeti_update_cell_params(daeti_ctx* ctx, const double* params, int n_params);
+
 /* Stability data computed by prepare (any pointer may be NULL). */
 int daeti_get_stability(daeti_ctx* ctx, double* dt_s, double* lambda_max, int* l,
                         int* k_max, double* dt_eff);

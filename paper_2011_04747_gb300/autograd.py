@@ -7,6 +7,12 @@ and back-propagates dL/d(d_node) and dL/d(tau_close).  The library computes the
 loss and both gradients in one call (forward with binomial checkpoints, then
 the reverse sweep); its nodal entry points form the element means and apply
 their chain rule to the gradient, so this wrapper only moves arrays.
+
+The problem keeps one prepared solver: later calls replace its conductivity
+(daeti_update_conductivity_nodal) and tau_close (daeti_update_cell_params)
+and keep the prepared schedule (dt, l, k_max) and the adjoint's device
+buffers; only an update that the prepared l cannot take stably
+(DAETI_EUNSTABLE) prepares a new solver.  ``problem.close()`` frees it.
 """
 from __future__ import annotations
 
@@ -32,6 +38,13 @@ class MisfitProblem:
     n_slots: int = 32
     precision: str = "fp32_kahan"
     dt: float = 0.1
+    _solver: object = dataclasses.field(default=None, repr=False, compare=False)
+    prepares: int = dataclasses.field(default=0, compare=False)   # solvers prepared so far
+
+    def close(self):
+        if self._solver is not None:
+            self._solver.close()
+            self._solver = None
 
     def elements(self):
         nx, ny = self.n[0], self.n[1]
@@ -43,9 +56,7 @@ class MisfitProblem:
         return base[:, None] + np.array(offs)[None, :]
 
 
-def _solve(problem: MisfitProblem, d_node: np.ndarray, tau_close: float):
-    params = list(problem.ms_params)
-    params[3] = float(tau_close)
+def _prepare(problem: MisfitProblem, d_node: np.ndarray, params):
     s = binding.Solver(precision=problem.precision, dt=problem.dt, graph_steps=0)
     try:
         s.daeti_set_mesh_grid(problem.dim, problem.n, problem.h)
@@ -54,11 +65,30 @@ def _solve(problem: MisfitProblem, d_node: np.ndarray, tau_close: float):
         for st in problem.stimuli:
             s.daeti_add_stimulus(st.nodes, st.t_start, st.duration, st.amplitude, st.period, st.count)
         s.daeti_prepare()
-        loss, g_node, g_tau = s.daeti_adjoint(problem.sensors, problem.data, problem.n_steps,
-                                              problem.sample_every, problem.n_slots, 0, nodal=True)
-    finally:
+    except Exception:
         s.close()
-    return loss, g_node, g_tau
+        raise
+    problem.prepares += 1
+    return s
+
+
+def _solve(problem: MisfitProblem, d_node: np.ndarray, tau_close: float):
+    params = list(problem.ms_params)
+    params[3] = float(tau_close)
+    s = problem._solver
+    if s is not None:
+        try:
+            s.daeti_update_conductivity_nodal(d_node)
+            s.daeti_update_cell_params(params)
+        except binding.DaetiError as e:
+            if e.code != binding.EUNSTABLE:
+                raise
+            problem.close()
+            s = None
+    if s is None:
+        s = problem._solver = _prepare(problem, d_node, params)
+    return s.daeti_adjoint(problem.sensors, problem.data, problem.n_steps, problem.sample_every,
+                           problem.n_slots, 0, nodal=True)
 
 
 class MonodomainMisfit(torch.autograd.Function):

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "daeti_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(daeti_tuning)]),
     "daeti_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "daeti_time_launches": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
+    "daeti_update_cell_params": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
     "daeti_get_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _I64P]),
     "daeti_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
     "daeti_update_conductivity": (ctypes.c_int, [_VP, ctypes.c_int64, _DP, _DP, _DP]),
@@ -410,6 +411,10 @@ class Solver:
             setattr(t, f, int(cur[f]))
         self._check(self.lib.daeti_set_tuning(self.ctx, ctypes.byref(t)))
         return self.daeti_get_tuning()
+
+    def daeti_update_cell_params(self, params):
+        p = _f64(params).reshape(-1)
+        self._check(self.lib.daeti_update_cell_params(self.ctx, _ptr(p, ctypes.c_double), p.shape[0]))
 
     def daeti_time_launches(self, which, count=20):
         """ms per launch of `count` back-to-back launches in a graph (changes the state)."""

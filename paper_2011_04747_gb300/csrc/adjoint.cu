@@ -69,6 +69,13 @@ struct AdjointBuffers {
 };
 
 namespace daeti_host {
+void drop_adjoint_graph(daeti_ctx* c) {
+    if (c->adj && c->adj->graph) {
+        cudaGraphExecDestroy(c->adj->graph);
+        c->adj->graph = nullptr;
+    }
+}
+
 void free_adjoint(daeti_ctx* c) {
     if (!c->adj) return;
     if (c->adj->graph) cudaGraphExecDestroy(c->adj->graph);

@@ -925,6 +925,32 @@ int daeti_update_conductivity(daeti_ctx* c, int64_t n_elem, const double* d_long
     return upload_operator(c, tab, table, K);
 }
 
+int daeti_update_cell_params(daeti_ctx* c, const double* params, int n_params) {
+    if (!c) return DAETI_EINVAL;
+    if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");
+    if (!params) return fail(c, DAETI_EINVAL, "null parameters");
+    if (c->model == DAETI_MODEL_MS) {
+        if (n_params != 5) return fail(c, DAETI_EINVAL, "Mitchell-Schaeffer takes 5 parameters");
+        for (int i = 0; i < 4; ++i)
+            if (!(params[i] > 0) || !std::isfinite(params[i])) return fail(c, DAETI_EINVAL, "time constants must be > 0");
+        if (!std::isfinite(params[4])) return fail(c, DAETI_EINVAL, "v_gate must be finite");
+    } else {
+        if (n_params != 1 || !(params[0] == 0.0 || params[0] == 1.0 || params[0] == 2.0))
+            return fail(c, DAETI_EINVAL, "TP06 takes 1 parameter: celltype 0, 1 or 2");
+        if (!c->ctypes.empty()) return fail(c, DAETI_EINVAL, "the cell types are given per node");
+    }
+    int rc = daeti_synchronize(c);
+    if (rc) return rc;
+    c->params.assign(params, params + n_params);
+    if (c->model == DAETI_MODEL_MS)
+        for (int i = 0; i < 5; ++i) c->margs.ms[i] = params[i];
+    else
+        c->margs.celltype = (int)params[0];
+    drop_graphs(c);            // launch arguments hold the model's rates
+    drop_adjoint_graph(c);
+    return DAETI_OK;
+}
+
 int daeti_get_stability(daeti_ctx* c, double* dt_s, double* lambda_max, int* l, int* k_max, double* dt_eff) {
     if (!c) return DAETI_EINVAL;
     if (!c->prepared) return fail(c, DAETI_ESTATE, "not prepared");

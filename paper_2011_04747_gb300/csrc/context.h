@@ -91,6 +91,7 @@ int dalloc(daeti_ctx* c, void** p, size_t bytes);
 size_t rsize(const daeti_ctx* c);
 int upload_real(daeti_ctx* c, void* dst, const double* src, int64_t count);
 void free_adjoint(daeti_ctx* c);
+void drop_adjoint_graph(daeti_ctx* c);   // the captured gradient sweep (kernel arguments changed)
 // Nodes of element e (returns their count); element means of a nodal field.
 int elem_nodes(const daeti_ctx* c, int64_t e, int64_t* out);
 void elem_means(const daeti_ctx* c, const double* nodal, std::vector<double>& out);

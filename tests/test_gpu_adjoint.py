@@ -192,6 +192,26 @@ def test_autograd_wrapper():
     assert abs(float(loss.detach()) - lo) <= 1e-9 * lo
     assert _rel(d_node.grad.numpy(), 2.0 * adjoint.nodal_gradient(conn, ge, wl.n_nodes)) <= 1e-8
     assert abs(float(tau.grad) - 2.0 * gt) <= 1e-8 * abs(2.0 * gt)
+    # later calls reuse the prepared solver (new D and tau_close by updates) ...
+    for scale, tau_v, prepares in ((1.2, 140.0, 1), (1.1, 160.0, 1), (30.0, 150.0, 2)):
+        d2 = torch.tensor(d_node.detach().numpy() * scale, requires_grad=True)
+        t2 = torch.tensor(tau_v, dtype=torch.float64, requires_grad=True)
+        loss2 = MonodomainMisfit.apply(d2, t2, p)
+        loss2.backward()
+        params = list(wl.model_params)
+        params[3] = tau_v
+        # ... with the prepared l while it is stable (D x 30 needs a new prepare)
+        assert p.prepares == prepares
+        l_used = p._solver.daeti_get_stability()["l"]
+        d2e = adjoint.element_d_from_nodes(conn, d2.detach().numpy())
+        o2 = adjoint.MSAdjointGrid(2, wl.n, wl.h, d2e, params, wl.stimuli, l_override=l_used)
+        if prepares == 2:
+            assert l_used == adjoint.MSAdjointGrid(2, wl.n, wl.h, d2e, params, wl.stimuli).l > 1
+        lo2, ge2, gt2, _ = o2.gradient(n_steps, sensors, 10, data)
+        assert abs(float(loss2.detach()) - lo2) <= 1e-9 * lo2
+        assert _rel(d2.grad.numpy(), adjoint.nodal_gradient(conn, ge2, wl.n_nodes)) <= 1e-8
+        assert abs(float(t2.grad) - gt2) <= 1e-8 * abs(gt2)
+    p.close()
 
 
 def test_adjoint_graph_replay_repeats_exactly():
