@@ -7,7 +7,6 @@
 #pragma once
 
 #include "common.cuh"
-#include "pack.cuh"
 
 namespace daeti {
 
@@ -60,26 +59,6 @@ struct TP06Consts {
 struct TP06Params {
     int celltype;  // 0 endo, 1 epi, 2 mid
     int gate_rl;   // 1 Rush-Larsen, 0 forward Euler gates (selects the RL instance of tp06_substep)
-    int celltype2; // the second node's type when two nodes are integrated together (F2)
-};
-
-// Per-node choices of the sub-step, for one node (float, double) or a node
-// pair (F2, in pack.cuh): a value by cell type, and the two branches of a
-// piecewise rate taken per node (a pair whose nodes fall on different sides
-// evaluates both and selects per lane).
-template <typename R>
-struct Lanes {
-    static __device__ __forceinline__ R by_type(const TP06Params& p, double endo, double epi, double mid) {
-        return (R)(p.celltype == 0 ? endo : (p.celltype == 1 ? epi : mid));
-    }
-    static __device__ __forceinline__ int endo_mask(const TP06Params& p) { return p.celltype == 0 ? 1 : 0; }
-    static __device__ __forceinline__ int ge_mask(R a, double b) { return a >= (R)b ? 1 : 0; }
-    static constexpr int all = 1;
-    template <class A, class B>
-    static __device__ __forceinline__ void branch2(int mask, const A& on, const B& off, R& o0, R& o1) {
-        if (mask) on(o0, o1);
-        else off(o0, o1);
-    }
 };
 
 template <typename R>
@@ -123,8 +102,8 @@ __device__ __forceinline__ double x_over_expm1<double>(double x, double e) {
 // written as 2^(a' V + b') with the constants scaled by log2(e) at compile
 // time, one FMA and one SFU operation each.
 // Returns dV/dt of the sub-step (mV/ms).
-template <typename R, bool RL = true, typename CP = float*>
-__device__ __forceinline__ R tp06_substep(TP06State<R>& x, CP cv, R dt, R J, const TP06Params& prm) {
+template <typename R, bool RL = true>
+__device__ __forceinline__ R tp06_substep(TP06State<R>& x, float* cv, R dt, R J, const TP06Params& prm) {
     typedef TP06Consts C;
     typedef Fm<R> M;
     const R one = (R)1;
@@ -149,8 +128,8 @@ __device__ __forceinline__ R tp06_substep(TP06State<R>& x, CP cv, R dt, R J, con
     const R ak = fma((R)0.1, e3, (R)0.1);
     const R xk1 = M::dv(ak, fma(e1 + e2, one + e0, ak));
 
-    const R Gks = Lanes<R>::by_type(prm, 0.392, 0.392, 0.098);
-    const R Gto = Lanes<R>::by_type(prm, 0.073, 0.294, 0.294);
+    const R Gks = prm.celltype == 2 ? (R)0.098 : (R)0.392;
+    const R Gto = prm.celltype == 0 ? (R)0.073 : (R)0.294;
 
     const R INa = (R)C::GNa * x.m * x.m * x.m * x.h * x.j * (V - ENa);
     // I_CaL = G d f f2 fCass 4 (V-15) F^2/RT (0.25 CaSS e^x - Cao)/(e^x - 1), x = 2 (V-15) F/RT
@@ -215,23 +194,21 @@ __device__ __forceinline__ R tp06_substep(TP06State<R>& x, CP cv, R dt, R J, con
         const R eh = one + EXL(V, 1.0 / 7.43, 71.55 / 7.43);
         const R hinf = M::dv(one, eh * eh);
         R rh, rj;
-        auto above = [&](R& r_h, R& r_j) {
+        if (V >= (R)-40) {
             // a_h = a_j = 0
-            r_h = M::dv((R)(0.77 / 0.13), one + EXL(V, -1.0 / 11.1, -10.66 / 11.1));
-            r_j = M::dv(EXL(V, 0.057, -0.5108256237659907), fma((R)0.04076220397836621, iE1, one));   // ln 0.6; e^{-3.2}
-        };
-        auto below = [&](R& r_h, R& r_j) {
-            r_h = EXL(V, -1.0 / 6.8, -80.0 / 6.8 - 2.864704011147587) +   // ln 0.057
-                  EXL(V, 0.079, 0.9932517730102834) +                  // ln 2.7
-                  EXL(V, 0.3485, 12.644327576461329);                  // ln 3.1e5
+            rh = M::dv((R)(0.77 / 0.13), one + EXL(V, -1.0 / 11.1, -10.66 / 11.1));
+            rj = M::dv(EXL(V, 0.057, -0.5108256237659907), fma((R)0.04076220397836621, iE1, one));   // ln 0.6; e^{-3.2}
+        } else {
+            rh = EXL(V, -1.0 / 6.8, -80.0 / 6.8 - 2.864704011147587) +   // ln 0.057
+                 EXL(V, 0.079, 0.9932517730102834) +                  // ln 2.7
+                 EXL(V, 0.3485, 12.644327576461329);                  // ln 3.1e5
             const R da = one + EXL(V, 0.311, 0.311 * 79.23);
             const R db = one + EXL(V, -0.1378, -0.1378 * 40.14);
             const R na = -(EXL(V, 0.2444, 10.1436062080563) + EXL(V, -0.04391, -11.877056709585416)) *
                          (V + (R)37.78);   // ln 2.5428e4, ln 6.948e-6
             const R nb = EXL(V, -0.01052, -3.719751117781023);   // ln 0.02424
-            r_j = M::dv(fma(na, db, nb * da), da * db);
-        };
-        Lanes<R>::branch2(Lanes<R>::ge_mask(V, -40.0), above, below, rh, rj);
+            rj = M::dv(fma(na, db, nb * da), da * db);
+        }
         x.h = gate_rate<RL>(x.h, hinf, rh, dt, ndtl);
         x.j = gate_rate<RL>(x.j, hinf, rj, dt, ndtl);
     }
@@ -272,19 +249,17 @@ __device__ __forceinline__ R tp06_substep(TP06State<R>& x, CP cv, R dt, R J, con
     }
     {
         R inf, rate;
-        auto endo = [&](R& g_inf, R& g_rate) {
-            g_inf = M::dv(one, fma((R)270.42640742615254, E2, one));                  // e^{5.6}
+        if (prm.celltype == 0) {
+            inf = M::dv(one, fma((R)270.42640742615254, E2, one));                    // e^{5.6}
             const R v67 = V + (R)67;
-            g_rate = M::dv(one, EXQ(v67, -0.001, 6.907755278982137) + (R)8);   // ln 1000
-        };
-        auto other = [&](R& g_inf, R& g_rate) {
-            g_inf = M::dv(one, fma((R)54.598150033144236, E2, one));                  // e^{4}
+            rate = M::dv(one, EXQ(v67, -0.001, 6.907755278982137) + (R)8);   // ln 1000
+        } else {
+            inf = M::dv(one, fma((R)54.598150033144236, E2, one));                    // e^{4}
             const R v45 = V + (R)45;
             const R dd = fma((R)0.01831563888873418, E2, one);                        // e^{-4}
             // tau = 85 e + 5/dd + 3
-            g_rate = M::dv(dd, fma(EXQ(v45, -1.0 / 320.0, 4.442651256490317) + (R)3, dd, (R)5));   // ln 85
-        };
-        Lanes<R>::branch2(Lanes<R>::endo_mask(prm), endo, other, inf, rate);
+            rate = M::dv(dd, fma(EXQ(v45, -1.0 / 320.0, 4.442651256490317) + (R)3, dd, (R)5));   // ln 85
+        }
         x.s = gate_rate<RL>(x.s, inf, rate, dt, ndtl);
     }
     const R iE05 = EXL(V, -0.05, 0.0);   // e^{-0.05 V}
@@ -335,53 +310,6 @@ __device__ __forceinline__ R tp06_substep(TP06State<R>& x, CP cv, R dt, R J, con
     x.Ki = fma(dt, dKi, x.Ki);
     x.RR = fma(dt, dRR, x.RR);
     return dV;
-}
-
-// ------------------------------------------------------------ node pairs
-// The choices of tp06_substep for two nodes (lane 0: celltype, lane 1:
-// celltype2).  A branch both nodes take is evaluated once; otherwise both
-// are evaluated and each lane keeps its own.
-template <>
-struct Lanes<F2> {
-    static __device__ __forceinline__ F2 by_type(const TP06Params& p, double endo, double epi, double mid) {
-        auto v = [&](int ct) { return (float)(ct == 0 ? endo : (ct == 1 ? epi : mid)); };
-        return F2(v(p.celltype), v(p.celltype2));
-    }
-    static __device__ __forceinline__ int endo_mask(const TP06Params& p) {
-        return (p.celltype == 0 ? 1 : 0) | (p.celltype2 == 0 ? 2 : 0);
-    }
-    static __device__ __forceinline__ int ge_mask(F2 a, double b) { return daeti::ge_mask(a, (float)b); }
-    template <class A, class B>
-    static __device__ __forceinline__ void branch2(int mask, const A& on, const B& off, F2& o0, F2& o1) {
-        if (mask == 3) {
-            on(o0, o1);
-        } else if (mask == 0) {
-            off(o0, o1);
-        } else {
-            F2 a0, a1, b0, b1;
-            on(a0, a1);
-            off(b0, b1);
-            o0 = select(mask, a0, b0);
-            o1 = select(mask, a1, b1);
-        }
-    }
-};
-
-template <>
-__device__ __forceinline__ F2 x_over_expm1<F2>(F2 x, F2 e) {
-    return F2(x_over_expm1<float>(x.lo(), e.lo()), x_over_expm1<float>(x.hi(), e.hi()));
-}
-
-// v += d with Kahan compensation per lane (the float add_comp in each lane).
-__device__ __forceinline__ void add_comp(F2& v, F2* c, F2 d) {
-    if (c) {
-        const F2 y = d - *c;
-        const F2 t = v + y;
-        *c = (t - v) - y;
-        v = t;
-    } else {
-        v = v + d;
-    }
 }
 
 }  // namespace daeti

@@ -9,8 +9,6 @@
 // launch.
 #pragma once
 
-#include <type_traits>
-
 #include "cells.cuh"
 #include "diffops.cuh"
 
@@ -139,113 +137,6 @@ __device__ __forceinline__ void react_node(const ReactArgs<R>& a, int i, int k, 
     if (KAHAN) a.C[i] = c;
 }
 
-// Step A of two TP06 nodes (float) with the same k in the packed FP32
-// instructions: lane 0 node i0, lane 1 node i1 (i1 == i0: one node, computed
-// in both lanes and stored once).  v0, c0: the nodes' V and Kahan term at the
-// start of the step.  Each lane performs the scalar sub-step's operations.
-template <bool KAHAN, bool EXT>
-__device__ __forceinline__ void react_pair_tp06(const ReactArgs<float>& a, int i0, int i1, int k, double tn,
-                                                bool any_stim, float v0a, float v0b, float c0a, float c0b) {
-    const unsigned m0 = any_stim ? a.stim_mask[i0] : 0u;
-    const unsigned m1 = any_stim ? a.stim_mask[i1] : 0u;
-    const double dt_ar = a.dtk[k];
-    const F2 h(a.dtkr[k]);
-    F2 c(c0a, c0b);
-    F2* cp = KAHAN ? &c : nullptr;
-    TP06State<F2> x;
-    const float* const S0 = a.S + (size_t)(i0 >> 5) * (18 * 32) + (i0 & 31);
-    const float* const S1 = a.S + (size_t)(i1 >> 5) * (18 * 32) + (i1 & 31);
-    x.V = F2(v0a, v0b);
-    x.Cai = F2(S0[0 * 32], S1[0 * 32]);
-    x.CaSR = F2(S0[1 * 32], S1[1 * 32]);
-    x.CaSS = F2(S0[2 * 32], S1[2 * 32]);
-    x.Nai = F2(S0[3 * 32], S1[3 * 32]);
-    x.Ki = F2(S0[4 * 32], S1[4 * 32]);
-    x.m = F2(S0[5 * 32], S1[5 * 32]);
-    x.h = F2(S0[6 * 32], S1[6 * 32]);
-    x.j = F2(S0[7 * 32], S1[7 * 32]);
-    x.xr1 = F2(S0[8 * 32], S1[8 * 32]);
-    x.xr2 = F2(S0[9 * 32], S1[9 * 32]);
-    x.xs = F2(S0[10 * 32], S1[10 * 32]);
-    x.r = F2(S0[11 * 32], S1[11 * 32]);
-    x.s = F2(S0[12 * 32], S1[12 * 32]);
-    x.d = F2(S0[13 * 32], S1[13 * 32]);
-    x.f = F2(S0[14 * 32], S1[14 * 32]);
-    x.f2 = F2(S0[15 * 32], S1[15 * 32]);
-    x.fcass = F2(S0[16 * 32], S1[16 * 32]);
-    x.RR = F2(S0[17 * 32], S1[17 * 32]);
-    TP06Params tp = a.tp;
-    tp.celltype2 = tp.celltype;
-    if (EXT && a.ctype) {
-        tp.celltype = a.ctype[i0];
-        tp.celltype2 = a.ctype[i1];
-    }
-    for (int s = 0; s < k; ++s) {
-        const double ts = tn + (double)s * dt_ar;
-        const F2 J(m0 ? stim_current<float>(m0, a.stims, ts) : 0.f, m1 ? stim_current<float>(m1, a.stims, ts) : 0.f);
-        const F2 dv = tp.gate_rl ? tp06_substep<F2, true, F2*>(x, cp, h, J, tp) : tp06_substep<F2, false, F2*>(x, cp, h, J, tp);
-        if (EXT && a.rrate && s == k - 1) {
-            a.rrate[i0] = dv.lo();
-            a.rrate[i1] = dv.hi();
-        }
-    }
-    auto store = [&](int i, bool hi) {
-        float* const S = a.S + (size_t)(i >> 5) * (18 * 32) + (i & 31);
-        auto ln = [&](const F2& v) { return hi ? v.hi() : v.lo(); };
-        a.V[i] = ln(x.V);
-        S[0 * 32] = ln(x.Cai);
-        S[1 * 32] = ln(x.CaSR);
-        S[2 * 32] = ln(x.CaSS);
-        S[3 * 32] = ln(x.Nai);
-        S[4 * 32] = ln(x.Ki);
-        S[5 * 32] = ln(x.m);
-        S[6 * 32] = ln(x.h);
-        S[7 * 32] = ln(x.j);
-        S[8 * 32] = ln(x.xr1);
-        S[9 * 32] = ln(x.xr2);
-        S[10 * 32] = ln(x.xs);
-        S[11 * 32] = ln(x.r);
-        S[12 * 32] = ln(x.s);
-        S[13 * 32] = ln(x.d);
-        S[14 * 32] = ln(x.f);
-        S[15 * 32] = ln(x.f2);
-        S[16 * 32] = ln(x.fcass);
-        S[17 * 32] = ln(x.RR);
-        if (KAHAN) a.C[i] = ln(c);
-    };
-    store(i0, false);
-    if (i1 != i0) store(i1, true);
-}
-
-// Start-of-step V and Kahan term of node i: the fused diffusion sub-step, or
-// the current buffer.
-template <typename R, bool KAHAN, int DIM, bool PAD, bool EXT>
-__device__ __forceinline__ void step_start(const ReactArgs<R>& a, const OpView<R>& op, int i, R& v0, float& c0) {
-    c0 = 0.f;
-    if (DIM >= 0) {
-        diffuse_node<R, (DIM < 0 ? 0 : DIM), KAHAN, PAD, EXT>(op, a.vsrc, a.csrc, i, v0, c0);
-    } else {
-        v0 = a.V[i];
-        if (KAHAN) c0 = a.C[i];
-    }
-}
-
-// Two items of a thread (float TP06): node i0 with k0 and, when has1, node i1
-// with k1; equal k are integrated as one pair, different k one at a time.
-template <bool KAHAN, int DIM, bool PAD, bool EXT>
-__device__ __forceinline__ void react_two(const ReactArgs<float>& a, const OpView<float>& op, int i0, int k0, bool has1,
-                                          int i1, int k1, double tn, bool any_stim) {
-    float va, vb = 0.f, ca, cb = 0.f;
-    step_start<float, KAHAN, DIM, PAD, EXT>(a, op, i0, va, ca);
-    if (has1) step_start<float, KAHAN, DIM, PAD, EXT>(a, op, i1, vb, cb);
-    if (has1 && k0 == k1) {
-        react_pair_tp06<KAHAN, EXT>(a, i0, i1, k0, tn, any_stim, va, vb, ca, cb);
-    } else {
-        react_pair_tp06<KAHAN, EXT>(a, i0, i0, k0, tn, any_stim, va, va, ca, ca);
-        if (has1) react_pair_tp06<KAHAN, EXT>(a, i1, i1, k1, tn, any_stim, vb, vb, cb, cb);
-    }
-}
-
 // Node of item t.  Buckets are laid out largest k first: bucket k holds the
 // items off[k] <= t < off[k-1], with off[k] = sum of the lengths of buckets
 // j > k non-increasing in k and off[j] = 0 for j >= kmax, so k is the
@@ -283,16 +174,8 @@ __device__ __forceinline__ void react_item(const ReactArgs<R>& a, const OpView<R
 // trade spills against occupancy.  DIM >= 0 fuses one diffusion sub-step
 // before the reaction (0: SELL-32, 2/3: stencil; PAD: V buffers with a ghost
 // margin, no per-neighbour boundary tests).
-// Resident 128-thread blocks per SM the registers must allow: the float TP06
-// instances integrate two nodes per thread and take half of MINB.
-template <typename R, int MODEL, int MINB>
-constexpr int react_min_blocks() {
-    return (MODEL == M_TP06 && std::is_same<R, float>::value) ? (MINB / 2 > 2 ? MINB / 2 : 2) : MINB;
-}
-
 template <typename R, int MODEL, bool KAHAN, int MINB, int DIM, bool PAD, bool EXT>
-__global__ void __launch_bounds__(128, (react_min_blocks<R, MODEL, MINB>())) reaction_kernel(ReactArgs<R> a,
-                                                                                           OpView<R> op) {
+__global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpView<R> op) {
     __shared__ int off[DAETI_MAX_K];
     __shared__ double sh_tn;
     __shared__ int sh_stim;
@@ -351,38 +234,6 @@ __global__ void __launch_bounds__(128, (react_min_blocks<R, MODEL, MINB>())) rea
     __syncthreads();
     const double tn = sh_tn;
     const bool any_stim = sh_stim != 0;
-    if constexpr (MODEL == M_TP06 && std::is_same<R, float>::value) {
-        // two consecutive items per thread (the grid covers n / 2 threads)
-        if (!a.lists) {
-            const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-            if (t < a.n)
-                react_two<KAHAN, DIM, PAD, EXT>(a, op, t, a.kk[t], t + 1 < a.n, t + 1, t + 1 < a.n ? a.kk[t + 1] : 0,
-                                                tn, any_stim);
-            return;
-        }
-        const int total = sh_total;
-        const int t = 2 * (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31));
-        if (sh_uni) {
-            if (t < total) react_two<KAHAN, DIM, PAD, EXT>(a, op, t, sh_uni, t + 1 < total, t + 1, sh_uni, tn, any_stim);
-        } else if (!sh_listed) {
-            const int k0 = t < total ? (int)a.kk[t] : 0;
-            const int k1 = t + 1 < total ? (int)a.kk[t + 1] : 0;
-            if (a.substeps) {
-                unsigned long long w = (unsigned long long)(k0 + k1);
-#pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
-                if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.substeps, w);
-            }
-            if (t < total) react_two<KAHAN, DIM, PAD, EXT>(a, op, t, k0, t + 1 < total, t + 1, k1, tn, any_stim);
-        } else if (t < total) {
-            int k0, k1 = 0, i1 = 0;
-            const int i0 = item_node(a.lists, a.n, off, t, k0);
-            const bool has1 = t + 1 < total;
-            if (has1) i1 = item_node(a.lists, a.n, off, t + 1, k1);
-            react_two<KAHAN, DIM, PAD, EXT>(a, op, i0, k0, has1, i1, k1, tn, any_stim);
-        }
-        return;
-    }
     if (!a.lists) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
         if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, a.kk[t], tn, any_stim);
