@@ -20,4 +20,5 @@ from .workloads import (  # noqa: F401
     batch_tissues,
     ms_adjoint_2d,
     MS_DEFAULT_PARAMS,
+    S1S2_S2_TIME,
 )

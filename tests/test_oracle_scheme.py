@@ -195,3 +195,20 @@ def test_ostar_step_reduction():
     assert abs(s.dt - 0.1 / math.ceil(0.1 / s.dt_s)) < 1e-15 and s.dt <= s.dt_s and s.l == 1
     d = scheme.simulation_from_workload(wl, scheme="daeti")
     assert d.l == 3 and abs(d.dt_ad - 0.1 / 6) < 1e-15
+
+
+def test_s1s2_time_is_the_scan_choice():
+    """The tet slab's S2 time is the S2 time of the oracle's 10 ms scan after
+    which activity persisted at 1000 ms (tests/golden/s1s2_scan_oracle.json,
+    written by make_s1s2_scan.py from oracle runs), and the recorded traces
+    show it re-entering: the active-node count falls and rises again."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "s1s2_scan_oracle.json")))
+    assert g["s2_with_activity_at_1000ms"] == [int(I.S1S2_S2_TIME)]
+    a = np.array(g["runs"][str(int(I.S1S2_S2_TIME))])
+    assert a[-1] > 0 and (a[55:] < 0.6 * a[55:].max()).any()
+    for s2, trace in g["runs"].items():
+        if int(s2) != int(I.S1S2_S2_TIME):
+            assert trace[-1] == 0, s2
