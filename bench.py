@@ -665,6 +665,46 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
     return line
 
 
+def bench_tets(args, env):
+    """The pathophysiological workload as stated: 2.06 M-node jittered tet slab
+    (30 % fibrosis, central scar), S1-S2 cross-field protocol, 1000 ms in
+    FP32 with compensated V.  Beside the timed runs: the number of nodes above
+    -40 mV every 50 ms (is activity still present at 1000 ms?) and the FP32
+    run against the FP64 path in lockstep, V of every node every 1 ms."""
+    import numpy as np
+
+    import inputs
+
+    wl = inputs.tet_slab_3d(t_end=1000.0)
+    line = bench_simple(args, env, wl, "tp06_tet_slab_201x201x51_1000ms", t_end=1000.0, steps_sample=2)
+    binding = env.binding
+    s32 = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=args.graph_steps)
+    s64 = binding.solver_from_workload(wl, precision="fp64", graph_steps=args.graph_steps)
+    for s in (s32, s64):
+        s.daeti_set_stream(env.stream)
+    active, worst, worst_t = [], 0.0, 0.0
+    for j in range(1, 1001):
+        s32.daeti_advance(float(j))
+        s64.daeti_advance(float(j))
+        v32, v64 = s32.daeti_read_v(), s64.daeti_read_v()
+        d = float(np.max(np.abs(v32 - v64)))
+        if d > worst:
+            worst, worst_t = d, float(j)
+        if j % 50 == 0:
+            active.append({"t_ms": j, "nodes_above_-40mV": int((v32 > -40.0).sum())})
+    a32, a64 = s32.daeti_read_activation(), s64.daeti_read_activation()
+    s32.close()
+    s64.close()
+    both = (a32 >= 0) & (a64 >= 0)
+    line["s2_time_ms"] = float(wl.stimuli[1].t_start)
+    line["activity"] = active
+    line["activity_at_1000ms"] = active[-1]["nodes_above_-40mV"]
+    line["fp32_vs_fp64"] = {"max_abs_dv_mv_every_1ms": worst, "at_ms": worst_t,
+                            "max_abs_dact_ms": float(np.abs(a32[both] - a64[both]).max()) if both.any() else None,
+                            "same_activated_set": bool(np.array_equal(a32 >= 0, a64 >= 0))}
+    return line
+
+
 def bench_batch(args, env):
     """512 uneven tissues in one batched launch sequence vs the same tissues run one by one."""
     import inputs
@@ -687,7 +727,8 @@ def bench_batch(args, env):
         batch.daeti_batch_advance(1.0)        # graphs captured, caches warm; 1 ms of the run
         secs[bucket] = env.timed(lambda: batch.daeti_batch_advance(t_end), 1, 0)
         batch.close()
-    sec_b = secs[1]
+    sec_b = min(secs.values())      # the faster of the two (an autotuner's pick)
+    best_bucket = 1 if secs[1] <= secs[0] else 0
     solvers = [binding.solver_from_workload(w, precision="fp32_kahan", graph_steps=args.graph_steps) for w in wls]
     for s in solvers:
         s.daeti_set_stream(env.stream)
@@ -707,6 +748,8 @@ def bench_batch(args, env):
             "config": {"workload": "batch_512_tissues_300ms", "nodes": n_nodes, "strang_steps": n_steps,
                        "timed": "1 ms .. 300 ms of each run (the first 1 ms captures the graphs)"},
             "sequential": {"value": n_nodes * n_steps / sec_s, "ms": sec_s * 1e3},
+            "k_lists_tp06": bool(best_bucket),
+            "with_k_lists": {"value": env.world * n_nodes * n_steps / secs[1], "ms": secs[1] * 1e3},
             "without_k_lists": {"value": env.world * n_nodes * n_steps / secs[0], "ms": secs[0] * 1e3},
             "batched_over_sequential": sec_s / sec_b}
 
@@ -787,8 +830,7 @@ def run_ours(args):
         line = bench_simple(args, env, inputs.aniso_sheet_2d(t_end=50.0), "tp06_sheet_501x501_h0.01_50ms",
                             t_end=50.0, steps_sample=5)
     elif wk == "tets":
-        line = bench_simple(args, env, inputs.tet_slab_3d(t_end=50.0), "tp06_tet_slab_201x201x51_50ms",
-                            t_end=50.0, steps_sample=2)
+        line = bench_tets(args, env)
     elif wk == "batch":
         line = bench_batch(args, env)
     elif wk == "accuracy":
