@@ -284,9 +284,6 @@ class Env:
         return self.max_over_ranks(sum(times) / len(times))
 
 
-ROOF_OPS = 450.0   # counted arithmetic operations per TP06 node sub-step (daeti_kernel_work)
-
-
 def _launch_samples(s, ck, n_steps, dt, every_ms=10.0, count=20):
     """Reaction and synchronising-diffusion launch durations (us) at states of
     one run, by daeti_time_launches, with the run's sub-steps per launch."""
@@ -535,14 +532,15 @@ def bench_slab(args, env):
     # CUDA events at the run's own state (saved before, restored after; one
     # step is re-run after a restore so that the bucketing mode is the run's)
     samples = _launch_samples(s32, ck, n_steps, wl.dt)
-    r_ops = sum(ROOF_OPS * sm["substeps_per_launch"] for sm in samples)
+    roof_ops = s32.daeti_kernel_work(0)[1]      # counted operations per node sub-step
+    r_ops = sum(roof_ops * sm["substeps_per_launch"] for sm in samples)
     r_s = sum(sm["reaction_us"] for sm in samples) * 1e-6
     mhz = clocks.get("sm_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
     roof.update({"achieved": r_ops / r_s / 1e12, "frac": r_ops / r_s / 1e12 / peak,
                  "avg_launch_us": r_s * 1e6 / len(samples),
                  "substeps_per_launch": sum(sm["substeps_per_launch"] for sm in samples) / len(samples),
-                 "xu_frac": TP06_XU_PER_SUBSTEP * r_ops / ROOF_OPS / r_s / (SM_COUNT * XU_LANES_PER_SM * mhz * 1e6),
+                 "xu_frac": TP06_XU_PER_SUBSTEP * r_ops / roof_ops / r_s / (SM_COUNT * XU_LANES_PER_SM * mhz * 1e6),
                  "timing": ("graph replays of 20 back-to-back reaction launches at the run's state every 10 ms "
                             "(50 samples), CUDA events around each replay on the launching stream; "
                             "event_nodes_frac: event-record nodes around every launch of the 500 ms run; "
@@ -858,6 +856,8 @@ def profile_run(args):
                                      bucket_k=bool(args.bucket))
     if args.diff_block >= 0:
         s.daeti_set_tuning(diff_block=args.diff_block)
+    if args.fuse_diffusion >= 0:
+        s.daeti_set_tuning(fuse_diffusion=args.fuse_diffusion)
     if args.profile_from > 0:
         s.daeti_advance(args.profile_from)
     s.daeti_advance(args.profile_from + args.profile_run)
@@ -884,6 +884,9 @@ def main():
     ap.add_argument("--diff-block", type=int, default=-1,
                     help="with --profile-run: diffusion launch shape (0 = 2D tiles / 3D register z-march, "
                          "256 = one thread per node; default: the library's)")
+    ap.add_argument("--fuse-diffusion", type=int, default=-1,
+                    help="with --profile-run: 1 = last step-I diffusion sub-step inside the reaction launch, "
+                         "0 = its own launch (default: the library's)")
     ap.add_argument("--profile-from", type=float, default=0.0,
                     help="with --profile-run: first advance to this time (ms), e.g. into the plateau "
                          "(60) or the resting phase (150)")

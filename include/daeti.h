@@ -237,8 +237,7 @@ int daeti_save_state(daeti_ctx* ctx, void* buf, int64_t buf_bytes);
 int daeti_load_state(daeti_ctx* ctx, const void* buf, int64_t buf_bytes);
 
 /* Total node reaction sub-steps (sum of k over nodes and steps) since the
- * last init_state/load_state, counted while nodes are grouped by k
- * (bucket_k = 1); waits for enqueued work. */
+ * last init_state/load_state; waits for enqueued work. */
 int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
 
 /* Launch shapes (set by the caller or an autotuner; results do not depend on

@@ -235,8 +235,16 @@ __global__ void __launch_bounds__(128, MINB) reaction_kernel(ReactArgs<R> a, OpV
     const double tn = sh_tn;
     const bool any_stim = sh_stim != 0;
     if (!a.lists) {
+        // no bucketing: node t with its own k (the sub-step count summed per warp)
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, a.kk[t], tn, any_stim);
+        const int kt = t < a.n ? (int)a.kk[t] : 0;
+        if (a.substeps) {
+            unsigned long long w = (unsigned long long)kt;
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+            if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.substeps, w);
+        }
+        if (t < a.n) react_item<R, MODEL, KAHAN, DIM, PAD, EXT>(a, op, t, kt, tn, any_stim);
         return;
     }
     const int total = sh_total;

@@ -31,8 +31,16 @@ def test_full_tet_slab_fp32_against_fp64():
     assert np.all(np.isfinite(v32))
     assert float(np.max(np.abs(v32 - v64))) <= 2.0
     da, same, n_act = act_error(a32, a64)
-    assert same and da <= 0.5
+    assert da <= 0.5
     assert n_act > 0                                 # the S1 front has started
+    # Activated sets: equal, except nodes on the front whose V at the last
+    # synchronisation lies within the FP32 V tolerance of the threshold (there
+    # a 2 mV difference decides whether -40 mV has been crossed yet).
+    differ = (a32 >= 0) != (a64 >= 0)
+    vth = wl.v_threshold if wl.v_threshold is not None else -40.0
+    near = np.abs(v64 - vth) <= 2.0
+    assert not np.any(differ & ~near), (int(differ.sum()), int((differ & ~near).sum()))
+    assert int(differ.sum()) <= max(1, n_act // 1000)
 
 
 def test_full_batch_sampled_tissues():
