@@ -680,16 +680,23 @@ def bench_tets(args, env):
     s64 = binding.solver_from_workload(wl, precision="fp64", graph_steps=args.graph_steps)
     for s in (s32, s64):
         s.daeti_set_stream(env.stream)
-    active, worst, worst_t = [], 0.0, 0.0
+    active, worst, worst_t, first_2mv, worst_50 = [], 0.0, 0.0, None, 0.0
     for j in range(1, 1001):
         s32.daeti_advance(float(j))
         s64.daeti_advance(float(j))
         v32, v64 = s32.daeti_read_v(), s64.daeti_read_v()
-        d = float(np.max(np.abs(v32 - v64)))
+        dv = np.abs(v32 - v64)
+        d = float(np.max(dv))
+        worst_50 = max(worst_50, d)
         if d > worst:
             worst, worst_t = d, float(j)
+        if first_2mv is None and d > 2.0:
+            first_2mv = float(j)
         if j % 50 == 0:
-            active.append({"t_ms": j, "nodes_above_-40mV": int((v32 > -40.0).sum())})
+            active.append({"t_ms": j, "nodes_above_-40mV": int((v32 > -40.0).sum()),
+                           "max_abs_dv_mv_last_50ms": round(worst_50, 4),
+                           "nodes_dv_above_2mV": int((dv > 2.0).sum())})
+            worst_50 = 0.0
     a32, a64 = s32.daeti_read_activation(), s64.daeti_read_activation()
     s32.close()
     s64.close()
@@ -698,6 +705,7 @@ def bench_tets(args, env):
     line["activity"] = active
     line["activity_at_1000ms"] = active[-1]["nodes_above_-40mV"]
     line["fp32_vs_fp64"] = {"max_abs_dv_mv_every_1ms": worst, "at_ms": worst_t,
+                            "first_ms_above_2mV": first_2mv,
                             "max_abs_dact_ms": float(np.abs(a32[both] - a64[both]).max()) if both.any() else None,
                             "same_activated_set": bool(np.array_equal(a32 >= 0, a64 >= 0))}
     return line
