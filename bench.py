@@ -46,7 +46,7 @@ TP06_XU_PER_SUBSTEP = 82.0     # SFU (MUFU) instructions per TP06 sub-step, ncu 
 # DRAM bytes (read + write) per reaction launch, mean of three resting-phase
 # launches captured with warm caches (profiles/reaction_tp06_fp32_slab.md; the
 # state stays in L2)
-REACTION_DRAM_BYTES_PER_LAUNCH = 23125.0
+REACTION_DRAM_BYTES_PER_LAUNCH = 12373.0
 
 
 def _dist():
@@ -457,6 +457,7 @@ def _reaction_roofline(solver, clocks, sub_per_step):
             "substeps_per_launch": sub_per_step,
             "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled), 1 op/lane/cycle",
             "xu_frac": TP06_XU_PER_SUBSTEP * sub_per_step / avg_s / xu_peak,
+            "xu_peak_basis": f"{XU_LANES_PER_SM} SFU lanes per SM (ncu rates its XU pipe at 32 lanes: half this fraction)",
             "bytes_per_launch": bytes_launch,
             "bytes_frac_of_measured_hbm": bytes_launch / avg_s / 1e9 / _peaks().get("hbm_gbs", 6786.9)}
 
