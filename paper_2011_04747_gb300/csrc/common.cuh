@@ -162,11 +162,11 @@ struct SyncParams {
 // Section 2's k rule from the rate of the split solution over the last step
 // (reading R-k; with rrate, the reaction's rate at its last sub-step, reading
 // R-k2) and the first-upward-crossing activation time (R-LAT).
-// EXT: p.rrate may be set (compiled out otherwise).
-// The same with V at the last synchronisation (vold) and the activation
-// time (a0) of node i already loaded by the caller.
-template <typename R, bool EXT>
-__device__ __forceinline__ int sync_node_loaded(const SyncParams<R>& p, int i, R vnew, R vold, R a0) {
+// EXT: p.rrate may be set (compiled out otherwise).  vold: V of node i at the
+// last synchronisation; act0(): its activation time so far, evaluated only
+// when V crosses the threshold upwards (the only case that needs it).
+template <typename R, bool EXT, class ActLoad>
+__device__ __forceinline__ int sync_core(const SyncParams<R>& p, int i, R vnew, R vold, const ActLoad& act0) {
     int k = 1;
     if (p.adaptive) {
         R rate = (EXT && p.rrate) ? p.rrate[i] * p.rrate_scale : (vnew - vold) * p.rate_scale;
@@ -177,7 +177,7 @@ __device__ __forceinline__ int sync_node_loaded(const SyncParams<R>& p, int i, R
         k = k < p.kmax ? k : p.kmax;
     }
     p.kk[i] = (uint8_t)k;
-    if (a0 < (R)0 && vold < p.vth && vnew >= p.vth) {
+    if (vold < p.vth && vnew >= p.vth && act0() < (R)0) {
         double tprev = (double)step_index(p.step) * p.dt;
         p.act[i] = (R)(tprev + p.dt * (double)((p.vth - vold) / (vnew - vold)));
     }
@@ -186,9 +186,16 @@ __device__ __forceinline__ int sync_node_loaded(const SyncParams<R>& p, int i, R
     return k;
 }
 
+// The same with V at the last synchronisation (vold) and the activation
+// time (a0) of node i already loaded by the caller.
+template <typename R, bool EXT>
+__device__ __forceinline__ int sync_node_loaded(const SyncParams<R>& p, int i, R vnew, R vold, R a0) {
+    return sync_core<R, EXT>(p, i, vnew, vold, [&] { return a0; });
+}
+
 template <typename R, bool EXT>
 __device__ __forceinline__ int sync_node(const SyncParams<R>& p, int i, R vnew) {
-    return sync_node_loaded<R, EXT>(p, i, vnew, p.vsync[i], p.act[i]);
+    return sync_core<R, EXT>(p, i, vnew, p.vsync[i], [&] { return p.act[i]; });
 }
 
 // Block-cooperative append of node i (valid lanes) to the list of its k
