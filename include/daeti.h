@@ -123,7 +123,9 @@ int daeti_set_stream(daeti_ctx* ctx, void* cuda_stream);
 int daeti_set_mesh_grid(daeti_ctx* ctx, int dim, const int64_t n[3], double h);
 
 /* Tetrahedral mesh (Section 3.3): xyz = 3*n_nodes doubles (cm), tets =
- * 4*n_tets node indices in [0, n_nodes).  Degenerate tets -> EINVAL. */
+ * 4*n_tets node indices in [0, n_nodes).  EINVAL for an index out of range
+ * or a node in no tetrahedron (it would have no lumped mass); degenerate
+ * tets -> EINVAL at prepare. */
 int daeti_set_mesh_tet(daeti_ctx* ctx, int64_t n_nodes, const double* xyz,
                        int64_t n_tets, const int64_t* tets);
 

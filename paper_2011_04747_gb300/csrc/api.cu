@@ -379,8 +379,14 @@ int daeti_set_mesh_tet(daeti_ctx* c, int64_t n_nodes, const double* xyz, int64_t
     if (c->prepared) return fail(c, DAETI_ESTATE, "mesh cannot change after prepare");
     if (n_nodes < 4 || n_tets < 1 || !xyz || !tets) return fail(c, DAETI_EINVAL, "bad tet mesh arguments");
     if (n_nodes >= (int64_t)1 << 31) return fail(c, DAETI_EINVAL, "more than 2^31 - 1 nodes");
-    for (int64_t e = 0; e < 4 * n_tets; ++e)
+    std::vector<unsigned char> used(n_nodes, 0);
+    for (int64_t e = 0; e < 4 * n_tets; ++e) {
         if (tets[e] < 0 || tets[e] >= n_nodes) return fail(c, DAETI_EINVAL, "tet node index out of range");
+        used[tets[e]] = 1;
+    }
+    // a node in no tetrahedron has no lumped mass (M_L^-1 K is undefined there)
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (!used[i]) return fail(c, DAETI_EINVAL, "node " + std::to_string(i) + " belongs to no tetrahedron");
     c->mesh_kind = 2;
     c->dim = 3;
     c->n_nodes = n_nodes;

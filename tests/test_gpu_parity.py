@@ -274,6 +274,14 @@ def test_error_paths():
     assert e.value.code == binding.ENONFINITE
     s.daeti_init_state()
     s.close()
+    # tet meshes: an index out of range, a node in no tetrahedron
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], dtype=float) * 0.1
+    for tets in (np.array([[0, 1, 2, 5]]), np.array([[0, 1, 2, 3]])):
+        s = binding.Solver(precision="fp64")
+        with pytest.raises(binding.DaetiError) as e:
+            s.daeti_set_mesh_tet(xyz, tets)
+        assert e.value.code == binding.EINVAL
+        s.close()
 
 
 def test_degenerate_inputs():
