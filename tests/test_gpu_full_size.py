@@ -1,5 +1,5 @@
-"""The tet-slab and batch workloads at their full bench sizes, in the bench's
-launch configuration (FP32 with compensated V, CUDA graphs of 20 steps).
+"""The bench slab, tet-slab and batch workloads at their full sizes, in the
+bench's launch configurations (FP32 with compensated V, CUDA graphs).
 
 The oracle cannot run 2 M nodes or 13 M nodes in seconds, so these check
 what holds at any size against paths that the oracle pins at small sizes:
@@ -7,7 +7,9 @@ sampled batch tissues bit for bit against the same tissues advanced alone
 (the single-tissue path is oracle-checked), the smallest Mitchell-Schaeffer
 and TP06 tissues of the batch against the oracle itself, and the full tet
 slab in FP32 against the FP64 path (oracle-checked on small tet meshes)
-within the FP32 tolerances."""
+within the FP32 tolerances, and the headline slab over its whole 500 ms run
+in FP32 against the FP64 path (oracle-checked on reduced slabs over whole
+action potentials)."""
 import numpy as np
 import pytest
 
@@ -93,3 +95,30 @@ def test_zmarch_diffusion_bit_identical_at_bench_sizes(dims):
         assert np.array_equal(out[0][0], o[0])
         assert np.array_equal(out[0][1], o[1])
         assert out[0][2] == o[2]
+
+
+def test_full_bench_slab_fp32_against_fp64_whole_run():
+    """The headline workload as the bench runs it (101 x 101 x 26 TP06 slab,
+    500 ms, FP32 with compensated V, graphs of 100 steps with programmatic
+    dependent launch, k lists) against the FP64 path over the whole run,
+    V of every node every 10 ms: within 2 mV, activation within 0.5 ms, the
+    same activated set, every node activated and back at rest at the end."""
+    binding = ensure_lib()
+    wl = I.tp06_slab_3d(t_end=500.0)
+    s32 = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=100)
+    s32.daeti_set_tuning(react_block=128, react_min_blocks=8, diff_block=256, fuse_diffusion=1, bucket_k=1, pdl=1)
+    s64 = binding.solver_from_workload(wl, precision="fp64", graph_steps=100)
+    worst = 0.0
+    for t in range(10, 501, 10):
+        s32.daeti_advance(float(t))
+        s64.daeti_advance(float(t))
+        worst = max(worst, float(np.max(np.abs(s32.daeti_read_v() - s64.daeti_read_v()))))
+    a32, a64 = s32.daeti_read_activation(), s64.daeti_read_activation()
+    v64 = s64.daeti_read_v()
+    s32.close()
+    s64.close()
+    assert worst <= 2.0, worst
+    da, same, n_act = act_error(a32, a64)
+    assert same and da <= 0.5, (same, da)
+    assert n_act == wl.n_nodes
+    assert float(v64.max()) < -70.0
