@@ -1053,7 +1053,6 @@ int daeti_synchronize(daeti_ctx* c) {
         int f[4];
         CK(cpy_(c, f, c->s.flags, 16, cudaMemcpyDeviceToHost));
         if (f[0] & 1) return fail(c, DAETI_ENONFINITE, "V became non-finite");
-        if (f[0] & 2) return fail(c, DAETI_ECUDA, "k histogram inconsistent with k (internal error)");
     }
     return DAETI_OK;
 }
