@@ -891,7 +891,7 @@ def main():
     ap.add_argument("--profile-run", type=float, default=0.0,
                     help="only simulate this many ms once on the slab (FP32), for profilers; no timing")
     ap.add_argument("--diff-block", type=int, default=-1,
-                    help="with --profile-run: diffusion launch shape (0 = 2D tiles / 3D register z-march, "
+                    help="with --profile-run: diffusion launch shape (0 = 2D tiles / 3D runs of nodes along y, "
                          "256 = one thread per node; default: the library's)")
     ap.add_argument("--fuse-diffusion", type=int, default=-1,
                     help="with --profile-run: 1 = last step-I diffusion sub-step inside the reaction launch, "

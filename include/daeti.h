@@ -247,18 +247,18 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
  * react_min_blocks: 6, 8 or 10 resident reaction blocks per SM the register
  * budget must allow (TP06 in float); diff_block: threads per block of the
  * one-thread-per-node diffusion kernel (32..256, multiple of 32; default
- * 256); 0: on structured grids, 2D shared-memory tiles or the 3D register
- * z-march (one thread per (x, y) column over a run of z planes, 9 loads per
- * node; other meshes take 256);
+ * 256); 0: on structured grids, 2D shared-memory tiles, or in 3D (float
+ * precisions, per-layer D) runs of diff_rows nodes along y per thread that
+ * share their rows' loads and go in pairs through packed FP32 operations
+ * (other meshes and FP64 take 256);
  * fuse_diffusion: run the last diffusion sub-step of step I inside the
  * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
  * steps per captured CUDA graph (rounded up to even, 0 = plain launches);
  * pdl: 1 = launch the per-step kernels with
  * programmatic dependent launch, so each one's blocks are resident when its
- * predecessor ends (default), 0 = plain launches; diff_zrun: z planes per
- * thread of the register z-march (diff_block = 0 on 3D grids), 0 = chosen
- * from the grid and the GPU's resident slots.  set waits for enqueued work and drops
- * captured graphs. */
+ * predecessor ends (default), 0 = plain launches; diff_rows: nodes per
+ * thread along y of that 3D kernel, 2 or 4 (0 = 2; other values EINVAL).
+ * set waits for enqueued work and drops captured graphs. */
 typedef struct daeti_tuning {
     int32_t struct_size;       /* sizeof(daeti_tuning) */
     int32_t react_block;
@@ -268,7 +268,7 @@ typedef struct daeti_tuning {
     int32_t bucket_k;
     int32_t graph_steps;
     int32_t pdl;
-    int32_t diff_zrun;
+    int32_t diff_rows;
 } daeti_tuning;
 int daeti_get_tuning(daeti_ctx* ctx, daeti_tuning* tuning);
 int daeti_set_tuning(daeti_ctx* ctx, const daeti_tuning* tuning);

@@ -68,12 +68,12 @@ class daeti_tuning(ctypes.Structure):
         ("bucket_k", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
         ("pdl", ctypes.c_int32),
-        ("diff_zrun", ctypes.c_int32),
+        ("diff_rows", ctypes.c_int32),
     ]
 
 
 TUNING_FIELDS = ("react_block", "react_min_blocks", "diff_block", "fuse_diffusion", "bucket_k", "graph_steps",
-                 "pdl", "diff_zrun")
+                 "pdl", "diff_rows")
 
 _lib = None
 

@@ -186,7 +186,7 @@ void L_react(daeti_ctx* c, StepRef ref, int buf, bool fused, cudaStream_t st, bo
 void L_diff(daeti_ctx* c, StepRef ref, int src, bool sync, cudaStream_t st, bool timed) {
     Timer t(c, st, timed, 1);
     launch_diffusion(c->s, c->op, src, sync, c->par ^ 1, c->sargs, ref, lists_mode(c), c->diff_block, st,
-                     c->rtune.pdl != 0, c->diff_zrun);
+                     c->rtune.pdl != 0, c->diff_rows);
 }
 
 // One Strang step from a synchronisation to the next: step I (l sub-steps,
@@ -659,6 +659,24 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
                 if (j != self) A[cls * DAETI_ROW + j] = c->dt_ad * tab.K[cls * 27 + j] / tab.m[cls];
         if (fresh && (rc = dalloc(c, &c->op.coef, R * A.size()))) return rc;
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
+        if (tab.dim == 3 && R == 4) {
+            // entry pairs (row of a node, row of the node one y above it) for
+            // the y-paired kernel, every pair of y classes
+            std::vector<double> P((size_t)tab.nz * 27 * 2 * DAETI_ROW, 0.0);
+            for (int z = 0; z < tab.nz; ++z)
+                for (int ca = 0; ca < 3; ++ca)
+                    for (int cb = 0; cb < 3; ++cb)
+                        for (int cx = 0; cx < 3; ++cx) {
+                            const size_t ra = ((size_t)z * 3 + ca) * 3 + cx, rb = ((size_t)z * 3 + cb) * 3 + cx;
+                            double* row = P.data() + ((((size_t)z * 3 + ca) * 3 + cb) * 3 + cx) * 2 * DAETI_ROW;
+                            for (int j = 0; j < DAETI_ROW; ++j) {
+                                row[2 * j] = A[ra * DAETI_ROW + j];
+                                row[2 * j + 1] = A[rb * DAETI_ROW + j];
+                            }
+                        }
+            if (!c->op.pcoef && (rc = dalloc(c, &c->op.pcoef, R * P.size()))) return rc;
+            if ((rc = upload_real(c, c->op.pcoef, P.data(), (int64_t)P.size()))) return rc;
+        }
         // per-node table row (z * 3 + y class) * 3 + x class, when it fits 16 bits
         if (fresh && (int64_t)tab.nz * 9 <= 65535) {
             std::vector<uint16_t> cls(N);
@@ -1321,7 +1339,7 @@ int daeti_get_tuning(daeti_ctx* c, daeti_tuning* t) {
     t->bucket_k = c->lists ? 1 : 0;
     t->graph_steps = c->graph_steps;
     t->pdl = c->rtune.pdl;
-    t->diff_zrun = c->diff_zrun;
+    t->diff_rows = c->diff_rows;
     return DAETI_OK;
 }
 
@@ -1329,7 +1347,8 @@ int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     if (!c || !t || t->struct_size != (int32_t)sizeof(daeti_tuning)) return DAETI_EINVAL;
     if (t->react_block <= 0 || t->react_block > 128 || t->react_block % 32 || t->diff_block < 0 ||
         t->diff_block > 256 || t->diff_block % 32 || t->graph_steps < 0 ||
-        (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1) || t->diff_zrun < 0)
+        (t->react_min_blocks != 6 && t->react_min_blocks != 8 && t->react_min_blocks != 10) || (t->pdl != 0 && t->pdl != 1) ||
+        (t->diff_rows != 0 && t->diff_rows != 2 && t->diff_rows != 4))
         return fail(c, DAETI_EINVAL, "bad tuning values");
     int rc = daeti_synchronize(c);
     if (rc) return rc;
@@ -1338,7 +1357,7 @@ int daeti_set_tuning(daeti_ctx* c, const daeti_tuning* t) {
     c->rtune.min_blocks = t->react_min_blocks;
     c->rtune.pdl = t->pdl;
     c->diff_block = t->diff_block;
-    c->diff_zrun = t->diff_zrun;
+    c->diff_rows = t->diff_rows;
     c->fused = t->fuse_diffusion != 0;
     const bool new_lists = t->bucket_k != 0;
     if (new_lists != c->lists && c->prepared) {

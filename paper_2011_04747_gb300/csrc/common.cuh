@@ -229,6 +229,45 @@ __device__ __forceinline__ void block_append(int* counts, int* lists, int n, int
     }
 }
 
+// block_append for N nodes per thread (node i[h] with k[h] where v[h]), with
+// one set of barriers.
+template <int N>
+__device__ __forceinline__ void block_append_n(int* counts, int* lists, int n, const int* i, const int* k,
+                                               const bool* v) {
+    __shared__ int blk[DAETI_MAX_K];
+    __shared__ int base[DAETI_MAX_K];
+    if (threadIdx.x < DAETI_MAX_K) blk[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int slot[N];
+#pragma unroll
+    for (int h = 0; h < N; ++h) {
+        slot[h] = 0;
+        const unsigned active = __ballot_sync(0xffffffffu, v[h]);
+        if (v[h]) {
+            const unsigned peers = __match_any_sync(active, k[h]);
+            const int leader = __ffs(peers) - 1;
+            int wbase = 0;
+            if (lane == leader) wbase = atomicAdd(&blk[k[h]], __popc(peers));
+            wbase = __shfl_sync(peers, wbase, leader);
+            slot[h] = wbase + __popc(peers & ((1u << lane) - 1u));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < DAETI_MAX_K) {
+        const int c = blk[threadIdx.x];
+        base[threadIdx.x] = c ? atomicAdd(&counts[threadIdx.x], c) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < N; ++h) {
+        if (v[h]) {
+            const int pos = base[k[h]] + slot[h];
+            if (pos < n) lists[(size_t)k[h] * n + pos] = i[h];
+        }
+    }
+}
+
 // Bucketing at a synchronisation.  counts[0] holds the mode the previous
 // step A chose: 1 = append every node to the list of its k (block_append);
 // -K = that step had k = K at every node, so only check that this one does
@@ -242,6 +281,21 @@ __device__ __forceinline__ void bucket_nodes(int* counts, int* lists, int* uflag
         return;
     }
     block_append(counts, lists, n, i, k, valid);
+}
+
+// bucket_nodes for N nodes per thread.
+template <int N>
+__device__ __forceinline__ void bucket_nodes_n(int* counts, int* lists, int* uflag, int n, const int* i, const int* k,
+                                               const bool* v) {
+    const int mode = counts[0];
+    if (mode < 0) {
+        bool d = false;
+#pragma unroll
+        for (int h = 0; h < N; ++h) d = d || (v[h] && k[h] != -mode);
+        if (__syncthreads_or(d) && threadIdx.x == 0) atomicOr(uflag, 1);
+        return;
+    }
+    block_append_n<N>(counts, lists, n, i, k, v);
 }
 
 }  // namespace daeti

@@ -61,7 +61,7 @@ struct daeti_ctx {
     // launch shapes
     ReactTuning rtune;
     int diff_block = 256;       // 0: shared-memory tiles on structured grids
-    int diff_zrun = 0;          // planes per thread of the register z-march (0: automatic)
+    int diff_rows = 0;          // nodes per thread along y of the 3D structured kernel (0 = 2, 2 or 4)
     bool fused = true;          // last sub-step of step I inside the reaction launch
     bool lists = true;
     int graph_steps = 20;

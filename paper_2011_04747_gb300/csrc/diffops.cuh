@@ -106,6 +106,7 @@ struct OpView {
     int nx, ny, nz;
     const R* coef;
     const uint16_t* cls;  // table row of each node (nullable)
+    const R* pcoef;       // 3D float table of entry pairs (y-paired kernel; nullable)
     int per_node;         // one coefficient row per node
     const int64_t* chunk_ptr;
     const int* chunk_w;
@@ -153,6 +154,7 @@ inline OpView<R> op_view(const DiffOp& op) {
     v.nz = op.nz;
     v.coef = (const R*)op.coef;
     v.cls = op.cls;
+    v.pcoef = (const R*)op.pcoef;
     v.per_node = op.per_node;
     v.chunk_ptr = op.chunk_ptr;
     v.chunk_w = op.chunk_w;

@@ -124,204 +124,202 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl
                   cout, sp);
 }
 
-// ------------------------------------------------- 3D register z-march
-// 3D structured grids with ghost-padded V buffers and the per-class table,
-// one thread per (x, y) column over a run of z planes and no barriers (but
-// the synchronisation's bucketing): a thread keeps the 3 x 3 neighbourhoods
-// of planes z - 1, z, z + 1 and z + 2 in registers and loads only the 9
-// values of one new plane per node (instead of 26 neighbours), two planes
-// ahead; the loop is unrolled by four so the planes change roles instead of
-// being copied.  Same
-// stencil_update, same term order: results equal the one-thread-per-node
-// kernel's.
-constexpr int RZX = 32, RZY = 8;
+// ------------------------------------ 3D runs of nodes along y, packed FP32
+// A thread updates the NY nodes (x, y + m, z), m = 0 .. NY - 1, y a multiple
+// of NY.  In each plane they share rows: NY + 2 rows of three values instead
+// of 3 NY (36 loads for two nodes, 54 for four, against 27 per node), and
+// the nodes go in pairs (m, m + 1) through packed f32x2 subtractions and
+// fmas.  Both halves of a packed operation round exactly as the scalar
+// operation does (round to nearest, no flush), and the terms are added in
+// stencil_update's order, so results equal the one-thread-per-node kernel's.
+// Coefficients come from the table of entry pairs (op.pcoef): one 16-byte
+// load gives the pairs of two entries.
 
-// One plane of a column: the 3 x 3 neighbourhood of V and, for planes the
-// thread computes, the node's Kahan term, V at the last synchronisation and
-// activation time (loaded with the plane, ahead of their use).
-template <typename R>
-struct ZPlane {
-    R v[9];
-    float c;
-    R vs, ac;
+// Quotient n / d for 0 <= n < 2^31 by a multiply and a shift (Granlund and
+// Montgomery, division by invariant integers): k = 32 + ceil(log2 d),
+// m = floor(2^k / d) + 1; then floor(n m / 2^k) = floor(n / d) because
+// n (m d - 2^k) <= n d < 2^k.
+struct FastDiv {
+    unsigned long long m;
+    int k;
 };
+inline FastDiv fast_div(unsigned d) {
+    int c = 0;
+    while ((1ull << c) < d) ++c;
+    FastDiv f;
+    f.k = 32 + c;
+    f.m = (1ull << f.k) / d + 1;
+    return f;
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+    return (int)(((unsigned long long)(unsigned)n * f.m) >> f.k);
+}
 
-template <typename R, bool KAHAN, bool SYNC>
-struct ZColumn {
-    const OpView<R>& op;
-    const R* base;        // V of this column at plane 0 (a column of the grid; column 0 off the grid)
-    long long nxy;
-    int nx, cx, cy, i0;   // i0: node index of the column at plane 0
-    bool col_in;
-    int z0, z1;
-    R* __restrict__ vout;
-    const float* __restrict__ cin;
-    float* __restrict__ cout;
-    const SyncParams<R>& sp;
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
-    __device__ __forceinline__ void load(ZPlane<R>& P, int p) const {
-        const R* q = base + nxy * p;
-        P.v[0] = q[-nx - 1];
-        P.v[1] = q[-nx];
-        P.v[2] = q[-nx + 1];
-        P.v[3] = q[-1];
-        P.v[4] = q[0];
-        P.v[5] = q[1];
-        P.v[6] = q[nx - 1];
-        P.v[7] = q[nx];
-        P.v[8] = q[nx + 1];
-        if (p >= z0 && p < z1) {
-            const int i = i0 + (int)(nxy * p);
-            if (KAHAN) P.c = __ldg(cin + i);
-            if (SYNC) {
-                P.vs = sp.vsync[i];
-                P.ac = sp.act[i];
+template <int NY, bool KAHAN, bool SYNC>
+__global__ void __launch_bounds__(256, NY == 2 ? 5 : 3)
+    yrun_substep_kernel(OpView<float> op, int nthreads, FastDiv dnx, FastDiv dnyr, const float* __restrict__ vin,
+                        float* __restrict__ vout, const float* __restrict__ cin, float* __restrict__ cout,
+                        SyncParams<float> sp) {
+    constexpr int NP = NY / 2;   // node pairs
+    pdl_wait();
+    pdl_trigger();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < nthreads;
+    const int tt = active ? t : 0;
+    const int nx = op.nx, ny = op.ny, nyr = (op.ny + NY - 1) / NY;
+    const int r = fdiv(tt, dnx), x = tt - r * nx;
+    const int z = fdiv(r, dnyr), y = NY * (r - z * nyr);
+    const int nxy = nx * ny;
+    const int i0 = x + nx * (y + ny * z);
+    bool ok[NY];
+    int idx[NY];
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+        ok[m] = active && y + m < ny;
+        idx[m] = i0 + m * nx;
+    }
+    // rows y - 1 .. y + NY of planes z - 1, z, z + 1; rows past y + 1 are
+    // clamped to row ny (only they can leave the grid): inside the ghost
+    // margins
+    const float* p = vin + i0;
+    int roff[NY + 2];
+#pragma unroll
+    for (int row = 0; row < NY + 2; ++row) roff[row] = (row < 3 ? row - 1 : min(row - 1, ny - y)) * nx;
+    float v[3][NY + 2][3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int row = 0; row < NY + 2; ++row) {
+            const float* q = p + ((dz - 1) * nxy + roff[row]);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) v[dz][row][dx] = q[dx - 1];
+        }
+    float ci[NY], vs[NY];
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+        ci[m] = KAHAN && ok[m] ? __ldg(cin + idx[m]) : 0.f;
+        // V at the last synchronisation, loaded with V (activation times
+        // only where V crosses the threshold)
+        vs[m] = SYNC && ok[m] ? sp.vsync[idx[m]] : 0.f;
+    }
+    const int cx = bclass(x, nx);
+    const float* prow[NP];
+    unsigned long long vi[NP], acc[NP];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        const int ca = ok[2 * h] ? bclass(y + 2 * h, ny) : 1;
+        const int cb = ok[2 * h + 1] ? bclass(y + 2 * h + 1, ny) : ca;
+        prow[h] = op.pcoef + ((((size_t)z * 3 + ca) * 3 + cb) * 3 + cx) * (2 * DAETI_ROW);
+        vi[h] = pack2(v[1][2 * h + 1][1], v[1][2 * h + 2][1]);
+        acc[h] = pack2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < DAETI_ROW / 2; ++q) {
+        float4 c4[NP];
+#pragma unroll
+        for (int h = 0; h < NP; ++h) c4[h] = __ldg(reinterpret_cast<const float4*>(prow[h]) + q);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int j = 2 * q + e;
+            if (j >= 27 || j == 13) continue;
+            const int dz = j / 9, dy = (j / 3) % 3, dx = j % 3;
+#pragma unroll
+            for (int h = 0; h < NP; ++h) {
+                const unsigned long long cj = e ? pack2(c4[h].z, c4[h].w) : pack2(c4[h].x, c4[h].y);
+                const unsigned long long vj = pack2(v[dz][2 * h + dy][dx], v[dz][2 * h + dy + 1][dx]);
+                acc[h] = fma2(cj, sub2(vj, vi[h]), acc[h]);
             }
         }
     }
-    // node at plane z from planes z - 1 (A), z (B) and z + 1 (C, loaded a
-    // step earlier); the load of plane z + 2 into D is issued first, so two
-    // planes of loads are in flight while the node is computed.  mode: the
-    // bucketing mode of this synchronisation (counts[0]); in the uniform-k
-    // mode (< 0) a node whose k differs only sets `differs`, voted on once
-    // per block at the end, instead of a block barrier per plane
-    __device__ __forceinline__ void step(const ZPlane<R>& A, const ZPlane<R>& B, const ZPlane<R>& C, ZPlane<R>& D,
-                                         int z, int mode, int& differs) const {
-        if (z + 2 <= z1) load(D, z + 2);
-        int k = 1;
-        const int i = i0 + (int)(nxy * z);
-        if (col_in) {
-            const R* crow = op.coef + ((size_t)(z * 3 + cy) * 3 + cx) * DAETI_ROW;
-            auto fetch = [&](int dx, int dy, int dz) {
-                const int j = (dy + 1) * 3 + (dx + 1);
-                return dz < 0 ? A.v[j] : (dz == 0 ? B.v[j] : C.v[j]);
-            };
-            R v;
-            float cc;
-            stencil_update<R, 3, KAHAN, true>(crow, 1, 1, 1, 3, B.v[4], KAHAN ? B.c : 0.f, fetch, v, cc);
-            vout[i] = v;
-            if (KAHAN) cout[i] = cc;
-            if (SYNC) k = sync_node_loaded<R, false>(sp, i, v, B.vs, B.ac);
-        }
-        if (SYNC && sp.counts) {
-            if (mode < 0) differs |= col_in && k != -mode;
-            else block_append(sp.counts, sp.lists, sp.n, i, k, col_in);
+    int kk[NY];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        float a[2];
+        unpack2(acc[h], a[0], a[1]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int m = 2 * h + e;
+            float vn = v[1][m + 1][1], cc = ci[m];
+            add_comp(vn, KAHAN ? &cc : (float*)nullptr, -a[e]);
+            kk[m] = 1;
+            if (ok[m]) {
+                vout[idx[m]] = vn;
+                if (KAHAN) cout[idx[m]] = cc;
+                if (SYNC) kk[m] = sync_core<float, false>(sp, idx[m], vn, vs[m], [&] { return sp.act[idx[m]]; });
+            }
         }
     }
-};
-
-template <typename R, bool KAHAN, bool SYNC>
-__global__ void __launch_bounds__(RZX * RZY, sizeof(R) == 4 ? 3 : 2) zreg_substep_kernel(OpView<R> op, int n, int zrun,
-                                                                const R* __restrict__ vin, R* __restrict__ vout,
-                                                                const float* __restrict__ cin,
-                                                                float* __restrict__ cout, SyncParams<R> sp) {
-    pdl_wait();
-    pdl_trigger();
-    const int gx = blockIdx.x * RZX + threadIdx.x % RZX, gy = blockIdx.y * RZY + threadIdx.x / RZX;
-    const int nx = op.nx, ny = op.ny, nz = op.nz;
-    const int z0 = blockIdx.z * zrun, z1 = min(nz, z0 + zrun);
-    const bool col_in = gx < nx && gy < ny;
-    // offsets reach one plane, row and node beyond the column, inside the
-    // ghost margins; columns off the grid read column 0 and store nothing
-    const int col = col_in ? gx + nx * gy : 0;
-    const ZColumn<R, KAHAN, SYNC> zc{op, vin + col, (long long)nx * ny, nx,
-                                     gx == 0 ? 0 : (gx == nx - 1 ? 2 : 1), gy == 0 ? 0 : (gy == ny - 1 ? 2 : 1),
-                                     col, col_in, z0, z1, vout, cin, cout, sp};
-    const int mode = SYNC && sp.counts ? sp.counts[0] : 1;
-    int differs = 0;
-    ZPlane<R> P0, P1, P2, P3;
-    zc.load(P0, z0 - 1);
-    zc.load(P1, z0);
-    zc.load(P2, z0 + 1);
-    int z = z0;
-    for (; z + 4 <= z1; z += 4) {
-        zc.step(P0, P1, P2, P3, z, mode, differs);
-        zc.step(P1, P2, P3, P0, z + 1, mode, differs);
-        zc.step(P2, P3, P0, P1, z + 2, mode, differs);
-        zc.step(P3, P0, P1, P2, z + 3, mode, differs);
-    }
-    if (z < z1) zc.step(P0, P1, P2, P3, z, mode, differs);
-    if (z + 1 < z1) zc.step(P1, P2, P3, P0, z + 1, mode, differs);
-    if (z + 2 < z1) zc.step(P2, P3, P0, P1, z + 2, mode, differs);
-    if (SYNC && sp.counts && mode < 0) {
-        if (__syncthreads_or(differs) && threadIdx.x == 0) atomicOr(sp.uflag, 1);
-    }
+    if (SYNC && sp.counts) bucket_nodes_n<NY>(sp.counts, sp.lists, sp.uflag, sp.n, idx, kk, ok);
 }
 
-// Resident blocks per SM of a kernel at `threads` threads, and the SM count
-// (queried once per kernel instance; 4 and 152 if a query fails).
-template <typename K>
-static int resident_blocks(K kern, int threads) {
-    static int cached = 0;
-    if (!cached) {
-        int nb = 0;
-        cached = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0) == cudaSuccess && nb > 0 ? nb : 4;
-    }
-    return cached;
-}
-static int sm_count() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, v = 0;
-        cached = cudaGetDevice(&dev) == cudaSuccess &&
-                         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
-                     ? v
-                     : 152;
-    }
-    return cached;
-}
-
-// diff_block = 0 on structured grids: 2D shared-memory tiles, or the 3D
-// register z-march with its z range split into runs (zrun_req planes, or
-// chosen so that the blocks cover the GPU's resident slots in few waves).
-template <typename R, bool KAHAN>
-static void tiled_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
-                         const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp,
-                         int zrun_req) {
-    if (dop.dim == 2) {
-        const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
-        if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
-        else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
-        return;
-    }
-    const long cols = (long)((dop.nx + RZX - 1) / RZX) * ((dop.ny + RZY - 1) / RZY);
-    const int nb = sync ? resident_blocks(zreg_substep_kernel<R, KAHAN, true>, RZX * RZY)
-                        : resident_blocks(zreg_substep_kernel<R, KAHAN, false>, RZX * RZY);
-    const long slots = (long)sm_count() * nb;
-    int best = 1;
-    double best_cost = 1e300;
-    for (int ns = 1; ns <= dop.nz; ++ns) {   // waves x (planes per run + prologue)
-        const int zr = (dop.nz + ns - 1) / ns;
-        const long blocks = cols * ((dop.nz + zr - 1) / zr);
-        const double cost = (double)((blocks + slots - 1) / slots) * (zr + 1.0);
-        if (cost < best_cost - 1e-9) {
-            best_cost = cost;
-            best = ns;
-        }
-    }
-    const int zrun = zrun_req > 0 ? std::min(zrun_req, dop.nz) : (dop.nz + best - 1) / best;
-    const dim3 grid((dop.nx + RZX - 1) / RZX, (dop.ny + RZY - 1) / RZY, (dop.nz + zrun - 1) / zrun);
+template <int NY, bool KAHAN>
+static void yrun_launch(bool sync, cudaStream_t st, bool pdl, const OpView<float>& op, const DiffOp& dop,
+                        const float* vin, float* vout, const float* cin, float* cout, const SyncParams<float>& sp) {
+    const int nyr = (dop.ny + NY - 1) / NY;
+    const long long nt = (long long)dop.nx * nyr * dop.nz;
+    const int grid = (int)((nt + 255) / 256);
+    if (!grid) return;
+    const FastDiv dnx = fast_div((unsigned)dop.nx), dnyr = fast_div((unsigned)nyr);
     if (sync)
-        launch_ex(zreg_substep_kernel<R, KAHAN, true>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
+        launch_ex(yrun_substep_kernel<NY, KAHAN, true>, grid, 256, st, pdl, op, (int)nt, dnx, dnyr, vin, vout, cin,
+                  cout, sp);
     else
-        launch_ex(zreg_substep_kernel<R, KAHAN, false>, grid, RZX * RZY, st, pdl, op, n, zrun, vin, vout, cin, cout, sp);
+        launch_ex(yrun_substep_kernel<NY, KAHAN, false>, grid, 256, st, pdl, op, (int)nt, dnx, dnyr, vin, vout, cin,
+                  cout, sp);
+}
+
+// diff_block = 0 on 2D structured grids: shared-memory tiles.
+template <typename R, bool KAHAN>
+static void tiled2d_launch(bool sync, cudaStream_t st, bool pdl, const OpView<R>& op, const DiffOp& dop, int n,
+                           const R* vin, R* vout, const float* cin, float* cout, const SyncParams<R>& sp) {
+    const dim3 grid((dop.nx + TX - 1) / TX, (dop.ny + TY - 1) / TY);
+    if (sync) launch_ex(tiled2d_substep_kernel<R, KAHAN, true>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
+    else launch_ex(tiled2d_substep_kernel<R, KAHAN, false>, grid, TX * TY, st, pdl, op, n, vin, vout, cin, cout, sp);
 }
 
 template <typename R, bool KAHAN>
 static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync, int par, const SyncArgs& sa,
-                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int zrun) {
+                       StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int rows) {
     SyncParams<R> sp = make_sync<R>(s, sa, step, par, lists);
     const bool padded = s.vpad >= stencil_reach(dop);
-    if (dop.kind == 0 && block == 0 && !dop.per_node && !(sync && s.rrate) && (dop.dim == 2 || padded)) {
-        // structured grid: 2D shared-memory tiles, or the 3D register
-        // z-march (which reads the ghost margins of padded V buffers)
+    const bool table = dop.kind == 0 && !dop.per_node && !(sync && s.rrate);
+    if (block == 0 && table) {
         const OpView<R> op = op_view<R>(dop);
         const R* vin = (const R*)s.V[src];
         R* vout = (R*)s.V[1 - src];
         const float* cin = KAHAN ? s.C[src] : nullptr;
         float* cout = KAHAN ? s.C[1 - src] : nullptr;
-        tiled_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp, zrun);
-        return;
+        if (dop.dim == 2) {
+            tiled2d_launch<R, KAHAN>(sync, st, pdl, op, dop, (int)s.n, vin, vout, cin, cout, sp);
+            return;
+        }
+        if constexpr (sizeof(R) == 4) {
+            // 3D in float with ghost-padded V: runs of 2 or 4 nodes along y
+            if (padded && dop.pcoef) {
+                if (rows == 4) yrun_launch<4, KAHAN>(sync, st, pdl, op, dop, vin, vout, cin, cout, sp);
+                else yrun_launch<2, KAHAN>(sync, st, pdl, op, dop, vin, vout, cin, cout, sp);
+                return;
+            }
+        }
     }
     if (block <= 0) block = 256;
     const int grid = (int)((s.n + block - 1) / block);
@@ -341,13 +339,13 @@ static void diff_typed(const DevState& s, const DiffOp& dop, int src, bool sync,
 }
 
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int zrun) {
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl, int rows) {
     if (s.prec == P_F64)
-        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
+        diff_typed<double, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, rows);
     else if (s.kahan)
-        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
+        diff_typed<float, true>(s, op, src, sync, par, sa, step, lists, block, st, pdl, rows);
     else
-        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, zrun);
+        diff_typed<float, false>(s, op, src, sync, par, sa, step, lists, block, st, pdl, rows);
 }
 
 // ---------------------------------------------------------- per-k node lists

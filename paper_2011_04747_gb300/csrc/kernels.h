@@ -60,6 +60,10 @@ struct DiffOp {
     int nx = 1, ny = 1, nz = 1;
     void* coef = nullptr;    // table: [nz*9][28] off-diagonal dt_ad K_ij / m_i (centre entry and pad 0)
     uint16_t* cls = nullptr; // table row of each node (nullable)
+    // 3D table in float: entry pairs of the rows of nodes (x, y, z) and
+    // (x, y + 1, z), [nz][3 y class of the first][3 y class of the second]
+    // [3 x class][28][2] (nullable)
+    void* pcoef = nullptr;
     int per_node = 0;        // 1: coef holds one row per node (row i for node i), cls unused
     // SELL-32 (rows in chunks of 32, column-major inside a chunk)
     int64_t n_chunks = 0;
@@ -136,9 +140,10 @@ void launch_reaction(const DevState& s, const ModelArgs& m, double dt, StepRef s
 // pdl: launch with programmatic dependent launch (the kernels wait for their
 // predecessor before touching memory either way).
 // block: 32..256 one thread per node; 0 on structured grids: 2D shared-memory
-// tiles or the 3D register z-march with zrun planes per thread (0: automatic).
+// tiles, or in 3D (float, ghost-padded V, per-class table) runs of `rows`
+// nodes along y per thread (2 or 4; 0 = 2), else one thread per node.
 void launch_diffusion(const DevState& s, const DiffOp& op, int src, bool sync, int par, const SyncArgs& sa,
-                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false, int zrun = 0);
+                      StepRef step, bool lists, int block, cudaStream_t st, bool pdl = false, int rows = 0);
 void launch_rebuild_lists(const DevState& s, int par, cudaStream_t st);
 void launch_tick(long long* ctr, long long inc, cudaStream_t st);
 void launch_set_counter(long long* ctr, long long value, cudaStream_t st);

@@ -76,17 +76,18 @@ def test_full_batch_sampled_tissues():
 
 
 @pytest.mark.parametrize("dims", [(101, 101, 26), (401, 401, 26)])
-def test_zmarch_diffusion_bit_identical_at_bench_sizes(dims):
-    """The register z-march diffusion kernel (diff_block = 0) against the
-    one-thread-per-node kernel on the bench slab and the 4.18 M-node slab,
-    over the stimulus and upstroke (lists, uniform-k votes and plain
-    sub-steps), FP32 with compensated V: identical states."""
+def test_yrun_diffusion_bit_identical_at_bench_sizes(dims):
+    """The 3D diffusion kernel with runs of 2 and 4 nodes along y per thread
+    (diff_block = 0, packed FP32) against the one-thread-per-node kernel on
+    the bench slab and the 4.18 M-node slab, over the stimulus and upstroke
+    (lists, uniform-k votes and plain sub-steps), FP32 with compensated V:
+    identical states."""
     binding = ensure_lib()
     wl = I.tp06_slab_3d(*dims, t_end=6.0)
     out = []
-    for diff_block in (256, 0):
+    for diff_block, rows in ((256, 0), (0, 2), (0, 4)):
         s = binding.solver_from_workload(wl, precision="fp32_kahan", graph_steps=20)
-        s.daeti_set_tuning(diff_block=diff_block)
+        s.daeti_set_tuning(diff_block=diff_block, diff_rows=rows)
         s.daeti_advance(3.0)
         s.daeti_advance(6.0)
         out.append((s.daeti_read_v(), s.daeti_read_activation(), s.daeti_get_substeps()))

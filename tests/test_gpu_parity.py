@@ -315,8 +315,10 @@ def test_full_slab_bench_config_first_steps(precision):
 def test_launch_shapes_do_not_change_results(wl_name):
     """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
     programmatic dependent launch or plain launches, graphs, and the
-    diff_block = 0 kernels (2D shared-memory tiles, 3D register z-march with
-    automatic and given z-runs) give bit-identical states (l = 1, 3 and 4)."""
+    diff_block = 0 kernels (2D shared-memory tiles; in 3D runs of 2 or 4 nodes
+    along y per thread with packed FP32 arithmetic, and the one-thread-per-node
+    kernel they fall back to in FP64) give bit-identical states (l = 1, 3
+    and 4)."""
     from parity_util import ensure_lib
 
     binding = ensure_lib()
@@ -338,8 +340,9 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 dict(diff_block=0),
                 dict(diff_block=0, fuse_diffusion=0, graph_steps=0),
                 dict(diff_block=0, bucket_k=0, pdl=0),
-                dict(diff_block=0, diff_zrun=2),
-                dict(diff_block=0, diff_zrun=5, fuse_diffusion=0, graph_steps=0)]
+                dict(diff_block=0, diff_rows=2),
+                dict(diff_block=0, diff_rows=4, fuse_diffusion=0, graph_steps=0),
+                dict(diff_block=0, diff_rows=4, bucket_k=0, pdl=0)]
     ref = None
     for prec in ("fp32_kahan", "fp64"):
         ref = None
