@@ -640,16 +640,20 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
     s.daeti_advance(prof_steps * st["dt"])
     s.daeti_synchronize()
     ms, nl = s.daeti_get_kernel_time(1)
-    b, _ = s.daeti_kernel_work(1)
+    b_plain, _ = s.daeti_kernel_work(1)
+    b_sync, _ = s.daeti_kernel_work(2)
     tuning_used = s.daeti_get_tuning()
     fused = tuning_used["fuse_diffusion"]
     s.daeti_set_profiling(0)
     s.close()
-    # diffusion sub-steps per diffusion launch (a 2D grid's tiled path applies several per launch);
-    # GB/s counts the algorithmic bytes of every sub-step the launch applies
-    sub_per_launch = (2 * st["l"] - (1 if fused else 0)) * prof_steps / max(nl, 1)
-    diff = {"avg_us": 1e3 * ms / max(nl, 1), "bytes_per_substep": b, "substeps_per_launch": sub_per_launch,
-            "GBs": b * sub_per_launch / (ms / max(nl, 1) / 1e3) / 1e9 if ms else None}
+    # separate diffusion launches per step: step I's l sub-steps (the last one
+    # inside the reaction launch when fused) and step III's l, the last of
+    # which synchronises; GB/s counts each launch's algorithmic bytes
+    per_step = 2 * st["l"] - (1 if fused else 0)
+    total_b = prof_steps * ((per_step - 1) * b_plain + b_sync)
+    diff = {"avg_us": 1e3 * ms / max(nl, 1), "launches": nl, "synchronising_per_step": 1,
+            "plain_per_step": per_step - 1, "bytes_plain": b_plain, "bytes_synchronising": b_sync,
+            "GBs": total_b / (ms / 1e3) / 1e9 if ms else None}
     if diff["GBs"]:
         diff["frac_of_measured_hbm"] = diff["GBs"] / _peaks().get("hbm_gbs", 6786.9)
     line = {"metric": UNIT + " (" + name + ")", "value": env.world * wl.n_nodes * n_steps / sec, "unit": UNIT,
