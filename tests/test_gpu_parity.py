@@ -273,6 +273,14 @@ def test_error_paths():
         s.daeti_synchronize()
     assert e.value.code == binding.ENONFINITE
     s.daeti_init_state()
+    # launch shapes outside their ranges are refused and leave the tuning as it was
+    before = s.daeti_get_tuning()
+    for bad_shape in (dict(diff_rows=3), dict(diff_rows=-1), dict(react_block=48), dict(diff_block=512),
+                      dict(react_min_blocks=7), dict(pdl=2)):
+        with pytest.raises(binding.DaetiError) as e:
+            s.daeti_set_tuning(**bad_shape)
+        assert e.value.code == binding.EINVAL, bad_shape
+    assert s.daeti_get_tuning() == before
     s.close()
     # tet meshes: an index out of range, a node in no tetrahedron
     xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], dtype=float) * 0.1
@@ -311,7 +319,7 @@ def test_full_slab_bench_config_first_steps(precision):
     _compare(wl, 30, 10, precision)
 
 
-@pytest.mark.parametrize("wl_name", ["slab", "slab_wide", "sheet2d", "sheet_l3", "sheet_l4", "hetero_slab"])
+@pytest.mark.parametrize("wl_name", ["slab", "slab_wide", "slab_even", "sheet2d", "sheet_l3", "sheet_l4", "hetero_slab"])
 def test_launch_shapes_do_not_change_results(wl_name):
     """Fused or separate diffusion sub-step, register caps, block sizes, k lists,
     programmatic dependent launch or plain launches, graphs, and the
@@ -327,6 +335,7 @@ def test_launch_shapes_do_not_change_results(wl_name):
                 "sheet_l3": (I.aniso_sheet_2d(n=37, length=0.36, model="tp06"), {}),
                 "sheet_l4": (I.aniso_sheet_2d(n=45, length=0.44, model="tp06"), dict(l_rounding="ceil")),
                 "slab_wide": (I.tp06_slab_3d(45, 21, 7, t_end=12), {}),
+                "slab_even": (I.tp06_slab_3d(24, 18, 6, t_end=12), {}),
                 "hetero_slab": (_heterogeneous(I.tp06_slab_3d(23, 19, 9, t_end=12)), {})}[wl_name]
     variants = [dict(),
                 dict(fuse_diffusion=0),
