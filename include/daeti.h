@@ -375,9 +375,10 @@ int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
  *     legacy default stream); results in *dt_s and *lambda_max (host);
  *     errbuf/errbuf_len: optional caller buffer for an error message.
  *   - The first call on each device (with that device current) looks up the
- *     array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.  Every call synchronises `stream` and copies
- *     its results into host memory before it returns.
+ *     array's device address (cudaGetSymbolAddress).  Every call synchronises
+ *     `stream` and copies its results into host memory before it returns, so
+ *     it must not be made on a stream under capture: such a call returns
+ *     DAETI_EINVAL before any work.
  *   - Every call shares the one array and leaves its contents behind; calls
  *     whose work overlaps on the GPU (from several host threads with
  *     different streams) race on it.  Host-side calls are serialised. */

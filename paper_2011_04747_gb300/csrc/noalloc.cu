@@ -97,6 +97,15 @@ extern "C" int daeti_grid_stability_noalloc(int dim, const int64_t n[3], double 
         set_err(errbuf, errbuf_len, "n_elem does not match the grid");
         return DAETI_EINVAL;
     }
+    // the call synchronises the stream and reads its results on the host,
+    // neither of which a capturing stream allows
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (qe != cudaSuccess) cudaGetLastError();
+    if (qe != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        set_err(errbuf, errbuf_len, "stream is capturing (or its capture status is unavailable)");
+        return DAETI_EINVAL;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
 
     for (int64_t e = 0; e < n_elem; ++e) {

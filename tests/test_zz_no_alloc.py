@@ -55,3 +55,27 @@ def test_noalloc_rejects_conductivity_varying_within_a_layer():
     with pytest.raises(binding.DaetiError) as e:
         binding.daeti_grid_stability_noalloc(wl.dim, wl.n, wl.h, d, wl.d_trans, wl.fibre)
     assert e.value.code == binding.EUNSUPPORTED
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream and reads results on the host, so on a
+    stream under capture it must return EINVAL before any work (and leave the
+    capture intact); afterwards it works as before."""
+    import torch
+
+    binding = ensure_lib()
+    wl = I.ms_square_2d(n=11)
+    ref_dts, _ = _context_path(binding, wl)
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device="cuda")
+    with torch.cuda.graph(graph, stream=stream):
+        x += 1.0
+        with pytest.raises(binding.DaetiError) as e:
+            binding.daeti_grid_stability_noalloc(wl.dim, wl.n, wl.h, wl.d_long, wl.d_trans, wl.fibre, stream=stream)
+    assert e.value.code == binding.EINVAL and "capturing" in str(e.value)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0            # recorded by the capture, run by the one replay
+    dts, _ = binding.daeti_grid_stability_noalloc(wl.dim, wl.n, wl.h, wl.d_long, wl.d_trans, wl.fibre)
+    assert abs(dts - ref_dts) <= 1e-12 * ref_dts
