@@ -517,6 +517,11 @@ def bench_slab(args, env):
         for which, name in ((0, "reaction"), (1, "diffusion")):
             ms, nl = s32.daeti_get_kernel_time(which)
             b, f = s32.daeti_kernel_work(which)
+            if which == 1:
+                # one launch per step ends step III and synchronises (its
+                # epilogue's bytes on top); the others are plain sub-steps
+                per_step = 2 * stab["l"] - (1 if s32.daeti_get_tuning()["fuse_diffusion"] else 0)
+                b += s32.daeti_kernel_work(2)[0] / per_step
             dst[name] = {"total_ms": ms, "launches": nl, "avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b}
         if mode == 2:
             roof = _reaction_roofline(s32, clocks, sub_per_step)
@@ -650,9 +655,9 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
     # inside the reaction launch when fused) and step III's l, the last of
     # which synchronises; GB/s counts each launch's algorithmic bytes
     per_step = 2 * st["l"] - (1 if fused else 0)
-    total_b = prof_steps * ((per_step - 1) * b_plain + b_sync)
+    total_b = prof_steps * (per_step * b_plain + b_sync)
     diff = {"avg_us": 1e3 * ms / max(nl, 1), "launches": nl, "synchronising_per_step": 1,
-            "plain_per_step": per_step - 1, "bytes_plain": b_plain, "bytes_synchronising": b_sync,
+            "plain_per_step": per_step - 1, "bytes_plain": b_plain, "bytes_synchronising": b_plain + b_sync,
             "GBs": total_b / (ms / 1e3) / 1e9 if ms else None}
     if diff["GBs"]:
         diff["frac_of_measured_hbm"] = diff["GBs"] / _peaks().get("hbm_gbs", 6786.9)

@@ -348,7 +348,11 @@ int daeti_time_launches(daeti_ctx* ctx, int which, int count, double* ms_per_lau
 /* Algorithmic bytes of one launch of kernel `which` at the current problem
  * and its arithmetic operations: for which = 1 (diffusion) per launch, for
  * which = 0 (reaction) per node sub-step (multiply by daeti_get_substeps per
- * launch); add/sub/mul/fma and each exp, log, reciprocal, rsqrt count one. */
+ * launch); add/sub/mul/fma and each exp, log, reciprocal, rsqrt count one.
+ * which = 2: the bytes the synchronisation adds to the diffusion launch that
+ * ends step III (V at the last synchronisation read and written, k written,
+ * activation time read, list entry written with k lists), so that launch
+ * moves the bytes of which = 1 plus these; no operations. */
 int daeti_kernel_work(daeti_ctx* ctx, int which, double* bytes, double* flops);
 
 /* ---------------------------------------------------------------------------
