@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "diffops.cuh"
+#include "fastdiv.h"
 
 namespace daeti {
 
@@ -134,26 +135,6 @@ static void sub_launch(bool sync, int grid, int block, cudaStream_t st, bool pdl
 // stencil_update's order, so results equal the one-thread-per-node kernel's.
 // Coefficients come from the table of entry pairs (op.pcoef): one 16-byte
 // load gives the pairs of two entries.
-
-// Quotient n / d for 0 <= n < 2^31 by a multiply and a shift (Granlund and
-// Montgomery, division by invariant integers): k = 32 + ceil(log2 d),
-// m = floor(2^k / d) + 1; then floor(n m / 2^k) = floor(n / d) because
-// n (m d - 2^k) <= n d < 2^k.
-struct FastDiv {
-    unsigned long long m;
-    int k;
-};
-inline FastDiv fast_div(unsigned d) {
-    int c = 0;
-    while ((1ull << c) < d) ++c;
-    FastDiv f;
-    f.k = 32 + c;
-    f.m = (1ull << f.k) / d + 1;
-    return f;
-}
-__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
-    return (int)(((unsigned long long)(unsigned)n * f.m) >> f.k);
-}
 
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     unsigned long long r;
