@@ -14,11 +14,10 @@
 // The launch that ends a diffusion half at t_n also runs the synchronisation
 // epilogue (activation time, k of the next step A, and either the per-k node
 // lists or, after a step with one k at every node, the check that k is still
-// uniform).  The
-// last sub-step of each step I is fused into the reaction launch
-// (reaction.cu).
-#include <algorithm>
-
+// uniform).  The last sub-step of each step I is fused into the reaction
+// launch (reaction_impl.cuh).  Launch shapes, all with the same terms in the
+// same order (bit-identical results): one thread per node; 2D shared-memory
+// tiles; in 3D (float) runs of 2 or 4 nodes along y per thread.
 #include "diffops.cuh"
 #include "fastdiv.h"
 
