@@ -440,6 +440,16 @@ def _adjoint_precision(binding, stream):
             "grad_tau_close_rel_err": abs(t32 - t64) / abs(t64)}
 
 
+def diffusion_launch_work(l, fused, bytes_substep, bytes_sync):
+    """Separate diffusion launches per Strang step and their algorithmic bytes
+    per step.  Step I has l sub-steps (the last one inside the reaction launch
+    when fused), step III has l, and the last of them also synchronises:
+    bytes_substep (daeti_kernel_work(1)) per launch plus bytes_sync
+    (daeti_kernel_work(2)) once per step."""
+    launches = 2 * l - (1 if fused else 0)
+    return launches, launches * bytes_substep + bytes_sync
+
+
 def _reaction_roofline(solver, clocks, sub_per_step):
     """ALU roofline of the reaction kernel from the per-launch event-timed pass."""
     ms, nl = solver.daeti_get_kernel_time(0)
@@ -518,10 +528,10 @@ def bench_slab(args, env):
             ms, nl = s32.daeti_get_kernel_time(which)
             b, f = s32.daeti_kernel_work(which)
             if which == 1:
-                # one launch per step ends step III and synchronises (its
-                # epilogue's bytes on top); the others are plain sub-steps
-                per_step = 2 * stab["l"] - (1 if s32.daeti_get_tuning()["fuse_diffusion"] else 0)
-                b += s32.daeti_kernel_work(2)[0] / per_step
+                # average over the step's launches, the synchronising one included
+                per_step, b_step = diffusion_launch_work(stab["l"], s32.daeti_get_tuning()["fuse_diffusion"], b,
+                                                         s32.daeti_kernel_work(2)[0])
+                b = b_step / per_step
             dst[name] = {"total_ms": ms, "launches": nl, "avg_us": 1e3 * ms / max(nl, 1), "bytes_per_launch": b}
         if mode == 2:
             roof = _reaction_roofline(s32, clocks, sub_per_step)
@@ -654,8 +664,8 @@ def bench_simple(args, env, wl, name, precision="fp32_kahan", t_end=None, steps_
     # separate diffusion launches per step: step I's l sub-steps (the last one
     # inside the reaction launch when fused) and step III's l, the last of
     # which synchronises; GB/s counts each launch's algorithmic bytes
-    per_step = 2 * st["l"] - (1 if fused else 0)
-    total_b = prof_steps * (per_step * b_plain + b_sync)
+    per_step, b_step = diffusion_launch_work(st["l"], fused, b_plain, b_sync)
+    total_b = prof_steps * b_step
     diff = {"avg_us": 1e3 * ms / max(nl, 1), "launches": nl, "synchronising_per_step": 1,
             "plain_per_step": per_step - 1, "bytes_plain": b_plain, "bytes_synchronising": b_plain + b_sync,
             "GBs": total_b / (ms / 1e3) / 1e9 if ms else None}
