@@ -661,7 +661,8 @@ static int upload_operator(daeti_ctx* c, const GridTable& tab, bool table, const
         if ((rc = upload_real(c, c->op.coef, A.data(), (int64_t)A.size()))) return rc;
         if (tab.dim == 3 && R == 4) {
             // entry pairs (row of a node, row of the node one y above it) for
-            // the y-paired kernel, every pair of y classes
+            // the 3D y-run diffusion kernel, every pair of y classes; the
+            // same doubles as the table, so the same floats
             std::vector<double> P((size_t)tab.nz * 27 * 2 * DAETI_ROW, 0.0);
             for (int z = 0; z < tab.nz; ++z)
                 for (int ca = 0; ca < 3; ++ca)
