@@ -250,7 +250,8 @@ int daeti_get_substeps(daeti_ctx* ctx, int64_t* total);
  * 256); 0: on structured grids, 2D shared-memory tiles, or in 3D (float
  * precisions, per-layer D) runs of diff_rows nodes along y per thread that
  * share their rows' loads and go in pairs through packed FP32 operations
- * (other meshes and FP64 take 256);
+ * (other meshes, FP64, per-node D and the synchronising launch of the
+ * reaction-rate k rule take 256);
  * fuse_diffusion: run the last diffusion sub-step of step I inside the
  * reaction launch; bucket_k: group nodes by k before step A; graph_steps:
  * steps per captured CUDA graph (rounded up to even, 0 = plain launches);
